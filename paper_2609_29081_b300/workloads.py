@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs shaped like the paper's test problems.
+
+This module only builds initial data: it evaluates an initial condition, takes
+cell averages by 5-point Gauss-Legendre quadrature per direction and samples the
+point values. It holds none of the AF method's arithmetic, and it is the one
+module that both the CUDA path (bench, tests) and the CPU oracle tests use.
+
+Packed state layout (component-major, x index fastest), shared with the C-ABI:
+  2D: avg[4][n2][n1], xe[4][n2][n1+1], ye[4][n2+1][n1], vx[4][n2+1][n1+1]
+  1D: avg[3][n1],     pt[3][n1+1]
+Components are conservative: (rho, rho*u, [rho*v,] E).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BC_PERIODIC, BC_WALL, BC_SYMMETRY, BC_TRANSMISSIVE = 0, 1, 2, 3
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: tuple
+    lo: tuple
+    hi: tuple
+    gamma: float
+    mu: float
+    Pr: float
+    bc: tuple
+    t_end: float
+    state: np.ndarray = field(repr=False)
+    steps: int = 0          # nominal step count of the configuration (0: run to t_end)
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.n[: self.dim]))
+
+
+def site_shapes(dim, n1, n2=1):
+    if dim == 1:
+        return [(3, n1), (3, n1 + 1)]
+    return [(4, n2, n1), (4, n2, n1 + 1), (4, n2 + 1, n1), (4, n2 + 1, n1 + 1)]
+
+
+def split_sites(state, dim, n1, n2=1):
+    """Views of the packed state, one per DoF site (avg, [xe, ye, vx] or [pt])."""
+    out, o = [], 0
+    for shp in site_shapes(dim, n1, n2):
+        sz = int(np.prod(shp))
+        out.append(state[o:o + sz].reshape(shp))
+        o += sz
+    assert o == state.size
+    return out
+
+
+def state_len(dim, n1, n2=1):
+    return sum(int(np.prod(s)) for s in site_shapes(dim, n1, n2))
+
+
+def _to_cons(gamma, rho, vel, p):
+    m = [rho * v for v in vel]
+    E = p / (gamma - 1.0) + 0.5 * rho * sum(v * v for v in vel)
+    return [rho, *m, E]
+
+
+def project(dim, n, lo, hi, gamma, prim_fn):
+    """Packed state of a primitive initial condition prim_fn(x[,y]) -> (rho, vel list, p)."""
+    gx, gw = np.polynomial.legendre.leggauss(5)
+    gw = gw / 2.0
+    if dim == 1:
+        n1 = n[0]
+        dx = (hi[0] - lo[0]) / n1
+        xc = lo[0] + (np.arange(n1) + 0.5) * dx
+        avg = np.zeros((3, n1))
+        for q in range(5):
+            rho, vel, p = prim_fn(xc + 0.5 * dx * gx[q])
+            for c, v in enumerate(_to_cons(gamma, rho, vel, p)):
+                avg[c] += gw[q] * v
+        xf = lo[0] + np.arange(n1 + 1) * dx
+        rho, vel, p = prim_fn(xf)
+        pt = np.array(_to_cons(gamma, rho, vel, p))
+        return np.concatenate([avg.ravel(), pt.ravel()])
+    n1, n2 = n
+    dx = (hi[0] - lo[0]) / n1
+    dy = (hi[1] - lo[1]) / n2
+    xc = lo[0] + (np.arange(n1) + 0.5) * dx
+    yc = lo[1] + (np.arange(n2) + 0.5) * dy
+    xf = lo[0] + np.arange(n1 + 1) * dx
+    yf = lo[1] + np.arange(n2 + 1) * dy
+    avg = np.zeros((4, n2, n1))
+    for qy in range(5):
+        Y = (yc + 0.5 * dy * gx[qy])[:, None]
+        for qx in range(5):
+            X = (xc + 0.5 * dx * gx[qx])[None, :]
+            rho, vel, p = prim_fn(np.broadcast_to(X, (n2, n1)), np.broadcast_to(Y, (n2, n1)))
+            for c, v in enumerate(_to_cons(gamma, rho, vel, p)):
+                avg[c] += gw[qx] * gw[qy] * v
+
+    def sample(x, y):
+        X, Y = np.meshgrid(x, y)
+        rho, vel, p = prim_fn(X, Y)
+        return np.array([np.broadcast_to(v, X.shape) for v in _to_cons(gamma, rho, vel, p)])
+
+    return np.concatenate([avg.ravel(), sample(xf, yc).ravel(), sample(xc, yf).ravel(),
+                           sample(xf, yf).ravel()])
+
+
+# ---------------------------------------------------------------------------
+# Configurations
+# ---------------------------------------------------------------------------
+
+def smooth_1d(n=128, mu=0.01, Pr=0.72, gamma=1.4, t_end=0.5):
+    """1D periodic smooth wave on [0, 2 pi): rho = 1 + 0.2 sin x, u = 1, p = 1."""
+    lo, hi = (0.0,), (2 * np.pi,)
+
+    def f(x):
+        return 1.0 + 0.2 * np.sin(x), [np.ones_like(x)], np.ones_like(x)
+
+    s = project(1, (n,), lo, hi, gamma, f)
+    return Workload("smooth_1d_periodic_N%d" % n, 1, (n,), lo, hi, gamma, mu, Pr,
+                    (BC_PERIODIC,) * 4, t_end, s)
+
+
+def shock_tube_1d(n=4096, mu=1e-3, Pr=0.72, gamma=1.4, t_end=0.2):
+    """1D viscous Sod-type tube on [0,1], transmissive ends."""
+    lo, hi = (0.0,), (1.0,)
+
+    def f(x):
+        left = x < 0.5
+        return (np.where(left, 1.0, 0.125), [np.zeros_like(x)], np.where(left, 1.0, 0.1))
+
+    s = project(1, (n,), lo, hi, gamma, f)
+    return Workload("shock_tube_1d_N%d" % n, 1, (n,), lo, hi, gamma, mu, Pr,
+                    (BC_TRANSMISSIVE,) * 4, t_end, s)
+
+
+def fourier_modes(seed, nmodes=8, amp=0.05, kmax=4):
+    """Seeded velocity perturbation: nmodes wavevectors from {1..kmax}^2 without
+    replacement, random phases, per-mode amplitude amp / nmodes."""
+    rng = np.random.default_rng(seed)
+    ks = [(a, b) for a in range(1, kmax + 1) for b in range(1, kmax + 1)]
+    pick = rng.choice(len(ks), size=nmodes, replace=False)
+    ph = rng.uniform(0.0, 2 * np.pi, size=(nmodes, 2))
+    return [(ks[p][0], ks[p][1], ph[q, 0], ph[q, 1], amp / nmodes) for q, p in enumerate(pick)]
+
+
+def smooth_2d(n=1024, mu=0.01, Pr=0.72, gamma=1.4, seed=3, steps=200, mean=(1.0, 0.5), amp=0.05,
+              t_end=0.0):
+    """2D periodic smooth flow on [0, 2 pi)^2: rho = 1 + 0.2 sin(x + y),
+    (u, v) = mean + 8-mode Fourier perturbation, p = 1."""
+    lo, hi = (0.0, 0.0), (2 * np.pi, 2 * np.pi)
+    modes = fourier_modes(seed, amp=amp)
+
+    def f(x, y):
+        du = np.zeros_like(x)
+        dv = np.zeros_like(x)
+        for k1, k2, p1, p2, a in modes:
+            du = du + a * np.sin(k1 * x + k2 * y + p1)
+            dv = dv + a * np.cos(k1 * x + k2 * y + p2)
+        return 1.0 + 0.2 * np.sin(x + y), [mean[0] + du, mean[1] + dv], np.ones_like(x)
+
+    nn = (n, n) if np.isscalar(n) else tuple(n)
+    s = project(2, nn, lo, hi, gamma, f)
+    return Workload("smooth_2d_periodic_%dx%d" % nn, 2, nn, lo, hi, gamma, mu, Pr,
+                    (BC_PERIODIC,) * 4, t_end, s, steps)
+
+
+def shock_tube_2d(n=(2000, 1000), mu=1e-3, Pr=0.73, gamma=1.4, t_end=1.0):
+    """2D viscous shock tube in a walled box [0,1]x[0,0.5] (Daru-Tenaud setup):
+    no-slip adiabatic walls at x=0, x=1, y=0; symmetry at y=0.5."""
+    lo, hi = (0.0, 0.0), (1.0, 0.5)
+
+    def f(x, y):
+        left = x < 0.5
+        rho = np.where(left, 120.0, 1.2)
+        return rho, [np.zeros_like(x), np.zeros_like(x)], rho / gamma
+
+    s = project(2, tuple(n), lo, hi, gamma, f)
+    return Workload("shock_tube_2d_%dx%d" % tuple(n), 2, tuple(n), lo, hi, gamma, mu, Pr,
+                    (BC_WALL, BC_WALL, BC_WALL, BC_SYMMETRY), t_end, s)
+
+
+def entropy_wave_2d(n=32, gamma=1.4, mean=(1.0, 0.5), t=0.0, amp=0.2):
+    """Exact Euler solution (mu = 0): rho = 1 + amp sin(x + y - (u+v) t), constant u, v, p."""
+    lo, hi = (0.0, 0.0), (2 * np.pi, 2 * np.pi)
+
+    def f(x, y):
+        ph = x + y - (mean[0] + mean[1]) * t
+        return 1.0 + amp * np.sin(ph), [np.full_like(x, mean[0]), np.full_like(x, mean[1])], np.ones_like(x)
+
+    nn = (n, n) if np.isscalar(n) else tuple(n)
+    s = project(2, nn, lo, hi, gamma, f)
+    return Workload("entropy_wave_2d_%dx%d" % nn, 2, nn, lo, hi, gamma, 0.0, 0.72,
+                    (BC_PERIODIC,) * 4, 0.0, s)
+
+
+def entropy_wave_1d(n=32, gamma=1.4, u=1.0, t=0.0, amp=0.2):
+    lo, hi = (0.0,), (2 * np.pi,)
+
+    def f(x):
+        return 1.0 + amp * np.sin(x - u * t), [np.full_like(x, u)], np.ones_like(x)
+
+    s = project(1, (n,), lo, hi, gamma, f)
+    return Workload("entropy_wave_1d_N%d" % n, 1, (n,), lo, hi, gamma, 0.0, 0.72,
+                    (BC_PERIODIC,) * 4, 0.0, s)
+
+
+def random_smooth_2d(n=(24, 20), seed=0, mu=0.01, Pr=0.72, gamma=1.4, bc=(0, 0, 0, 0), amp=0.1,
+                     lo=(0.0, 0.0), hi=(2 * np.pi, 2 * np.pi)):
+    """Seeded smooth periodic-in-shape fields for parity cases (uneven sizes)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, size=(4, 3, 2))
+    L = (hi[0] - lo[0], hi[1] - lo[1])
+
+    def f(x, y):
+        X = 2 * np.pi * (x - lo[0]) / L[0]
+        Y = 2 * np.pi * (y - lo[1]) / L[1]
+        g = []
+        for q in range(4):
+            v = 0.0
+            for k in range(3):
+                v = v + c[q, k, 0] * np.sin((k + 1) * X + c[q, k, 1]) * np.cos(k * Y + 0.5 * c[q, k, 0])
+            g.append(v)
+        return 1.0 + amp * g[0], [0.3 + amp * g[1], -0.2 + amp * g[2]], 1.0 + amp * g[3]
+
+    s = project(2, tuple(n), lo, hi, gamma, f)
+    return Workload("random_smooth_2d_%dx%d_s%d" % (n[0], n[1], seed), 2, tuple(n), lo, hi, gamma,
+                    mu, Pr, tuple(bc), 0.0, s)
+
+
+def blast_2d(n=(32, 32), seed=0, mu=1e-3, Pr=0.72, gamma=1.4, rho_min=1e-6, p_min=1e-8):
+    """Near-vacuum Gaussian blast on a periodic square (stresses both limiters)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = (0.0, 0.0), (1.0, 1.0)
+    cx, cy = rng.uniform(0.3, 0.7, size=2)
+    sig = 1.0 / 16.0
+
+    def f(x, y):
+        r2 = (x - cx) ** 2 + (y - cy) ** 2
+        g = np.exp(-r2 / (2 * sig * sig))
+        return rho_min + g, [np.zeros_like(x), np.zeros_like(x)], p_min + g
+
+    s = project(2, tuple(n), lo, hi, gamma, f)
+    return Workload("blast_2d_%dx%d_s%d" % (n[0], n[1], seed), 2, tuple(n), lo, hi, gamma, mu, Pr,
+                    (BC_PERIODIC,) * 4, 0.0, s)

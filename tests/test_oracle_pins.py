@@ -1,0 +1,537 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+The paper prints no numeric tables or worked examples (all its error plots are
+figures), so every pin here is a closed form, an invariant, a textbook special
+case, an exact solution or a convergence rate. Each test names the passage it
+pins and the mistakes it would catch.
+"""
+import numpy as np
+import pytest
+
+from paper_2609_29081_b300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1 operators, Eqs. (7)-(10)
+# ---------------------------------------------------------------------------
+
+def lattice_samples(f, x0, h):
+    return np.array([f(x0 + k * h) for k in range(-2, 3)])
+
+
+def test_biased_operators_exact_on_cubics(orc):
+    """Eq. (7): D_+ / D_- differentiate the cubic through their 4 nodes exactly."""
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        c = rng.normal(size=4)
+        f = lambda x: c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+        df = lambda x: c[1] + 2 * c[2] * x + 3 * c[3] * x ** 2
+        dx = rng.uniform(0.1, 1.0)
+        x0 = rng.uniform(-1, 1)
+        z = lattice_samples(f, x0, dx / 2)
+        assert orc.op("dplus", z, dx) == pytest.approx(df(x0), rel=1e-11, abs=1e-11)
+        assert orc.op("dminus", z, dx) == pytest.approx(df(x0), rel=1e-11, abs=1e-11)
+    # they are genuinely biased: a quartic is not differentiated exactly, with
+    # errors of opposite sign, so swapping the two would flip the upwinding
+    f = lambda x: x ** 4
+    z = lattice_samples(f, 0.0, 0.5)
+    ep, em = orc.op("dplus", z, 1.0), orc.op("dminus", z, 1.0)
+    assert ep != 0.0 and em != 0.0 and np.sign(ep) == -np.sign(em)
+
+
+def test_central_operator_is_half_sum_and_fourth_order(orc):
+    """Eq. (8): D_c = (D_+ + D_-)/2, exact on quartics."""
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        z = rng.normal(size=5)
+        dx = rng.uniform(0.1, 2.0)
+        half = 0.5 * (orc.op("dplus", z, dx) + orc.op("dminus", z, dx))
+        assert orc.op("dcentral", z, dx) == pytest.approx(half, rel=1e-12, abs=1e-12)
+    c = rng.normal(size=5)
+    f = lambda x: sum(c[k] * x ** k for k in range(5))
+    df = lambda x: sum(k * c[k] * x ** (k - 1) for k in range(1, 5))
+    z = lattice_samples(f, 0.3, 0.2)
+    assert orc.op("dcentral", z, 0.4) == pytest.approx(df(0.3), rel=1e-11)
+
+
+def test_compact_second_derivative_textbook_case(orc):
+    """Eqs. (9)-(10) with K = 1: the textbook 5-point fourth-order second derivative
+    on spacing h = dx/2, (-1, 16, -30, 16, -1)/(12 h^2); rows of B sum to zero."""
+    B = orc.bmatrix()
+    assert np.allclose(B.sum(axis=0), np.array([-1, 16, -30, 16, -1]) / 12.0, atol=1e-15)
+    assert np.allclose(B.sum(axis=1), 0.0, atol=1e-15)
+    rng = np.random.default_rng(2)
+    z = rng.normal(size=5)
+    dx = 0.7
+    h = dx / 2
+    ref = (-z[0] + 16 * z[1] - 30 * z[2] + 16 * z[3] - z[4]) / (12 * h * h)
+    assert orc.d2_scalar(np.ones(5), z, dx) == pytest.approx(ref, rel=1e-12)
+
+
+def test_compact_second_derivative_variable_k_fourth_order(orc):
+    """Eq. (9) approximates (K Z')' to fourth order for smooth variable K."""
+    K = lambda x: 1.0 + 0.3 * np.sin(x)
+    Z = lambda x: np.cos(2 * x)
+    exact = lambda x: 0.3 * np.cos(x) * (-2 * np.sin(2 * x)) + K(x) * (-4 * np.cos(2 * x))
+    errs = []
+    for dx in (0.2, 0.1, 0.05, 0.025):
+        e = 0.0
+        for x0 in np.linspace(0.1, 3.0, 7):
+            k5 = lattice_samples(K, x0, dx / 2)
+            z5 = lattice_samples(Z, x0, dx / 2)
+            e = max(e, abs(orc.d2_scalar(k5, z5, dx) - exact(x0)))
+        errs.append(e)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.8), rates
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3: SSP-RK54
+# ---------------------------------------------------------------------------
+
+def test_ssprk54_order_conditions(orc):
+    """The Shu-Osher table is a 5-stage 4th-order SSP method: convex rows,
+    nonnegative coefficients, and all 8 Butcher order conditions to order 4."""
+    a, b = orc.rk_table()
+    assert np.allclose(a.sum(axis=1), 1.0, atol=1e-14)
+    assert (a >= 0).all() and (b >= 0).all()
+    # Shu-Osher -> Butcher: u(i+1) = sum_k a[i,k] u(k) + b[i,k] dt L(u(k))
+    # stage values Y_k = u(k), k=0..4 (Y_0 = u^n); Butcher A (5x5) and weights
+    A = np.zeros((6, 5))  # row i: u(i) = u^n + dt sum_j A[i,j] L(Y_j)
+    for i in range(5):
+        for k in range(i + 1):
+            A[i + 1] += a[i, k] * A[k]
+            A[i + 1, k] += b[i, k]
+    Ab, wb = A[:5], A[5]
+    c = Ab.sum(axis=1)
+    conds = [
+        (wb.sum(), 1.0),
+        (wb @ c, 1 / 2),
+        (wb @ c ** 2, 1 / 3),
+        (wb @ Ab @ c, 1 / 6),
+        (wb @ c ** 3, 1 / 4),
+        (wb @ (c * (Ab @ c)), 1 / 8),
+        (wb @ Ab @ c ** 2, 1 / 12),
+        (wb @ Ab @ Ab @ c, 1 / 24),
+    ]
+    for got, want in conds:
+        assert got == pytest.approx(want, abs=1e-13)
+    # SSP coefficient min a/b over b>0 is about 1.508 (Spiteri-Ruuth)
+    r = min(a[i, k] / b[i, k] for i in range(5) for k in range(5) if b[i, k] > 0)
+    assert r == pytest.approx(1.508, abs=2e-3)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 1 / Sec. 2.2 physics and Sec. 3.1 lemmas
+# ---------------------------------------------------------------------------
+
+def random_states(rng, n, dim, gamma=1.4):
+    rho = rng.uniform(0.05, 3.0, n)
+    vel = rng.normal(0, 1.5, (n, dim))
+    p = rng.uniform(0.01, 3.0, n)
+    E = p / (gamma - 1) + 0.5 * rho * (vel ** 2).sum(axis=1)
+    return np.column_stack([rho, rho[:, None] * vel, E])
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_viscous_flux_matrices_match_stress_definition(orc, dim):
+    """Sec. 2.2 K matrices reproduce F^v of Eq. (2) with tau, q of Eq. (3)."""
+    rng = np.random.default_rng(3)
+    P = orc.problem(dim, 8, 8, mu=0.37, Pr=0.81, gamma=1.3)
+    kappa = P.gamma * P.mu / ((P.gamma - 1) * P.Pr)
+    for U in random_states(rng, 30, dim, gamma=P.gamma):
+        G = rng.normal(size=(dim, dim + 2))
+        G[:, 0] = 0.0
+        gu = G[:, 1:1 + dim]           # gu[m, k] = d u_k / d x_m
+        div = np.trace(gu)
+        tau = P.mu * (gu.T + gu - 2.0 / 3.0 * div * np.eye(dim))   # tau[k, l]
+        q = -kappa * G[:, dim + 1]
+        u = U[1:1 + dim] / U[0]
+        for l in range(dim):
+            Fv = orc.viscous_flux(P, U, G, l)
+            want = np.concatenate([[0.0], tau[:, l], [u @ tau[:, l] - q[l]]])
+            assert np.allclose(Fv, want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_lemma_3_1_inviscid_split_states(orc, dim):
+    """Lemma 3.1: U +- F^c_l / alpha in G for alpha >= |u_l| + c."""
+    rng = np.random.default_rng(4)
+    P = orc.problem(dim, 8, 8)
+    for U in random_states(rng, 200, dim):
+        for l in range(dim):
+            a = orc.wave_speed(P, U, l)
+            F = orc.inviscid_flux(P, U, l)
+            for s in (1.0, -1.0):
+                V = U + s * F / a
+                assert V[0] > 0 and orc.pressure(P, V) > -1e-12 * U[-1]
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_lemma_3_2_viscous_bound_is_sharp(orc, dim):
+    """Lemma 3.2: rho e(U +- F^v/beta) > 0 for beta > b_l, and b_l is the root:
+    at beta = b_l the worse sign lands exactly on rho e = 0."""
+    rng = np.random.default_rng(5)
+    P = orc.problem(dim, 8, 8, mu=0.05, Pr=0.72)
+    for U in random_states(rng, 100, dim):
+        G = rng.normal(size=(dim, dim + 2))
+        G[:, 0] = 0
+        for l in range(dim):
+            b = orc.visc_bound(P, U, G, l)
+            Fv = orc.viscous_flux(P, U, G, l)
+            rhoe = orc.pressure(P, U) / (P.gamma - 1)
+            at_b = min(orc.pressure(P, U + s * Fv / b) for s in (1, -1)) / (P.gamma - 1)
+            above = min(orc.pressure(P, U + s * Fv / (1.001 * b)) for s in (1, -1))
+            assert abs(at_b) < 1e-9 * rhoe
+            assert above > 0
+
+
+def test_theta_function_property(orc):
+    """Sec. 3.3: (1-t) zL + t zH >= eps for t in [0, Theta], Theta in [0,1]."""
+    rng = np.random.default_rng(6)
+    for _ in range(500):
+        eps = 10 ** rng.uniform(-14, -2)
+        zL = eps + abs(rng.normal()) * 10 ** rng.uniform(-6, 1)
+        zH = rng.normal() * 10 ** rng.uniform(-6, 1)
+        th = orc.theta(zL, zH, eps)
+        assert 0.0 <= th <= 1.0
+        for t in np.linspace(0, th, 5):
+            assert (1 - t) * zL + t * zH >= eps * (1 - 1e-12) - 1e-15
+        if zH < eps:
+            assert (1 - th) * zL + th * zH == pytest.approx(eps, rel=1e-9, abs=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Whole scheme: invariants
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,bc", [(1, (0, 0, 0, 0)), (1, (1, 3, 0, 0)), (2, (0, 0, 0, 0)),
+                                    (2, (1, 1, 1, 2)), (2, (3, 3, 2, 2))])
+@pytest.mark.parametrize("lim", [0, 2])
+def test_constant_state_preserved(orc, dim, bc, lim):
+    """A uniform state is an exact solution: the residual vanishes to roundoff."""
+    n = (10, 7)
+    wall = any(b in (1, 2) for b in bc[:2 * dim])
+    vel = [0.0, 0.0] if wall else [0.3, -0.2]
+    if dim == 1:
+        s = W.project(1, n[:1], (0.0,), (1.0,), 1.4, lambda x: (1.3 + 0 * x, [vel[0] + 0 * x], 0.9 + 0 * x))
+    else:
+        s = W.project(2, n, (0.0, 0.0), (1.0, 0.8), 1.4,
+                      lambda x, y: (1.3 + 0 * x, [vel[0] + 0 * x, vel[1] + 0 * x], 0.9 + 0 * x))
+    P = orc.problem(dim, n[0], n[1], lo=(0, 0), hi=(1.0, 0.8), mu=0.02, bc=bc, limiter=lim)
+    L, bad = orc.residual(P, s, 1e-3)
+    assert bad == 0
+    assert np.abs(L).max() < 1e-11
+
+
+@pytest.mark.parametrize("case", ["smooth", "blast"])
+def test_periodic_conservation(orc, case):
+    """Eq. (6a)/(12): the cell-average update is in flux form, so the sums of mass,
+    momentum and energy residuals vanish to roundoff on periodic grids, also where
+    the flux limiter is active."""
+    w = W.random_smooth_2d((14, 11), seed=7) if case == "smooth" else W.blast_2d((16, 16), seed=1)
+    P = orc.problem(2, *w.n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc)
+    dt = 0.5 * orc.dt_max(P, w.state)
+    L, ts, tp, bad = orc.residual(P, w.state, dt, with_theta=True)
+    avg = W.split_sites(L, 2, *w.n)[0]
+    scale = np.abs(avg).max(axis=(1, 2))
+    assert np.all(np.abs(avg.sum(axis=(1, 2))) < 1e-12 * scale * avg[0].size)
+    if case == "blast":
+        assert tp.min() < 1.0 or ts.min() < 1.0   # the limiter did fire
+
+
+def test_mirror_and_transpose_symmetry(orc):
+    """Reflection x -> -x (u -> -u) and transposition x <-> y (u <-> v) commute with L."""
+    n = 12
+    w = W.random_smooth_2d((n, n), seed=8, mu=0.05)
+    P = orc.problem(2, n, n, lo=w.lo, hi=w.hi, mu=0.05, Pr=0.7)
+    dt = 0.3 * orc.dt_max(P, w.state)
+    L = orc.residual(P, w.state, dt)[0]
+    avg, xe, ye, vx = W.split_sites(w.state, 2, n, n)
+    Lavg, Lxe, Lye, Lvx = W.split_sites(L, 2, n, n)
+    sgn = np.array([1, -1, 1, 1])[:, None, None]
+
+    def refl_cell(a):   # cell i -> n-1-i
+        return a[:, :, ::-1] * sgn
+
+    def refl_face(a):   # face i -> n-i (periodic duplicate at both ends)
+        return a[:, :, ::-1] * sgn
+
+    s2 = np.concatenate([refl_cell(avg).ravel(), refl_face(xe).ravel(), refl_cell(ye).ravel(),
+                         refl_face(vx).ravel()])
+    L2 = orc.residual(P, s2, dt)[0]
+    M = W.split_sites(L2, 2, n, n)
+    for got, want in zip(M, [refl_cell(Lavg), refl_face(Lxe), refl_cell(Lye), refl_face(Lvx)]):
+        assert np.allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+    perm = [0, 2, 1, 3]
+
+    def tr(a):
+        return np.ascontiguousarray(a[perm].transpose(0, 2, 1))
+
+    s3 = np.concatenate([tr(avg).ravel(), tr(ye).ravel(), tr(xe).ravel(), tr(vx).ravel()])
+    L3 = orc.residual(P, s3, dt)[0]
+    M = W.split_sites(L3, 2, n, n)
+    for got, want in zip(M, [tr(Lavg), tr(Lye), tr(Lxe), tr(Lvx)]):
+        assert np.allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+# ---------------------------------------------------------------------------
+# Whole scheme: accuracy
+# ---------------------------------------------------------------------------
+
+def _ns_rhs(dim, gamma, mu, Pr):
+    """Exact right-hand side -div(F^c - F^v) of Eq. (1) for a smooth field, by sympy
+    from Eqs. (1)-(3) (independent of the K matrices and of every discrete operator)."""
+    import sympy as sp
+    x, y = sp.symbols("x y")
+    kappa = gamma * mu / ((gamma - 1) * Pr)
+    if dim == 1:
+        rho = 1 + sp.Rational(1, 5) * sp.sin(x)
+        u = sp.Rational(1, 2) + sp.Rational(1, 5) * sp.cos(x + sp.Rational(3, 10))
+        p = 1 + sp.Rational(1, 5) * sp.cos(2 * x)
+        E = p / (gamma - 1) + rho * u ** 2 / 2
+        T = p / rho
+        tau = mu * sp.Rational(4, 3) * sp.diff(u, x)
+        q = -kappa * sp.diff(T, x)
+        F = [rho * u, rho * u ** 2 + p - tau, (E + p) * u - (u * tau - q)]
+        U = [rho, rho * u, E]
+        rhs = [-sp.diff(f, x) for f in F]
+        return [sp.lambdify(x, e, "numpy") for e in U], [sp.lambdify(x, e, "numpy") for e in rhs]
+    rho = 1 + sp.Rational(1, 5) * sp.sin(x) * sp.cos(y)
+    u = sp.Rational(1, 2) + sp.Rational(1, 5) * sp.sin(y + sp.Rational(3, 10)) * sp.cos(x)
+    v = -sp.Rational(3, 10) + sp.Rational(1, 5) * sp.cos(x - sp.Rational(1, 5) + y)
+    p = 1 + sp.Rational(1, 5) * sp.cos(x + 2 * y)
+    E = p / (gamma - 1) + rho * (u ** 2 + v ** 2) / 2
+    T = p / rho
+    ux, uy, vx, vy = sp.diff(u, x), sp.diff(u, y), sp.diff(v, x), sp.diff(v, y)
+    div = ux + vy
+    txx = mu * (2 * ux - sp.Rational(2, 3) * div)
+    tyy = mu * (2 * vy - sp.Rational(2, 3) * div)
+    txy = mu * (uy + vx)
+    qx, qy = -kappa * sp.diff(T, x), -kappa * sp.diff(T, y)
+    Fx = [rho * u, rho * u * u + p - txx, rho * u * v - txy, (E + p) * u - (u * txx + v * txy - qx)]
+    Fy = [rho * v, rho * u * v - txy, rho * v * v + p - tyy, (E + p) * v - (u * txy + v * tyy - qy)]
+    U = [rho, rho * u, rho * v, E]
+    rhs = [-sp.diff(a, x) - sp.diff(b, y) for a, b in zip(Fx, Fy)]
+    return [sp.lambdify((x, y), e, "numpy") for e in U], [sp.lambdify((x, y), e, "numpy") for e in rhs]
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("mu", [0.0, 0.05])
+def test_residual_consistent_with_navier_stokes(orc, dim, mu):
+    """The unlimited semi-discrete residual (Eq. (6) / Eq. (12)) converges to the
+    exact Navier-Stokes right-hand side: cell averages at fourth order. Point
+    residuals converge at third order for mu = 0 (the FVS term) and at second
+    order for mu > 0: D^2 of Eq. (9) also reads the reconstructed centre values,
+    whose O(dx^4) error it divides by dx^2 (the scheme damps that mode, so the
+    solution still converges at fourth order, see the self-convergence pin).
+    Catches any dropped term, wrong sign, wrong K entry or transposed operator."""
+    gamma, Pr = 1.4, 0.7
+    Uf, Rf = _ns_rhs(dim, gamma, mu, Pr)
+    L2 = 2 * np.pi
+    gx, gw = np.polynomial.legendre.leggauss(5)
+    gw = gw / 2
+    sizes = (16, 32, 64) if dim == 2 else (32, 64, 128, 256)
+    ec, ep = [], []
+    for n in sizes:
+        h = L2 / n
+        if dim == 1:
+            xc = (np.arange(n) + 0.5) * h
+            xf = np.arange(n + 1) * h
+            avg = np.array([sum(gw[q] * f(xc + 0.5 * h * gx[q]) for q in range(5)) for f in Uf])
+            pt = np.array([f(xf) for f in Uf])
+            s = np.concatenate([avg.ravel(), pt.ravel()])
+            ravg = np.array([sum(gw[q] * f(xc + 0.5 * h * gx[q]) for q in range(5)) for f in Rf])
+            rpt = np.array([f(xf) for f in Rf])
+            P = orc.problem(1, n, lo=(0.0,), hi=(L2,), gamma=gamma, mu=mu, Pr=Pr, limiter=0)
+            L = orc.residual(P, s, 1e-3)[0]
+            La, Lp = W.split_sites(L, 1, n)
+            ec.append(np.abs(La - ravg).max())
+            ep.append(np.abs(Lp - rpt).max())
+        else:
+            xc = (np.arange(n) + 0.5) * h
+            xf = np.arange(n + 1) * h
+
+            def cavg(f):
+                acc = 0.0
+                for qy in range(5):
+                    for qx in range(5):
+                        X, Y = np.meshgrid(xc + 0.5 * h * gx[qx], xc + 0.5 * h * gx[qy])
+                        acc = acc + gw[qx] * gw[qy] * f(X, Y)
+                return acc
+
+            def samp(f, xs, ys):
+                X, Y = np.meshgrid(xs, ys)
+                return np.broadcast_to(f(X, Y), X.shape)
+
+            s = np.concatenate([np.array([cavg(f) for f in Uf]).ravel()] +
+                               [np.array([samp(f, a, b) for f in Uf]).ravel()
+                                for a, b in ((xf, xc), (xc, xf), (xf, xf))])
+            P = orc.problem(2, n, n, lo=(0, 0), hi=(L2, L2), gamma=gamma, mu=mu, Pr=Pr, limiter=0)
+            L = orc.residual(P, s, 1e-3)[0]
+            sites = W.split_sites(L, 2, n, n)
+            ec.append(np.abs(sites[0] - np.array([cavg(f) for f in Rf])).max())
+            e = 0.0
+            for site, (a, b) in zip(sites[1:], ((xf, xc), (xc, xf), (xf, xf))):
+                e = max(e, np.abs(site - np.array([samp(f, a, b) for f in Rf])).max())
+            ep.append(e)
+    rc = np.log2(np.array(ec[:-1]) / np.array(ec[1:]))
+    rp = np.log2(np.array(ep[:-1]) / np.array(ep[1:]))
+    # (1D, mu = 0: the cell update differences exact point fluxes, so it is exact)
+    assert rc[-1] > 3.6 or ec[-1] < 1e-12, (ec, rc)
+    assert rp[-1] > (2.7 if mu == 0.0 else 1.8), (ep, rp)
+    assert ec[-1] < 1e-4 and ep[-1] < 1e-3
+
+
+@pytest.mark.parametrize("lim", [0, 2])
+def test_entropy_wave_fourth_order_1d(orc, lim):
+    """mu = 0: rho = 1 + 0.2 sin(x - t), u = 1, p = 1 solves the Euler equations
+    exactly; the full scheme (SSP-RK54 + CFL of Eq. (13)) converges at order 4."""
+    errs = []
+    for n in (16, 32, 64, 128):
+        w = W.entropy_wave_1d(n)
+        P = orc.problem(1, n, lo=w.lo, hi=w.hi, mu=0.0, limiter=lim)
+        s = w.state.copy()
+        rc, ns, nr = orc.advance(P, s, 0.0, 1.0)
+        assert rc == 0
+        ex = W.entropy_wave_1d(n, t=1.0).state
+        errs.append(np.abs(s - ex).mean())
+    r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert r[-1] > 3.8, (errs, r)
+
+
+def test_entropy_wave_fourth_order_2d(orc):
+    """2D exact Euler solution rho = 1 + 0.2 sin(x + y - 1.5 t), (u,v) = (1, 0.5)."""
+    errs = []
+    for n in (8, 16, 32):
+        w = W.entropy_wave_2d(n)
+        P = orc.problem(2, n, n, lo=w.lo, hi=w.hi, mu=0.0, limiter=2)
+        s = w.state.copy()
+        rc, ns, nr = orc.advance(P, s, 0.0, 0.5)
+        assert rc == 0
+        errs.append(np.abs(s - W.entropy_wave_2d(n, t=0.5).state).mean())
+    r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert r[-1] > 3.6, (errs, r)
+
+
+def test_viscous_self_convergence_1d(orc):
+    """Config 1 (mu = 0.01): fourth-order self-convergence of cell averages
+    (the 2-to-1 restriction of cell averages is exact)."""
+    sol = {}
+    for n in (32, 64, 128, 256):
+        w = W.smooth_1d(n, t_end=0.5)
+        P = orc.problem(1, n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, limiter=0)
+        s = w.state.copy()
+        assert orc.advance(P, s, 0.0, 0.5)[0] == 0
+        sol[n] = W.split_sites(s, 1, n)[0]
+    e = [np.abs(sol[n] - 0.5 * (sol[2 * n][:, 0::2] + sol[2 * n][:, 1::2])).mean() for n in (32, 64, 128)]
+    r = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert r[-1] > 3.6, (e, r)
+
+
+# ---------------------------------------------------------------------------
+# Positivity (Sec. 3, Prop. 3.2, Theorem 3.1) and restart (Remark 3.2)
+# ---------------------------------------------------------------------------
+
+def _pressure(sites, gamma, dim):
+    out = []
+    for U in sites:
+        m2 = sum(U[1 + k] ** 2 for k in range(dim))
+        out.append((gamma - 1) * (U[dim + 1] - 0.5 * m2 / U[0]))
+    return out
+
+
+def test_shock_tube_1d_positive_and_conservative(orc):
+    """Config 2 (coarse): densities and pressures stay positive at averages and
+    points. No acoustic wave reaches the ends by t = 0.2; only the thermal
+    precursor of the viscous shock touches the right end, so mass and energy
+    change by less than 1e-6 relative."""
+    n = 256
+    w = W.shock_tube_1d(n)
+    P = orc.problem(1, n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc)
+    s = w.state.copy()
+    m0 = W.split_sites(s, 1, n)[0].sum(axis=1)
+    rc, ns, nr = orc.advance(P, s, 0.0, 0.2)
+    assert rc == 0
+    sites = W.split_sites(s, 1, n)
+    for U, p in zip(sites, _pressure(sites, 1.4, 1)):
+        assert np.isfinite(U).all() and U[0].min() > 0 and p.min() > 0
+    m1 = sites[0].sum(axis=1)
+    assert abs(m1[0] - m0[0]) < 1e-6 * m0[0] and abs(m1[2] - m0[2]) < 1e-6 * m0[2]
+
+
+def test_near_vacuum_blast_positive_with_restarts(orc):
+    """Near-vacuum Gaussian blast (rho_min 1e-6, p_min 1e-8): positivity holds at
+    all DoFs and the halving restart of Remark 3.2 is exercised."""
+    w = W.blast_2d((20, 20), seed=0)
+    P = orc.problem(2, 20, 20, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc)
+    s = w.state.copy()
+    rc, ns, nr = orc.advance(P, s, 0.0, 1.0, max_steps=12)
+    assert rc == 0 and ns == 12 and nr > 0
+    sites = W.split_sites(s, 2, 20, 20)
+    for U, p in zip(sites, _pressure(sites, 1.4, 2)):
+        assert np.isfinite(U).all() and U[0].min() > 0 and p.min() > 0
+
+
+def test_limited_update_positive_prop_3_2(orc):
+    """Prop. 3.2: whenever no low-order state failed (notpp = 0), the limited cell
+    average update U + dt L stays in G, for rough random data and a range of dt."""
+    rng = np.random.default_rng(9)
+    n = (12, 10)
+    for trial in range(4):
+        rho = np.exp(rng.normal(0, 1.5, size=(n[1], n[0])))
+        p = np.exp(rng.normal(0, 2.0, size=(n[1], n[0])))
+        u = rng.normal(0, 2, size=(2, n[1], n[0]))
+        E = p / 0.4 + 0.5 * rho * (u ** 2).sum(axis=0)
+        avg = np.array([rho, rho * u[0], rho * u[1], E])
+        s = np.concatenate([avg.ravel()] + [np.broadcast_to(avg.mean(axis=(1, 2))[:, None, None], shp).ravel()
+                                            for shp in [(4, n[1], n[0] + 1), (4, n[1] + 1, n[0]),
+                                                        (4, n[1] + 1, n[0] + 1)]])
+        P = orc.problem(2, *n, lo=(0, 0), hi=(1, 1), mu=0.01)
+        dt0 = orc.dt_max(P, s)
+        for f in (0.05, 0.2, 0.5, 1.0):
+            L, bad = orc.residual(P, s, f * dt0)
+            if bad:
+                continue
+            new = W.split_sites(s + f * dt0 * L, 2, *n)[0]
+            assert new[0].min() > 0
+            assert _pressure([new], 1.4, 2)[0].min() > 0
+
+
+def test_walls_conserve_mass_and_hold_no_slip(orc):
+    """Config 4 (coarse, walled box): no mass flux through walls; wall point values
+    keep zero velocity (no-slip) and zero normal velocity (symmetry)."""
+    w = W.shock_tube_2d((24, 12))
+    P = orc.problem(2, 24, 12, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc)
+    s = w.state.copy()
+    m0 = W.split_sites(s, 2, 24, 12)[0][0].sum()
+    rc, ns, nr = orc.advance(P, s, 0.0, 0.02)
+    assert rc == 0 and ns >= 3
+    avg, xe, ye, vx = W.split_sites(s, 2, 24, 12)
+    assert abs(avg[0].sum() - m0) < 1e-13 * m0
+    assert np.all(xe[1:3, :, 0] == 0) and np.all(xe[1:3, :, -1] == 0)
+    assert np.all(ye[1:3, 0, :] == 0) and np.all(ye[2, -1, :] == 0)
+
+
+def test_smoothness_sensor_textbook_values(orc):
+    """Sec. 3.2 reduces to the Jameson-Schmidt-Turkel pressure switch
+    |p+ - 2p + p-| / (p+ + 2p + p-) times the Ducros compression switch (~1 for
+    pure compression, 0 for expansion): with C_s = 1, pressure (1, 1, 3) around a
+    compressed cell gives theta_s = exp(-1/3); (1, 3, 3) gives exp(-1/5); a face
+    whose two cells both expand is not limited."""
+    n = 8
+    dx = 1.0 / n
+    p = np.array([1, 1, 1, 3, 3, 3, 3, 3], float)
+    u = np.array([0, 0, 1, -1, 0, 0, 0, 0], float)
+    rho = np.ones(n)
+    avg = np.array([rho, rho * u, p / 0.4 + 0.5 * rho * u * u])
+    pt = np.array([np.ones(n + 1), np.zeros(n + 1), np.full(n + 1, 2.0 / 0.4)])
+    s = np.concatenate([avg.ravel(), pt.ravel()])
+    P = orc.problem(1, n, lo=(0.0,), hi=(1.0,), mu=0.0)
+    L, ts, tp, bad = orc.residual(P, s, 1e-9, with_theta=True)
+    assert ts[3] == pytest.approx(np.exp(-1.0 / 3.0), rel=1e-12)   # cells 2|3
+    assert ts[4] == pytest.approx(np.exp(-1.0 / 5.0), rel=1e-12)   # cells 3|4
+    assert ts[0] == 1.0 and ts[6] == 1.0                           # no compression
+    assert ts[2] == pytest.approx(np.exp(-1.0 / 3.0), rel=1e-12)   # cells 1|2: phi1(2)=1/3, phi2(2)=1
