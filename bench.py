@@ -1,0 +1,287 @@
+#!/usr/bin/env python
+"""Benchmark of the AF-NS Runge-Kutta step on one B300 (or N replicas).
+
+A "step" is one SSP-RK54 time step of the 2D smooth periodic Navier-Stokes
+workload (1024 x 1024 cells, 4 point sites + cell averages, mu = 0.01, Pr = 0.72):
+CFL reduction (Eq. (13)), five fused stage kernels (point residual, high- and
+low-order face fluxes, smoothness and positivity limiters, point scaling
+limiter, RK combination) with their ghost fills, and the restart-flag read
+(Remark 3.2). The metric is cell-stage updates per second:
+cells x 5 x steps / seconds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   (the CPU oracle, timed on a bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D cell-stage updates/s and HBM fraction, FP32-mixed vs FP64, at stated L1 error vs oracle"
+UNIT = "cell-stage updates/s"
+N_CELLS = 1024
+# FP64 peak of one B300 (TFLOP/s): the published dense FP64 rate of the part
+# (the FP64 pipe is 1/64 of the FP32 rate on sm_103); see the design doc for its derivation.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def clocks_start():
+    f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+    f.close()
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200",
+                              "-i", os.environ.get("LOCAL_RANK", "0"), "-f", f.name],
+                             stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+    except Exception:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(p, path):
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    if p is None:
+        return out
+    time.sleep(0.3)
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    try:
+        rows = [r.split(",") for r in open(path).read().strip().splitlines() if r.strip()]
+        os.unlink(path)
+    except Exception:
+        return out
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        r = [x.strip() for x in r]
+        try:
+            sm.append(float(r[1]))
+            mx.append(float(r[2]))
+        except Exception:
+            continue
+        for k, nm in enumerate(names):
+            if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                reasons.add(nm)
+    if sm:
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        out = {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+               "samples": len(sm)}
+    return out
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+        return dist, rank, ws
+    return None, 0, 1
+
+
+def reference_arm(args, rank, ws):
+    """The oracle as it stands, on the host cores: each timed step is one full
+    SSP-RK54 step of the same flow on a 128 x 128 sample of the grid."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2609_29081_b300 import workloads as W
+    n = 128
+    w = W.smooth_2d(n)
+    P = O.problem(2, n, n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, gamma=w.gamma)
+    s = w.state.copy()
+    for _ in range(args.warmup):
+        O.step(P, s, O.dt_max(P, s))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(P, s, O.dt_max(P, s))
+    sec = time.perf_counter() - t0
+    val = n * n * 5 * args.steps / sec
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "2D smooth periodic NS, [0,2pi)^2, mu=0.01, Pr=0.72, 8-mode perturbation",
+                       "grid": "%dx%d sample of 1024x1024" % (n, n), "limiter": "s+pp"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d SSP-RK54 steps on a %dx%d sample of the workload" % (args.steps, n, n)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, S, args):
+    """The oracle's residual of one stage at full size, timed on the host, and the
+    L1 distance of the GPU residual from it (bounded sample: one stage)."""
+    import oracle as O
+    P = O.problem(2, *w.n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, gamma=w.gamma)
+    dt = O.dt_max(P, w.state)
+    t0 = time.perf_counter()
+    Lr, _ = O.residual(P, w.state, dt)
+    sec = time.perf_counter() - t0
+    return Lr, dt, {"value": w.cells / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": "one limited stage residual L(u) of the full %dx%d workload (%.1f s)"
+                              % (w.n[0], w.n[1], sec)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libafns")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=N_CELLS)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    dist, rank, ws = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, rank, ws)
+        return
+
+    import torch
+    from paper_2609_29081_b300 import Solver, build, workloads as W
+    from paper_2609_29081_b300._native import FP64, MIXED
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = W.smooth_2d(args.n)
+    prec = FP64 if args.precision == "fp64" else MIXED
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = Solver.from_workload(w, precision=prec, stream=stream)
+        S.set_state(w.state)
+        for _ in range(args.warmup):
+            S.step(0.0)
+        torch.cuda.synchronize()
+        S.set_profiling(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        cp, cpath = clocks_start()
+        time.sleep(0.4)
+        ev0.record(stream)
+        restarts = 0
+        for _ in range(args.steps):
+            _, h = S.step(0.0)
+            restarts += h
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = clocks_stop(cp, cpath)
+        ms = ev0.elapsed_time(ev1)
+        prof = S.profile()
+        S.set_profiling(False)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        cells = w.cells
+        value = cells * 5 * args.steps * ws / (ms / 1e3)
+
+        # end to end through the public API with pinned host buffers
+        host_in = torch.from_numpy(S.get_state()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            S.set_state(host_in.numpy())
+            S.step(0.0)
+            S.get_state(host_out.numpy())
+        torch.cuda.synchronize()
+        e2e_sec = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_sec], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_sec = float(t.item())
+        e2e_val = cells * 5 * args.e2e_steps * ws / e2e_sec
+        state_bytes = host_in.numel() * 8
+
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    stage_ms = prof["stage_ms"] / max(prof["stage_launches"], 1)
+    # algorithmic work per launch (one stage over all cells), see the design doc
+    if args.precision == "fp64":
+        flops_per_cell = FLOPS_PER_CELL_STAGE
+        achieved = flops_per_cell * cells / (stage_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "k_stage2d<double>", "work_per_cell": flops_per_cell,
+                    "peak_source": "published FP64 rate of B300 (not in MEASURED_PEAKS.json)"}
+    else:
+        bpc = BYTES_PER_CELL_STAGE_MIXED
+        achieved = bpc * cells / (stage_ms / 1e3) / 1e9
+        pk = peaks.get("hbm_gbs", 6400.0)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                    "traffic": None, "kernel": "k_stage2d<float>", "work_per_cell": bpc,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "2D smooth periodic NS %dx%d (rho=1+0.2sin(x+y), (u,v)=(1,0.5)+8-mode "
+                                   "perturbation, p=1, mu=0.01, Pr=0.72), CFL steps, limiter s+pp"
+                                   % (args.n, args.n),
+                       "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (state %.0f MB per buffer, 5 buffers)" % (state_bytes / 1e6),
+                       "restarts": restarts},
+            "roofline": roofline, "clocks": clocks,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": prof["launches"],
+            "stage_ms": stage_ms}
+    if not args.no_cpu:
+        w0 = W.smooth_2d(args.n)
+        S.set_state(w0.state)
+        Lr, dt, cb = cpu_baseline(w0, S, args)
+        Lg, _ = S.residual(dt)
+        avg_r = W.split_sites(Lr, 2, *w0.n)[0]
+        avg_g = W.split_sites(Lg, 2, *w0.n)[0]
+        line["cpu_baseline"] = cb
+        line["l1_vs_oracle"] = {"what": "relative L1 distance of one stage residual of cell averages, GPU vs oracle",
+                                "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum())}
+    print(json.dumps(line), flush=True)
+
+
+# Algorithmic work of one 2D stage per cell (counted from the operation counts of
+# the stage): FP64 floating-point operations and, for the mixed
+# path, the minimum HBM bytes of the stage (3.2 state copies of 16 FP32 words plus
+# 4 compensation words per stage on average over the five SSP-RK54 stages).
+FLOPS_PER_CELL_STAGE = 3000
+BYTES_PER_CELL_STAGE_MIXED = 256
+
+
+if __name__ == "__main__":
+    main()

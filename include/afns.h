@@ -1,0 +1,162 @@
+/*
+ * afns.h -- C-ABI of libafns: the per-Runge-Kutta-stage update of the compact
+ * fourth-order positivity-preserving active flux (AF) method for the 1D/2D
+ * compressible Navier-Stokes equations on Cartesian grids (Duan, Barsukow,
+ * Klingenberg, arXiv 2609.29081), on one NVIDIA B300 GPU (sm_103a).
+ *
+ * The problem solved is Eq. (1) with the fluxes of Eq. (2), Newtonian stress and
+ * Fourier heat flux of Eq. (3), nondimensional temperature T = p/rho,
+ * kappa = gamma mu / ((gamma-1) Pr) and the ideal-gas law (Sec. 1). The degrees of
+ * freedom are cell averages plus shared point values (Sec. 2.1, Sec. 2.2).
+ *
+ * Conventions for every call:
+ *  - Every call returns af_status; nothing aborts, traps on the device or throws
+ *    across this boundary. On failure af_last_error() describes the cause.
+ *  - All device work is issued on the CUDA stream given to af_create (NULL = the
+ *    legacy default stream). Calls that return host data synchronise that stream.
+ *  - A context is not thread-safe; use one context per host thread.
+ *
+ * DoF layout of af_set_state / af_get_state ("site arrays", conservative
+ * variables, component-major, x index fastest, FP64):
+ *   2D: site[0] = avg [4][n2  ][n1  ]  cell averages U-bar_{ij}
+ *       site[1] = xe  [4][n2  ][n1+1]  x-edge points U_{i+1/2,j}
+ *       site[2] = ye  [4][n2+1][n1  ]  y-edge points U_{i,j+1/2}
+ *       site[3] = vx  [4][n2+1][n1+1]  vertex points U_{i+1/2,j+1/2}
+ *   1D: site[0] = avg [3][n1], site[1] = pt [3][n1+1]; site[2], site[3] unused.
+ *   Components: (rho, rho u, [rho v,] E). Face index i of xe/vx/pt lies at
+ *   x = lo[0] + i dx. On a periodic side the last face row/column duplicates
+ *   the first: af_set_state requires them equal, af_get_state writes them equal.
+ */
+#ifndef AFNS_H
+#define AFNS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afns_ctx afns_ctx; /* opaque */
+
+typedef enum {
+    AF_OK = 0,
+    AF_EINVAL = 1,  /* bad argument or inadmissible state (rho <= 0, p <= 0, NaN) */
+    AF_ENOMEM = 2,  /* device or host allocation failed / workspace too small */
+    AF_ECUDA = 3,   /* a CUDA call failed */
+    AF_ENOTPP = 4,  /* max_halvings exceeded in the restart of Remark 3.2 */
+    AF_ESTATE = 5   /* call out of order (e.g. step before set_state) */
+} af_status;
+
+typedef enum {
+    AF_BC_PERIODIC = 0,
+    AF_BC_WALL = 1,        /* no-slip adiabatic wall */
+    AF_BC_SYMMETRY = 2,    /* slip wall / symmetry plane */
+    AF_BC_TRANSMISSIVE = 3 /* zero-gradient outflow */
+} af_bc_kind;
+
+typedef enum { AF_FP64 = 0, AF_MIXED = 1 } af_precision;
+typedef enum { AF_LIM_NONE = 0, AF_LIM_PP = 1, AF_LIM_S_PP = 2 } af_limiter;
+
+typedef struct {
+    int dim;        /* 1 or 2 */
+    int n[2];       /* cells per direction (n[1] ignored in 1D); each >= 4 */
+    double lo[2];   /* domain [lo, hi] per direction */
+    double hi[2];
+} af_grid;
+
+typedef struct {
+    int side[4];    /* af_bc_kind of x-lo, x-hi, y-lo, y-hi; a periodic side needs a periodic partner */
+} af_bc;
+
+typedef struct {
+    int precision;     /* af_precision (AF_MIXED: FP32 stencils, FP64 positivity islands) */
+    int limiter;       /* af_limiter; AF_LIM_S_PP is the paper's scheme */
+    double c_s;        /* smoothness-limiter strength C_s (Sec. 3.2); paper: 1 */
+    double cfl_c;      /* inviscid CFL number C^c of Eq. (13); paper: 1.04/d */
+    double cfl_v;      /* viscous CFL number C^v of Eq. (13); paper: 0.33/d */
+    double eps;        /* positivity floor cap epsilon (Sec. 3.3); paper: 1e-13 */
+    int max_halvings;  /* restarts allowed per step (Remark 3.2); default 30 */
+    int tile_x;        /* 2D tile width in cells (0 = autotuned default) */
+    int tile_y;        /* 2D tile height in cells (0 = autotuned default) */
+} af_opts;
+
+/* Fill *o with the paper's defaults for a problem of dimension dim. */
+af_status af_opts_default(int dim, af_opts *o);
+
+/* Bytes of device workspace af_create needs for this grid and these options. */
+af_status af_workspace_bytes(const af_grid *grid, const af_opts *opts, size_t *bytes);
+
+/*
+ * Create a solver context.
+ *  grid, bc: problem geometry (Sec. 2.1 / Sec. 2.2); gamma > 1, mu >= 0, Pr > 0.
+ *  opts: NULL = af_opts_default(grid->dim).
+ *  cuda_stream: a cudaStream_t (or NULL) on which all work is issued.
+ *  workspace: device memory of at least af_workspace_bytes() bytes, 256-byte
+ *    aligned, owned by the caller and kept alive until af_destroy; NULL lets the
+ *    library allocate (and free) its own with cudaMalloc.
+ */
+af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, const af_bc *bc,
+                    const af_opts *opts, void *cuda_stream, void *workspace, size_t workspace_bytes,
+                    afns_ctx **out);
+af_status af_destroy(afns_ctx *ctx);
+
+/*
+ * Copy the DoFs in (layout above). on_device: 1 = the site pointers are device
+ * memory, 0 = host memory. The library copies; the caller keeps ownership.
+ * Validates that every DoF is finite with rho > 0 and p > 0 (Def. 3.1, the
+ * method starts from G) and that periodic duplicates match (AF_EINVAL otherwise).
+ */
+af_status af_set_state(afns_ctx *ctx, const double *const site[4], int on_device, double t);
+af_status af_get_state(afns_ctx *ctx, double *const site[4], int on_device, double *t);
+
+/* Largest stable step of Eq. (13) on the current cell averages. */
+af_status af_dt_max(afns_ctx *ctx, double *dt);
+
+/*
+ * One SSP-RK54 step (Sec. 2.3) of size dt; dt <= 0 takes the CFL step of
+ * Eq. (13). If a low-order state the limiters evaluate is not admissible, the
+ * step is recomputed from the start with dt/2 (Remark 3.2), at most
+ * max_halvings times (AF_ENOTPP, state left at the step's start).
+ * *dt_taken (may be NULL) receives the accepted step, *halvings the restarts.
+ */
+af_status af_step(afns_ctx *ctx, double dt, double *dt_taken, int *halvings);
+
+/* Advance to t_end with CFL steps (last step clipped); counts may be NULL. */
+af_status af_advance(afns_ctx *ctx, double t_end, int *steps, int *restarts);
+
+/*
+ * The limited semi-discrete residual L(u) of every DoF for a forward-Euler
+ * stage of size dt (dt enters the limiters through mu_l = dt/dx_l, Sec. 3), in
+ * the DoF layout above. This is one RK stage's right-hand side, exported for
+ * parity checks. *notpp (may be NULL) receives 1 when a low-order state was
+ * inadmissible.
+ */
+af_status af_residual(afns_ctx *ctx, double dt, double *const L[4], int on_device, int *notpp);
+
+/*
+ * Per-face limiter values of the last af_residual call: theta_s (Sec. 3.2) and
+ * theta^rho theta^p (Sec. 3.3). Layout: x-faces [n2][n1+1], then (2D) y-faces
+ * [n2+1][n1]. Host pointers; either may be NULL.
+ */
+af_status af_get_limiter(afns_ctx *ctx, double *theta_s, double *theta_pp);
+
+/* Number of cells n1*n2 and of faces (sizes of the arrays above). */
+af_status af_sizes(const afns_ctx *ctx, size_t *cells, size_t *faces, size_t *site_elems4);
+
+/*
+ * Profiling. af_set_profiling(ctx, 1) resets the counters and, from then on,
+ * brackets every fused stage-kernel launch with CUDA events on the context's
+ * stream; af_get_profile returns the summed stage-kernel time (ms, harvested at
+ * each step's restart-flag read), the number of stage-kernel launches and the
+ * number of all kernel launches issued by the library since the reset.
+ * Not part of the method (no counterpart in the paper).
+ */
+af_status af_set_profiling(afns_ctx *ctx, int on);
+af_status af_get_profile(afns_ctx *ctx, double *stage_ms, long long *stage_launches, long long *launches);
+
+const char *af_last_error(const afns_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

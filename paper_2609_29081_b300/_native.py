@@ -1,0 +1,225 @@
+"""ctypes binding of libafns (include/afns.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module allocates the
+device workspace through PyTorch, passes pointers and sizes, and converts
+between the packed state layout and the per-site pointers of the C-ABI.
+There is no CPU fallback: a missing library or GPU raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libafns.so")
+
+AF_OK, AF_EINVAL, AF_ENOMEM, AF_ECUDA, AF_ENOTPP, AF_ESTATE = range(6)
+FP64, MIXED = 0, 1
+LIM_NONE, LIM_PP, LIM_S_PP = 0, 1, 2
+
+EXPORTED = ["af_opts_default", "af_workspace_bytes", "af_create", "af_destroy", "af_set_state",
+            "af_get_state", "af_dt_max", "af_step", "af_advance", "af_residual", "af_get_limiter",
+            "af_sizes", "af_set_profiling", "af_get_profile", "af_last_error"]
+
+
+class AfnsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libafns status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 2), ("lo", ctypes.c_double * 2),
+                ("hi", ctypes.c_double * 2)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int * 4)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("limiter", ctypes.c_int), ("c_s", ctypes.c_double),
+                ("cfl_c", ctypes.c_double), ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libafns.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libafns.so is missing: build it with paper_2609_29081_b300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, dp, ip, sp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), \
+        ctypes.POINTER(ctypes.c_size_t)
+    P4 = ctypes.c_void_p * 4
+    L.af_opts_default.argtypes = [ctypes.c_int, ctypes.POINTER(Opts)]
+    L.af_workspace_bytes.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), sp]
+    L.af_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            ctypes.POINTER(BC), ctypes.POINTER(Opts), vp, vp, ctypes.c_size_t,
+                            ctypes.POINTER(vp)]
+    L.af_destroy.argtypes = [vp]
+    L.af_set_state.argtypes = [vp, P4, ctypes.c_int, ctypes.c_double]
+    L.af_get_state.argtypes = [vp, P4, ctypes.c_int, dp]
+    L.af_dt_max.argtypes = [vp, dp]
+    L.af_step.argtypes = [vp, ctypes.c_double, dp, ip]
+    L.af_advance.argtypes = [vp, ctypes.c_double, ip, ip]
+    L.af_residual.argtypes = [vp, ctypes.c_double, P4, ctypes.c_int, ip]
+    L.af_get_limiter.argtypes = [vp, vp, vp]
+    L.af_sizes.argtypes = [vp, sp, sp, sp]
+    L.af_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.af_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    L.af_last_error.argtypes = [vp]
+    L.af_last_error.restype = ctypes.c_char_p
+    for f in EXPORTED:
+        if f != "af_last_error":
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def default_opts(dim, precision=FP64, limiter=LIM_S_PP, **kw) -> Opts:
+    o = Opts()
+    load().af_opts_default(dim, ctypes.byref(o))
+    o.precision = precision
+    o.limiter = limiter
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One AF-NS problem on cuda:0 (device memory owned by a torch tensor)."""
+
+    def __init__(self, dim, n, lo, hi, gamma, mu, Pr, bc, precision=FP64, limiter=LIM_S_PP, stream=None,
+                 **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libafns needs a CUDA GPU; none is available")
+        self.torch = torch
+        self.lib = load()
+        self.dim = dim
+        self.n = (int(n[0]), int(n[1]) if dim == 2 else 1)
+        g = Grid()
+        g.dim = dim
+        g.n[0], g.n[1] = self.n
+        g.lo[0], g.hi[0] = lo[0], hi[0]
+        g.lo[1], g.hi[1] = (lo[1], hi[1]) if dim == 2 else (0.0, 1.0)
+        b = BC()
+        for k in range(4):
+            b.side[k] = bc[k] if k < len(bc) else 0
+        self.opts = default_opts(dim, precision, limiter, **opts)
+        nbytes = ctypes.c_size_t(0)
+        self._check(self.lib.af_workspace_bytes(ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(nbytes)))
+        self.ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+        base = self.ws.data_ptr()
+        base = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p()
+        st = self._check(self.lib.af_create(ctypes.byref(g), gamma, mu, Pr, ctypes.byref(b), ctypes.byref(self.opts),
+                                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(base),
+                                            nbytes.value, ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.shapes = workloads.site_shapes(dim, *self.n)
+        self.size = workloads.state_len(dim, *self.n)
+        cells, faces = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        self.lib.af_sizes(self.ctx, ctypes.byref(cells), ctypes.byref(faces), None)
+        self.faces = faces.value
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.dim, w.n, w.lo, w.hi, w.gamma, w.mu, w.Pr, w.bc, **kw)
+
+    def _check(self, st):
+        if st != AF_OK:
+            msg = self.lib.af_last_error(getattr(self, "ctx", None)) if getattr(self, "ctx", None) else b""
+            raise AfnsError(st, (msg or b"").decode())
+        return st
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.af_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- site pointer arrays of a packed buffer (numpy host array or torch tensor)
+    def _ptrs(self, buf):
+        P4 = ctypes.c_void_p * 4
+        p = P4()
+        if isinstance(buf, np.ndarray):
+            assert buf.dtype == np.float64 and buf.flags.c_contiguous and buf.size == self.size
+            base, on_dev = buf.ctypes.data, 0
+        else:
+            assert buf.dtype == self.torch.float64 and buf.is_contiguous() and buf.numel() == self.size
+            base, on_dev = buf.data_ptr(), int(buf.is_cuda)
+        o = 0
+        for k, shp in enumerate(self.shapes):
+            p[k] = base + 8 * o
+            o += int(np.prod(shp))
+        return p, on_dev
+
+    def set_state(self, state, t=0.0):
+        if isinstance(state, np.ndarray):
+            state = np.ascontiguousarray(state, dtype=np.float64)
+        p, dev = self._ptrs(state)
+        self._check(self.lib.af_set_state(self.ctx, p, dev, t))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.size, dtype=np.float64)
+        p, dev = self._ptrs(out)
+        t = ctypes.c_double(0)
+        self._check(self.lib.af_get_state(self.ctx, p, dev, ctypes.byref(t)))
+        self.t = t.value
+        return out
+
+    def dt_max(self):
+        d = ctypes.c_double(0)
+        self._check(self.lib.af_dt_max(self.ctx, ctypes.byref(d)))
+        return d.value
+
+    def step(self, dt=0.0):
+        d, h = ctypes.c_double(0), ctypes.c_int(0)
+        self._check(self.lib.af_step(self.ctx, dt, ctypes.byref(d), ctypes.byref(h)))
+        return d.value, h.value
+
+    def advance(self, t_end):
+        ns, nr = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.af_advance(self.ctx, t_end, ctypes.byref(ns), ctypes.byref(nr)))
+        return ns.value, nr.value
+
+    def residual(self, dt, out=None):
+        if out is None:
+            out = np.empty(self.size, dtype=np.float64)
+        p, dev = self._ptrs(out)
+        nb = ctypes.c_int(0)
+        self._check(self.lib.af_residual(self.ctx, dt, p, dev, ctypes.byref(nb)))
+        return out, nb.value
+
+    def limiter(self):
+        ts = np.empty(self.faces)
+        tp = np.empty(self.faces)
+        self._check(self.lib.af_get_limiter(self.ctx, ts.ctypes.data_as(ctypes.c_void_p),
+                                            tp.ctypes.data_as(ctypes.c_void_p)))
+        return ts, tp
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.af_set_profiling(self.ctx, int(on)))
+
+    def profile(self):
+        ms, ns, nl = ctypes.c_double(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
+        self._check(self.lib.af_get_profile(self.ctx, ctypes.byref(ms), ctypes.byref(ns), ctypes.byref(nl)))
+        return {"stage_ms": ms.value, "stage_launches": ns.value, "launches": nl.value}

@@ -1,0 +1,587 @@
+// afns.cu -- host driver and C-ABI of libafns (declared in include/afns.h).
+//
+// Owns the device workspace (or borrows the caller's), lays the state out as
+// padded structure-of-arrays planes with two ghost layers, and sequences the
+// kernels of one SSP-RK54 step: CFL reduction, then per stage a ghost fill and
+// one fused stage kernel, then a 4-byte read of the restart flag (Remark 3.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "afns.h"
+#include "stage2d.cuh"
+
+namespace afns {
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, cudaStream_t st);
+cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
+                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
+cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st);
+cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st);
+
+__global__ void k_set_ctl(Ctl *ctl, double dt, double t, double t_end)
+{
+    ctl->dt = dt;
+    ctl->t = t;
+    ctl->t_end = t_end;
+    ctl->notpp = 0;
+}
+__global__ void k_halve_ctl(Ctl *ctl)
+{
+    ctl->dt *= 0.5;
+    ctl->notpp = 0;
+}
+}  // namespace afns
+
+using namespace afns;
+
+// SSP-RK54, Spiteri-Ruuth SSPRK(5,4), Shu-Osher form (Sec. 2.3; the paper names
+// the method but does not print its coefficients).
+static const double kRK_a[5][5] = {
+    {1.0, 0, 0, 0, 0},
+    {0.444370493651235, 0.555629506348765, 0, 0, 0},
+    {0.620101851488403, 0, 0.379898148511597, 0, 0},
+    {0.178079954393132, 0, 0, 0.821920045606868, 0},
+    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269},
+};
+static const double kRK_b[5] = {0.391752226571890, 0.368410593050371, 0.251891774271694, 0.544974750228521,
+                                0.226007483236906};
+static const double kRK_b43 = 0.063692468666290;
+
+struct afns_ctx {
+    int dim = 2;
+    int n1 = 0, n2 = 1;
+    double lo[2] = {0, 0}, hi[2] = {1, 1};
+    double gamma = 1.4, mu = 0, Pr = 1, kappa = 0;
+    int bc[4] = {0, 0, 0, 0};
+    af_opts opts{};
+    cudaStream_t st = nullptr;
+    Layout L{};
+    size_t state_bytes = 0;
+    char *ws = nullptr;
+    bool own_ws = false;
+    void *U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // u^n, u1/u3/u5, u2/acc, u4, residual
+    Ctl *ctl = nullptr;
+    Ctl *h_ctl = nullptr;   // pinned mirror
+    double *partial = nullptr;
+    int nparts = 0;
+    double *theta = nullptr;
+    int *flag = nullptr;
+    int *h_flag = nullptr;
+    size_t nfaces = 0;
+    // profiling: CUDA events around every stage-kernel launch, launch counters
+    int profiling = 0;
+    cudaEvent_t ev[5][2] = {};
+    int ev_used = 0;
+    double stage_ms = 0;
+    long long stage_launches = 0;
+    long long launches = 0;
+    double t = 0;
+    bool has_state = false;
+    std::string err;
+};
+
+static af_status fail(afns_ctx *c, af_status s, const std::string &m)
+{
+    if (c) c->err = m;
+    return s;
+}
+
+static af_status cuda_check(afns_ctx *c, cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return AF_OK;
+    return fail(c, AF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void make_layout(const af_grid *g, const int *bc, Layout *L)
+{
+    std::memset(L, 0, sizeof(*L));
+    L->dim = g->dim;
+    L->nc = g->dim + 2;
+    L->n1 = g->n[0];
+    L->n2 = g->dim == 2 ? g->n[1] : 1;
+    L->nsite = g->dim == 2 ? 4 : 2;
+    L->pitch = ((L->n1 + 5) + 31) / 32 * 32;
+    L->rows = g->dim == 2 ? L->n2 + 5 : 1;
+    long long pl = (long long)L->pitch * L->rows;
+    L->plane = (pl + 63) / 64 * 64;
+    for (int k = 0; k < 4; ++k) L->bc[k] = bc[k];
+    L->dx = (g->hi[0] - g->lo[0]) / g->n[0];
+    L->dy = g->dim == 2 ? (g->hi[1] - g->lo[1]) / g->n[1] : 1.0;
+}
+
+struct WsPlan {
+    size_t state, ctl, partial, theta, flag, total;
+    int nparts;
+    size_t nfaces;
+};
+
+static WsPlan plan_ws(const Layout &L, const af_opts *o)
+{
+    WsPlan p{};
+    size_t esz = o->precision == AF_MIXED ? sizeof(float) : sizeof(double);
+    size_t planes = (size_t)L.nsite * L.nc + (o->precision == AF_MIXED ? L.nc : 0);
+    p.state = align256(planes * (size_t)L.plane * esz);
+    p.ctl = align256(sizeof(Ctl));
+    p.nparts = 148 * 4;
+    p.partial = align256(sizeof(double) * 2 * p.nparts);
+    p.nfaces = L.dim == 2 ? (size_t)(L.n1 + 1) * L.n2 + (size_t)L.n1 * (L.n2 + 1) : (size_t)L.n1 + 1;
+    p.theta = align256(sizeof(double) * 2 * p.nfaces);
+    p.flag = align256(sizeof(int) * 4);
+    p.total = 5 * p.state + p.ctl + p.partial + p.theta + p.flag;
+    return p;
+}
+
+static af_status check_args(const af_grid *g, double gamma, double mu, double Pr, const af_bc *bc, const af_opts *o,
+                            std::string *why)
+{
+    if (!g || !bc) return *why = "grid and bc are required", AF_EINVAL;
+    if (g->dim != 1 && g->dim != 2) return *why = "dim must be 1 or 2", AF_EINVAL;
+    for (int l = 0; l < g->dim; ++l) {
+        if (g->n[l] < 4) return *why = "need at least 4 cells per direction", AF_EINVAL;
+        if (!(g->hi[l] > g->lo[l])) return *why = "need hi > lo", AF_EINVAL;
+    }
+    if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return *why = "need gamma > 1, mu >= 0, Pr > 0", AF_EINVAL;
+    for (int l = 0; l < g->dim; ++l) {
+        int a = bc->side[2 * l], b = bc->side[2 * l + 1];
+        if (a < 0 || a > 3 || b < 0 || b > 3) return *why = "unknown boundary kind", AF_EINVAL;
+        if ((a == AF_BC_PERIODIC) != (b == AF_BC_PERIODIC)) return *why = "periodic sides come in pairs", AF_EINVAL;
+    }
+    if (o->precision != AF_FP64 && o->precision != AF_MIXED) return *why = "unknown precision", AF_EINVAL;
+    if (o->limiter < 0 || o->limiter > 2) return *why = "unknown limiter", AF_EINVAL;
+    if (!(o->cfl_c > 0) || !(o->cfl_v > 0) || !(o->eps > 0) || o->max_halvings < 0)
+        return *why = "bad CFL numbers, eps or max_halvings", AF_EINVAL;
+    if (g->dim == 1) return *why = "the 1D path is not available in this build", AF_EINVAL;
+    if (o->precision == AF_MIXED) return *why = "the mixed-precision path is not available in this build", AF_EINVAL;
+    return AF_OK;
+}
+
+extern "C" {
+
+af_status af_opts_default(int dim, af_opts *o)
+{
+    if (!o || (dim != 1 && dim != 2)) return AF_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = AF_FP64;
+    o->limiter = AF_LIM_S_PP;
+    o->c_s = 1.0;
+    o->cfl_c = 1.04 / dim;
+    o->cfl_v = 0.33 / dim;
+    o->eps = 1e-13;
+    o->max_halvings = 30;
+    return AF_OK;
+}
+
+af_status af_workspace_bytes(const af_grid *grid, const af_opts *opts, size_t *bytes)
+{
+    if (!grid || !bytes) return AF_EINVAL;
+    af_opts d;
+    if (!opts) {
+        if (af_opts_default(grid->dim, &d) != AF_OK) return AF_EINVAL;
+        opts = &d;
+    }
+    int bc[4] = {0, 0, 0, 0};
+    Layout L;
+    make_layout(grid, bc, &L);
+    *bytes = plan_ws(L, opts).total;
+    return AF_OK;
+}
+
+af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, const af_bc *bc, const af_opts *opts,
+                    void *cuda_stream, void *workspace, size_t workspace_bytes, afns_ctx **out)
+{
+    if (!out) return AF_EINVAL;
+    *out = nullptr;
+    af_opts d;
+    if (!opts) {
+        if (!grid || af_opts_default(grid->dim, &d) != AF_OK) return AF_EINVAL;
+        opts = &d;
+    }
+    std::string why;
+    af_status s = check_args(grid, gamma, mu, Pr, bc, opts, &why);
+    if (s != AF_OK) {
+        std::fprintf(stderr, "af_create: %s\n", why.c_str());
+        return s;
+    }
+    afns_ctx *c = new (std::nothrow) afns_ctx();
+    if (!c) return AF_ENOMEM;
+    c->dim = grid->dim;
+    c->n1 = grid->n[0];
+    c->n2 = grid->dim == 2 ? grid->n[1] : 1;
+    for (int l = 0; l < 2; ++l) c->lo[l] = grid->lo[l], c->hi[l] = grid->hi[l];
+    c->gamma = gamma;
+    c->mu = mu;
+    c->Pr = Pr;
+    c->kappa = gamma * mu / ((gamma - 1.0) * Pr);
+    for (int k = 0; k < 4; ++k) c->bc[k] = grid->dim == 2 || k < 2 ? bc->side[k] : AF_BC_PERIODIC;
+    c->opts = *opts;
+    c->st = (cudaStream_t)cuda_stream;
+    make_layout(grid, c->bc, &c->L);
+    WsPlan p = plan_ws(c->L, opts);
+    if (workspace) {
+        if (workspace_bytes < p.total || ((uintptr_t)workspace & 255)) {
+            delete c;
+            return AF_ENOMEM;
+        }
+        c->ws = (char *)workspace;
+    } else {
+        if (cudaMalloc((void **)&c->ws, p.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return AF_ENOMEM;
+        }
+        c->own_ws = true;
+    }
+    char *q = c->ws;
+    c->state_bytes = p.state;
+    for (int k = 0; k < 5; ++k) c->U[k] = q, q += p.state;
+    c->ctl = (Ctl *)q;
+    q += p.ctl;
+    c->partial = (double *)q;
+    q += p.partial;
+    c->nparts = p.nparts;
+    c->theta = (double *)q;
+    q += p.theta;
+    c->flag = (int *)q;
+    c->nfaces = p.nfaces;
+    if (cudaMallocHost((void **)&c->h_ctl, sizeof(Ctl) + 16) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->own_ws) cudaFree(c->ws);
+        delete c;
+        return AF_ENOMEM;
+    }
+    c->h_flag = (int *)(c->h_ctl + 1);
+    // NaN-free workspace: ghost rows of unused padding are never read, but zero it once
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, p.total, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "af_create: %s\n", cudaGetErrorString(e));
+        af_destroy(c);
+        return AF_ECUDA;
+    }
+    *out = c;
+    return AF_OK;
+}
+
+af_status af_destroy(afns_ctx *c)
+{
+    if (!c) return AF_EINVAL;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    for (int k = 0; k < 5; ++k)
+        for (int q = 0; q < 2; ++q)
+            if (c->ev[k][q]) cudaEventDestroy(c->ev[k][q]);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    delete c;
+    return AF_OK;
+}
+
+const char *af_last_error(const afns_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+af_status af_sizes(const afns_ctx *c, size_t *cells, size_t *faces, size_t *site_elems4)
+{
+    if (!c) return AF_EINVAL;
+    if (cells) *cells = (size_t)c->n1 * c->n2;
+    if (faces) *faces = c->nfaces;
+    if (site_elems4) {
+        if (c->dim == 2) {
+            site_elems4[0] = (size_t)4 * c->n1 * c->n2;
+            site_elems4[1] = (size_t)4 * (c->n1 + 1) * c->n2;
+            site_elems4[2] = (size_t)4 * c->n1 * (c->n2 + 1);
+            site_elems4[3] = (size_t)4 * (c->n1 + 1) * (c->n2 + 1);
+        } else {
+            site_elems4[0] = (size_t)3 * c->n1;
+            site_elems4[1] = (size_t)3 * (c->n1 + 1);
+            site_elems4[2] = site_elems4[3] = 0;
+        }
+    }
+    return AF_OK;
+}
+
+}  // extern "C"
+
+// Width/height of site s (2D).
+static void site_dims(const afns_ctx *c, int s, int *w, int *h)
+{
+    *w = (s == 1 || s == 3) ? c->n1 + 1 : c->n1;
+    *h = (s == 2 || s == 3) ? c->n2 + 1 : c->n2;
+}
+
+// Copy between the public site arrays and a padded state buffer (dir 0: in, 1: out).
+static af_status copy_sites(afns_ctx *c, void *buf, double *const site[4], int on_device, int dir)
+{
+    for (int s = 0; s < c->L.nsite; ++s) {
+        if (!site[s]) return fail(c, AF_EINVAL, "null site pointer");
+        int w, h;
+        site_dims(c, s, &w, &h);
+        for (int comp = 0; comp < c->L.nc; ++comp) {
+            double *dev = (double *)buf + plane_of(c->L, s, comp) + cell_off(c->L, 0, 0);
+            double *host = site[s] + (size_t)comp * w * h;
+            cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+            cudaError_t e = dir == 0 ? cudaMemcpy2DAsync(dev, c->L.pitch * sizeof(double), host, w * sizeof(double),
+                                                        w * sizeof(double), h, k, c->st)
+                                     : cudaMemcpy2DAsync(host, w * sizeof(double), dev, c->L.pitch * sizeof(double),
+                                                         w * sizeof(double), h, k, c->st);
+            if (e != cudaSuccess) return cuda_check(c, e, "state copy");
+        }
+    }
+    return AF_OK;
+}
+
+extern "C" af_status af_set_state(afns_ctx *c, const double *const site[4], int on_device, double t)
+{
+    if (!c || !site) return fail(c, AF_EINVAL, "null argument");
+    af_status s = copy_sites(c, c->U[0], const_cast<double *const *>(site), on_device, 0);
+    if (s != AF_OK) return s;
+    cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
+    if (e == cudaSuccess) e = launch_validate2d_fp64(c->L, (const double *)c->U[0], c->gamma, c->flag, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "af_set_state");
+    if (*c->h_flag & 1) return fail(c, AF_EINVAL, "state has a DoF outside G (rho <= 0, p <= 0 or not finite)");
+    if (*c->h_flag & 2) return fail(c, AF_EINVAL, "periodic duplicate point values differ from their partners");
+    c->t = t;
+    c->has_state = true;
+    return AF_OK;
+}
+
+extern "C" af_status af_get_state(afns_ctx *c, double *const site[4], int on_device, double *t)
+{
+    if (!c || !site) return fail(c, AF_EINVAL, "null argument");
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    cudaError_t e = launch_ghost2d_fp64(c->L, (double *)c->U[0], c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "ghost fill");
+    af_status s = copy_sites(c, c->U[0], site, on_device, 1);
+    if (s != AF_OK) return s;
+    e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "af_get_state");
+    if (t) *t = c->t;
+    return AF_OK;
+}
+
+static StageArgs base_args(afns_ctx *c)
+{
+    StageArgs A{};
+    A.L = c->L;
+    A.ctl = c->ctl;
+    A.gamma = c->gamma;
+    A.mu = c->mu;
+    A.kappa = c->kappa;
+    A.eps = c->opts.eps;
+    A.c_s = c->opts.c_s;
+    A.limiter = c->opts.limiter;
+    return A;
+}
+
+// One fused stage: ghost fill of the input, then the stage kernel.
+static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &k, double *theta)
+{
+    cudaError_t e = launch_ghost2d_fp64(c->L, (double *)in, c->st);
+    if (e != cudaSuccess) return e;
+    c->launches += 2;
+    StageArgs A = base_args(c);
+    A.uin = in;
+    A.u0 = c->U[0];
+    A.aux = c->U[2];
+    A.out = out;
+    A.theta = theta;
+    A.k = k;
+    bool prof = c->profiling && c->ev_used < 5;
+    if (prof) cudaEventRecord(c->ev[c->ev_used][0], c->st);
+    e = launch_stage2d_fp64(A, c->opts.tile_x, c->opts.tile_y, c->st);
+    if (prof) cudaEventRecord(c->ev[c->ev_used++][1], c->st);
+    c->launches += 1;
+    c->stage_launches += 1;
+    return e;
+}
+
+// Accumulate the stage-kernel event times of the work issued so far (the stream
+// has been synchronised by the caller).
+static void harvest_events(afns_ctx *c)
+{
+    for (int k = 0; k < c->ev_used; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[k][0], c->ev[k][1]) == cudaSuccess) c->stage_ms += ms;
+    }
+    c->ev_used = 0;
+}
+
+// The five SSP-RK54 stages from U[0]; the result lands in U[1].
+static cudaError_t run_rk(afns_ctx *c)
+{
+    bool walls = false;
+    for (int k = 0; k < 4; ++k) walls |= c->bc[k] == AF_BC_WALL || c->bc[k] == AF_BC_SYMMETRY;
+    StageCoef k{};
+    k.wall_fix = walls;
+    cudaError_t e;
+    // u1 = u0 + b0 dt L(u0)
+    k.a0 = 0; k.a1 = 1; k.a2 = 0; k.cl = kRK_b[0];
+    if ((e = run_stage(c, c->U[0], c->U[1], k, nullptr)) != cudaSuccess) return e;
+    // u2 = a10 u0 + a11 u1 + b1 dt L(u1)
+    k.a0 = kRK_a[1][0]; k.a1 = kRK_a[1][1]; k.cl = kRK_b[1];
+    if ((e = run_stage(c, c->U[1], c->U[2], k, nullptr)) != cudaSuccess) return e;
+    // u3 = a20 u0 + a22 u2 + b2 dt L(u2)
+    k.a0 = kRK_a[2][0]; k.a1 = kRK_a[2][2]; k.cl = kRK_b[2];
+    if ((e = run_stage(c, c->U[2], c->U[1], k, nullptr)) != cudaSuccess) return e;
+    // u4 = a30 u0 + a33 u3 + b3 dt L(u3); acc = a42 u2 + a43 u3 + b43 dt L(u3)
+    k.a0 = kRK_a[3][0]; k.a1 = kRK_a[3][3]; k.cl = kRK_b[3];
+    k.acc = 1; k.b2 = kRK_a[4][2]; k.b1 = kRK_a[4][3]; k.bl = kRK_b43;
+    if ((e = run_stage(c, c->U[1], c->U[3], k, nullptr)) != cudaSuccess) return e;
+    // u5 = acc + a44 u4 + b4 dt L(u4)
+    k.acc = 0; k.a0 = 0; k.a2 = 1; k.a1 = kRK_a[4][4]; k.cl = kRK_b[4];
+    return run_stage(c, c->U[3], c->U[1], k, nullptr);
+}
+
+static af_status read_ctl(afns_ctx *c)
+{
+    cudaError_t e = cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess && c->profiling) harvest_events(c);
+    return cuda_check(c, e, "control read");
+}
+
+// Step with the dt already in ctl; restarts with dt/2 on a non-PP low-order state.
+static af_status step_from_ctl(afns_ctx *c, double *dt_taken, int *halvings)
+{
+    int h = 0;
+    for (;;) {
+        cudaError_t e = run_rk(c);
+        if (e != cudaSuccess) return cuda_check(c, e, "stage");
+        af_status s = read_ctl(c);
+        if (s != AF_OK) return s;
+        if (!c->h_ctl->notpp) break;
+        if (h >= c->opts.max_halvings) {
+            if (halvings) *halvings = h;
+            return fail(c, AF_ENOTPP, "low-order states not admissible after max_halvings restarts");
+        }
+        ++h;
+        k_halve_ctl<<<1, 1, 0, c->st>>>(c->ctl);
+        c->launches += 1;
+    }
+    std::swap(c->U[0], c->U[1]);
+    c->t += c->h_ctl->dt;
+    if (dt_taken) *dt_taken = c->h_ctl->dt;
+    if (halvings) *halvings = h;
+    return AF_OK;
+}
+
+static cudaError_t launch_dt(afns_ctx *c, int clip)
+{
+    c->launches += 2;
+    return launch_dt2d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+                            c->partial, c->nparts, c->ctl, clip, c->st);
+}
+
+extern "C" af_status af_dt_max(afns_ctx *c, double *dt)
+{
+    if (!c || !dt) return fail(c, AF_EINVAL, "null argument");
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, c->t);
+    cudaError_t e = launch_dt(c, 0);
+    if (e != cudaSuccess) return cuda_check(c, e, "dt");
+    af_status s = read_ctl(c);
+    if (s != AF_OK) return s;
+    *dt = c->h_ctl->dt_cfl;
+    return AF_OK;
+}
+
+extern "C" af_status af_step(afns_ctx *c, double dt, double *dt_taken, int *halvings)
+{
+    if (!c) return AF_EINVAL;
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    c->launches += 1;
+    if (dt > 0) {
+        k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, dt, c->t, c->t);
+    } else {
+        k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, c->t);
+        cudaError_t e = launch_dt(c, 0);
+        if (e != cudaSuccess) return cuda_check(c, e, "dt");
+    }
+    return step_from_ctl(c, dt_taken, halvings);
+}
+
+extern "C" af_status af_advance(afns_ctx *c, double t_end, int *steps, int *restarts)
+{
+    if (!c) return AF_EINVAL;
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    int ns = 0, nr = 0;
+    af_status s = AF_OK;
+    while (c->t < t_end) {
+        k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, t_end);
+        c->launches += 1;
+        cudaError_t e = launch_dt(c, 1);
+        if (e != cudaSuccess) {
+            s = cuda_check(c, e, "dt");
+            break;
+        }
+        int h = 0;
+        s = step_from_ctl(c, nullptr, &h);
+        nr += h;
+        if (s != AF_OK) break;
+        ++ns;
+    }
+    if (steps) *steps = ns;
+    if (restarts) *restarts = nr;
+    return s;
+}
+
+extern "C" af_status af_residual(afns_ctx *c, double dt, double *const Lout[4], int on_device, int *notpp)
+{
+    if (!c || !Lout) return fail(c, AF_EINVAL, "null argument");
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, dt, c->t, c->t);
+    StageCoef k{};
+    k.residual = 1;
+    cudaError_t e = run_stage(c, c->U[0], c->U[4], k, c->theta);
+    if (e == cudaSuccess) e = launch_ghost2d_fp64(c->L, (double *)c->U[4], c->st);   // periodic duplicates
+    if (e != cudaSuccess) return cuda_check(c, e, "residual");
+    af_status s = copy_sites(c, c->U[4], Lout, on_device, 1);
+    if (s != AF_OK) return s;
+    s = read_ctl(c);
+    if (s != AF_OK) return s;
+    if (notpp) *notpp = c->h_ctl->notpp;
+    return AF_OK;
+}
+
+extern "C" af_status af_get_limiter(afns_ctx *c, double *theta_s, double *theta_pp)
+{
+    if (!c) return AF_EINVAL;
+    cudaError_t e = cudaSuccess;
+    if (theta_s) e = cudaMemcpyAsync(theta_s, c->theta, c->nfaces * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && theta_pp)
+        e = cudaMemcpyAsync(theta_pp, c->theta + c->nfaces, c->nfaces * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    return cuda_check(c, e, "af_get_limiter");
+}
+
+extern "C" af_status af_set_profiling(afns_ctx *c, int on)
+{
+    if (!c) return AF_EINVAL;
+    if (on && !c->ev[0][0]) {
+        for (int k = 0; k < 5; ++k)
+            for (int q = 0; q < 2; ++q)
+                if (cudaEventCreate(&c->ev[k][q]) != cudaSuccess) return cuda_check(c, cudaGetLastError(), "event");
+    }
+    c->profiling = on ? 1 : 0;
+    c->ev_used = 0;
+    c->stage_ms = 0;
+    c->stage_launches = 0;
+    c->launches = 0;
+    return AF_OK;
+}
+
+extern "C" af_status af_get_profile(afns_ctx *c, double *stage_ms, long long *stage_launches, long long *launches)
+{
+    if (!c) return AF_EINVAL;
+    if (stage_ms) *stage_ms = c->stage_ms;
+    if (stage_launches) *stage_launches = c->stage_launches;
+    if (launches) *launches = c->launches;
+    return AF_OK;
+}

@@ -1,0 +1,130 @@
+// afns_dev.cuh -- device-side layout, physics and stencil helpers of libafns.
+//
+// State layout in HBM (one "state buffer"): structure of arrays, one plane per
+// (DoF site, conservative component). 2D sites: 0 = cell average, 1 = x-edge
+// point, 2 = y-edge point, 3 = vertex point; 1D sites: 0 = cell average,
+// 1 = interface point. Every plane covers indices i in [-2, n1+2],
+// j in [-2, n2+2] (two ghost layers), element (i, j) at (j+2)*pitch + (i+2).
+// The mixed-precision form adds one FP32 compensation plane per cell-average
+// component (the average is hi + lo).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace afns {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_SYMMETRY = 2, BC_TRANSMISSIVE = 3 };
+enum { LIM_NONE = 0, LIM_PP = 1, LIM_S_PP = 2 };
+
+struct Layout {
+    int dim;        // 1 or 2
+    int nc;         // components: dim + 2
+    int n1, n2;     // cells (n2 = 1 in 1D)
+    int pitch;      // elements per row
+    int rows;       // rows per plane
+    long long plane;  // elements per plane (multiple of 64)
+    int nsite;      // 4 in 2D, 2 in 1D
+    int comp;       // compensation planes present (mixed precision)
+    int bc[4];
+    double dx, dy;
+};
+
+// Plane index of (site, component); compensation plane of cell-average comp c.
+__host__ __device__ __forceinline__ long long plane_of(const Layout &L, int site, int c)
+{
+    return (long long)(site * L.nc + c) * L.plane;
+}
+__host__ __device__ __forceinline__ long long comp_plane(const Layout &L, int c)
+{
+    return (long long)(L.nsite * L.nc + c) * L.plane;
+}
+__host__ __device__ __forceinline__ long long cell_off(const Layout &L, int i, int j)
+{
+    return (long long)(j + 2) * L.pitch + (i + 2);
+}
+
+// Gas constants in the compute precision.
+template <class R>
+struct Gas {
+    R gamma, gm1, mu, kappa, eps;
+};
+
+// Control block in device memory shared by the kernels of one step.
+struct Ctl {
+    double dt;        // step size used by the stage kernels
+    double t;         // current time
+    double t_end;     // clip target of the CFL step (<= t: no clip)
+    double dt_cfl;    // last CFL bound
+    int notpp;        // a low-order state the limiters evaluate left G
+    int pad;
+};
+
+// SSP-RK54 stage combination: out = a0 u0 + a1 uin + a2 aux + cl dt L(uin);
+// with acc: aux <- b2 aux + b1 uin + bl dt L(uin). Residual mode writes L itself.
+struct StageCoef {
+    double a0, a1, a2, cl;
+    double b1, b2, bl;
+    int acc;
+    int residual;
+    int wall_fix;
+};
+
+// --- ghost index images (two ghost layers; walls mirror about the boundary node,
+// periodic wraps). "pt" = point-like along the direction (index i <-> lattice 2i),
+// otherwise cell-like (index i <-> lattice 2i+1).
+__host__ __device__ __forceinline__ int ghost_image(int i, int n, bool pt, int kind_lo, int kind_hi, int *side)
+{
+    // returns the interior index; *side = 0 (lo), 1 (hi), or -1 (not a ghost)
+    if (pt) {
+        if (i < 0) {
+            *side = 0;
+            return kind_lo == BC_PERIODIC ? i + n : -i;
+        }
+        if (i > n || (i == n && kind_hi == BC_PERIODIC)) {
+            *side = 1;
+            return kind_hi == BC_PERIODIC ? i - n : 2 * n - i;
+        }
+    } else {
+        if (i < 0) {
+            *side = 0;
+            return kind_lo == BC_PERIODIC ? i + n : -i - 1;
+        }
+        if (i >= n) {
+            *side = 1;
+            return kind_hi == BC_PERIODIC ? i - n : 2 * n - 1 - i;
+        }
+    }
+    *side = -1;
+    return i;
+}
+
+// Momentum sign of component c (1..dim) under the mirror of a side of kind `kind`
+// normal to direction l.
+__host__ __device__ __forceinline__ double mirror_sign(int kind, int l, int c, int dim)
+{
+    if (c < 1 || c > dim) return 1.0;
+    if (kind == BC_WALL) return -1.0;
+    if (kind == BC_SYMMETRY && c - 1 == l) return -1.0;
+    return 1.0;
+}
+
+// Theta of Sec. 3.3 (limiter blending toward the low-order value).
+template <class R>
+__device__ __forceinline__ R theta_fn(R zL, R zH, R eps)
+{
+    return zH < eps ? (zL - eps) / (zL - zH) : R(1);
+}
+
+template <class R>
+__device__ __forceinline__ R dmax(R a, R b)
+{
+    return b > a ? b : a;   // a NaN in b is ignored
+}
+template <class R>
+__device__ __forceinline__ R dmin(R a, R b)
+{
+    return a < b ? a : b;
+}
+
+}  // namespace afns

@@ -1,0 +1,65 @@
+// stage2d.cu -- host-side launchers of the 2D kernels (stage2d_kernels.cuh).
+#include <algorithm>
+
+#include "stage2d_kernels.cuh"
+
+namespace afns {
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (called from the C-ABI driver)
+// ---------------------------------------------------------------------------
+template <class S>
+cudaError_t launch_ghost2d(const Layout &L, S *buf, cudaStream_t st)
+{
+    for (int pass = 0; pass < 2; ++pass) {
+        int span = pass == 0 ? (L.n2 + 1) : (L.n1 + 5);
+        int total = 4 * span * 5;
+        int blocks = (total + 255) / 256;
+        k_ghost2d<S><<<blocks, 256, 0, st>>>(L, buf, pass);
+    }
+    return cudaGetLastError();
+}
+
+template <class R, class S, int TX, int TY>
+cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st)
+{
+    using T = Tile2<TX, TY>;
+    size_t smem = sizeof(R) * (size_t)T::total;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_stage2d<R, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((A.L.n1 + TX - 1) / TX, (A.L.n2 + TY - 1) / TY);
+    k_stage2d<R, S, TX, TY><<<grid, 256, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, cudaStream_t st)
+{
+    (void)tx;
+    (void)ty;
+    return launch_stage2d_t<double, double, 16, 8>(A, st);
+}
+
+cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
+                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st)
+{
+    k_dt_partial2d<double><<<nparts, 256, 0, st>>>(L, buf, gamma, mu, Pr, cfl_c, cfl_v, partial);
+    k_dt_final<<<1, 256, 0, st>>>(partial, nparts, ctl, clip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st) { return launch_ghost2d<double>(L, buf, st); }
+
+cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st)
+{
+    long long total = (long long)(L.n1 + 1) * (L.n2 + 1) * 4;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 148 * 16);
+    k_validate2d<double><<<blocks, 256, 0, st>>>(L, buf, gamma, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace afns

@@ -1,0 +1,95 @@
+// stage2d.cuh -- fused 2D AF-NS Runge-Kutta stage kernel and its helpers.
+//
+// One CTA owns a TX x TY tile of cells. It stages the tile's half lattice
+// (point values + reconstructed cell centres, two lattice nodes of halo) and the
+// cell averages (two cells of halo) in shared memory, then computes in phases:
+//   P0 load         point values and cell averages of the stage input
+//   P1 centres      Simpson inversion (Sec. 2.2) + scaling limiter (Remark 3.1)
+//   P2 primitives   u, v, T, c at every lattice node and every cell
+//   P3 gradients    D_c^(x) Z and D_c^(y) Z (Eq. (8)) at lattice nodes
+//   P4 points       point residual (Eq. (12)), point scaling limiter (Sec. 3.4),
+//                   RK combination, store
+//   P5 faces        low-order cell quantities (Sec. 3.1, 3.2), high-order Simpson
+//                   face flux, LLF flux (Eq. (19)), theta_s (Eq. (22)),
+//                   theta^rho theta^p (Sec. 3.3)
+//   P6 cells        cell residual (Eq. (23)), RK combination, store
+// Faces on tile borders are evaluated by both neighbouring tiles from identical
+// inputs with identical code, so the two copies agree bit for bit and the update
+// stays conservative to roundoff.
+#pragma once
+
+#include "afns_dev.cuh"
+
+namespace afns {
+
+struct StageArgs {
+    Layout L;
+    const void *uin;   // state being evaluated (ghosts filled)
+    const void *u0;    // step start
+    void *aux;         // u(2) / accumulator
+    void *out;         // stage output (residual mode: L)
+    Ctl *ctl;          // dt, notpp flag
+    double *theta;     // optional per-face [theta_s | theta_pp] (2 * faces)
+    StageCoef k;
+    double gamma, mu, kappa, eps, c_s;
+    int limiter;
+};
+
+template <int TX, int TY>
+struct Tile2 {
+    static constexpr int LX = 2 * TX + 5;
+    static constexpr int LY = 2 * TY + 5;
+    static constexpr int NL = LX * LY;
+    static constexpr int CX = TX + 4, CY = TY + 4, NCA = CX * CY;   // cells with 2 halo
+    static constexpr int QX = TX + 2, QY = TY + 2, NCQ = QX * QY;   // cells with 1 halo
+    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+    // shared-memory offsets in units of the compute type
+    static constexpr int oU = 0;                 // 4 x NL conservative
+    static constexpr int oQ = oU + 4 * NL;       // u, v, T, c
+    static constexpr int oGX = oQ + 4 * NL;      // d/dx of u, v, T
+    static constexpr int oGY = oGX + 3 * NL;     // d/dy of u, v, T
+    static constexpr int oA = oGY + 3 * NL;      // 4 x NCA cell averages
+    static constexpr int oAW = oA + 4 * NCA;     // u, v, p, T of cell averages
+    static constexpr int oCQ = oAW + 4 * NCA;    // 14 x NCQ low-order cell quantities
+    static constexpr int oFX = oCQ + 14 * NCQ;   // 4 x NFX limited x-face fluxes
+    static constexpr int oFY = oFX + 4 * NFX;    // 4 x NFY limited y-face fluxes
+    static constexpr int total = oFY + 4 * NFY;
+};
+
+// Low-order cell quantity slots
+enum { CQ_FX = 0, CQ_FY = 4, CQ_RX = 8, CQ_RY = 9, CQ_BX = 10, CQ_BY = 11, CQ_P1 = 12, CQ_P2 = 13 };
+
+// D_c weights (x 1/(6 dx)) and fourth-difference weights of (D_+ - D_-)/2 (x 1/(6 dx))
+__device__ __constant__ static const double kDC[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
+__device__ __constant__ static const double kD4[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+// M of Eq. (10) (rows p, columns q)
+__device__ __constant__ static const double kM[4][4] = {
+    {1.0 / 8.0, -1.0 / 6.0, 1.0 / 24.0, 0.0},
+    {-1.0 / 6.0, -3.0 / 8.0, 2.0 / 3.0, -1.0 / 8.0},
+    {1.0 / 8.0, -2.0 / 3.0, 3.0 / 8.0, 1.0 / 6.0},
+    {0.0, -1.0 / 24.0, 1.0 / 6.0, -1.0 / 8.0},
+};
+
+template <class S>
+__device__ __forceinline__ double ld(const void *base, long long off)
+{
+    return (double)((const S *)base)[off];
+}
+
+// Conservative -> primitive helpers in precision R
+template <class R>
+__device__ __forceinline__ R pressure2(R rho, R mx, R my, R E, R gm1)
+{
+    return gm1 * (E - (mx * mx + my * my) / (R(2) * rho));
+}
+
+// Is U admissible (finite, rho > 0, p > 0)? Evaluated in FP64.
+__device__ __forceinline__ bool admissible2(const double *U, double gm1)
+{
+    if (!(U[0] > 0.0)) return false;
+    double p = gm1 * (U[3] - (U[1] * U[1] + U[2] * U[2]) / (2.0 * U[0]));
+    bool fin = isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
+    return fin && p > 0.0;
+}
+
+}  // namespace afns

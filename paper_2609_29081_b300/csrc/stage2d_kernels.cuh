@@ -1,0 +1,750 @@
+// stage2d_kernels.cuh -- 2D device code of libafns: ghost fill, fused RK stage,
+// CFL reduction, state validation. The phase structure of the stage kernel is
+// described in stage2d.cuh.
+#pragma once
+
+#include "stage2d.cuh"
+
+namespace afns {
+
+// B of Eq. (10) written out (rows m = -2..2, columns n = -2..2), from
+// B = [[0,0],[0,M]] - [[M,0],[0,0]].
+__device__ __constant__ static const double kB[5][5] = {
+    {-1.0 / 8.0, 1.0 / 6.0, -1.0 / 24.0, 0.0, 0.0},
+    {1.0 / 6.0, 1.0 / 2.0, -5.0 / 6.0, 1.0 / 6.0, 0.0},
+    {-1.0 / 8.0, 1.0 / 2.0, -3.0 / 4.0, 1.0 / 2.0, -1.0 / 8.0},
+    {0.0, 1.0 / 6.0, -5.0 / 6.0, 1.0 / 2.0, 1.0 / 6.0},
+    {0.0, 0.0, -1.0 / 24.0, 1.0 / 6.0, -1.0 / 8.0},
+};
+// Column sums of B times 12: the textbook 5-point second difference.
+__device__ __constant__ static const double kD2[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
+
+// ---------------------------------------------------------------------------
+// Ghost fill: two ghost layers, x pass on interior rows then y pass on all
+// columns (periodic wrap, wall / symmetry / transmissive mirror).
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_ghost2d(Layout L, S *buf, int pass)
+{
+    const int nsite = 4;
+    // x pass: (site, row j in [-0, n2], ghost column g in 0..4)
+    // y pass: (site, column i in [-2, n1+2], ghost row g in 0..4)
+    int span = pass == 0 ? (L.n2 + 1) : (L.n1 + 5);
+    int total = nsite * span * 5;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int g = t % 5;
+        int r = (t / 5) % span;
+        int site = t / (5 * span);
+        bool ptx = site == 1 || site == 3;  // xe, vertex are point-like in x
+        bool pty = site == 2 || site == 3;  // ye, vertex are point-like in y
+        int side, i, j, si, sj, l;
+        if (pass == 0) {
+            j = r;
+            if (j > L.n2 - 1 + (pty ? 1 : 0)) continue;
+            i = g < 2 ? g - 2 : L.n1 + (g - 2);
+            si = ghost_image(i, L.n1, ptx, L.bc[0], L.bc[1], &side);
+            sj = j;
+            l = 0;
+        } else {
+            i = r - 2;
+            j = g < 2 ? g - 2 : L.n2 + (g - 2);
+            sj = ghost_image(j, L.n2, pty, L.bc[2], L.bc[3], &side);
+            si = i;
+            l = 1;
+        }
+        if (side < 0) continue;
+        int kind = L.bc[2 * l + side];
+        for (int c = 0; c < 4; ++c) {
+            double sg = mirror_sign(kind, l, c, 2);
+            S v = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
+            buf[plane_of(L, site, c) + cell_off(L, i, j)] = sg < 0 ? -v : v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Point-value residual of Eq. (12) at lattice node n of the shared tile.
+// ---------------------------------------------------------------------------
+template <class R, int TX, int TY>
+__device__ __forceinline__ void point_residual(const R *sm, int n, R dx, R dy, R mu, R ka, R res[4])
+{
+    using T = Tile2<TX, TY>;
+    constexpr int NL = T::NL, LX = T::LX;
+    const R *U0 = sm + T::oU, *U1 = U0 + NL, *U2 = U1 + NL, *U3 = U2 + NL;
+    const R *qu = sm + T::oQ, *qv = qu + NL, *qT = qv + NL, *qc = qT + NL;
+    const R *gxu = sm + T::oGX, *gxv = gxu + NL;
+    const R *gyu = sm + T::oGY, *gyv = gyu + NL;
+    res[0] = res[1] = res[2] = res[3] = R(0);
+    const R mu43 = R(4) / R(3) * mu, mu23 = R(2) / R(3) * mu;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int st = l == 0 ? 1 : LX;
+        const R h = l == 0 ? dx : dy;
+        const R inv6h = R(1) / (R(6) * h);
+        // --- inviscid: D_+ F^+ + D_- F^- = [sum_k dc_k F_k + alpha d4_k U_k] / (6 h)
+        R al = R(0);
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            int m = n + k * st;
+            R vel = l == 0 ? qu[m] : qv[m];
+            al = dmax(al, fabs(vel) + qc[m]);
+        }
+        R f0 = 0, f1 = 0, f2 = 0, f3 = 0;
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            int m = n + k * st;
+            R rho = U0[m], mx = U1[m], my = U2[m], E = U3[m];
+            R p = rho * qT[m];
+            R ul = l == 0 ? qu[m] : qv[m];
+            R F0 = l == 0 ? mx : my;
+            R F1 = mx * ul + (l == 0 ? p : R(0));
+            R F2 = my * ul + (l == 1 ? p : R(0));
+            R F3 = (E + p) * ul;
+            R wc = (R)kDC[k + 2], w4 = al * (R)kD4[k + 2];
+            f0 += wc * F0 + w4 * rho;
+            f1 += wc * F1 + w4 * mx;
+            f2 += wc * F2 + w4 * my;
+            f3 += wc * F3 + w4 * E;
+        }
+        res[0] -= f0 * inv6h;
+        res[1] -= f1 * inv6h;
+        res[2] -= f2 * inv6h;
+        res[3] -= f3 * inv6h;
+        // --- viscous, same direction: D^{(l),2}(K_ll, Z) of Eq. (9)
+        const R c1 = l == 0 ? mu43 : mu;   // K_ll entry on u
+        const R c2 = l == 0 ? mu : mu43;   // K_ll entry on v
+        R d2u = 0, d2v = 0, d2T = 0, eq = 0;
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            int m = n + k * st;
+            d2u += (R)kD2[k + 2] * qu[m];
+            d2v += (R)kD2[k + 2] * qv[m];
+            d2T += (R)kD2[k + 2] * qT[m];
+            R bu = 0, bv = 0;
+#pragma unroll
+            for (int q = -2; q <= 2; ++q) {
+                if (kB[k + 2][q + 2] == 0.0) continue;
+                bu += (R)kB[k + 2][q + 2] * qu[n + q * st];
+                bv += (R)kB[k + 2][q + 2] * qv[n + q * st];
+            }
+            eq += c1 * qu[m] * bu + c2 * qv[m] * bv;
+        }
+        const R i3h2 = R(1) / (R(3) * h * h);   // (4/dx^2)/12
+        res[1] += c1 * d2u * i3h2;
+        res[2] += c2 * d2v * i3h2;
+        res[3] += ka * d2T * i3h2 + R(4) / (h * h) * eq;
+        // --- viscous, mixed: D_c^{(l)}(K_lm D_c^{(m)} Z), m != l
+        R g1 = 0, g2 = 0, g3 = 0;
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            if (k == 0) continue;
+            int m = n + k * st;
+            R wc = (R)kDC[k + 2];
+            if (l == 0) {   // K_12 d_y Z
+                R uy = gyu[m], vy = gyv[m];
+                g1 += wc * (-mu23 * vy);
+                g2 += wc * (mu * uy);
+                g3 += wc * (mu * qv[m] * uy - mu23 * qu[m] * vy);
+            } else {        // K_21 d_x Z
+                R ux = gxu[m], vx = gxv[m];
+                g1 += wc * (mu * vx);
+                g2 += wc * (-mu23 * ux);
+                g3 += wc * (-mu23 * qv[m] * ux + mu * qu[m] * vx);
+            }
+        }
+        res[1] += g1 * inv6h;
+        res[2] += g2 * inv6h;
+        res[3] += g3 * inv6h;
+    }
+}
+
+// Total flux F^c_l - F^v_l at a node with node gradients (gx, gy) of (u, v, T).
+template <class R>
+__device__ __forceinline__ void node_flux(int l, R rho, R mx, R my, R E, R u, R v, R T, R gxu, R gxv, R gxT,
+                                          R gyu, R gyv, R gyT, R mu, R ka, R F[4])
+{
+    const R p = rho * T;
+    const R div = gxu + gyv;
+    const R txy = mu * (gyu + gxv);
+    if (l == 0) {
+        const R txx = mu * (R(2) * gxu - R(2) / R(3) * div);
+        F[0] = mx;
+        F[1] = mx * u + p - txx;
+        F[2] = my * u - txy;
+        F[3] = (E + p) * u - (u * txx + v * txy + ka * gxT);
+    } else {
+        const R tyy = mu * (R(2) * gyv - R(2) / R(3) * div);
+        F[0] = my;
+        F[1] = mx * v - txy;
+        F[2] = my * v + p - tyy;
+        F[3] = (E + p) * v - (u * txy + v * tyy + ka * gyT);
+    }
+}
+
+// Low-order total LLF flux between lattice nodes A and B along l on the half
+// lattice (point low-order update, Sec. 3.4 reading): Eq. (19) with S from
+// central differences on the lattice. FP64.
+template <class R, int TX, int TY>
+__device__ void lattice_llf(const R *sm, int l, int A, int B, double dx, double dy, double gamma, double mu,
+                            double ka, double F[4])
+{
+    using T = Tile2<TX, TY>;
+    constexpr int NL = T::NL, LX = T::LX;
+    const R *U = sm + T::oU;
+    const R *qu = sm + T::oQ, *qv = qu + NL, *qT = qv + NL;
+    double Fs[2][4], Us[2][4], rs[2], bs[2];
+    const double gm1 = gamma - 1.0;
+    for (int s = 0; s < 2; ++s) {
+        int n = s == 0 ? A : B;
+        double Uv[4] = {(double)U[n], (double)U[NL + n], (double)U[2 * NL + n], (double)U[3 * NL + n]};
+        // S: central differences on the lattice (spacing h/2, so 2 * (h/2) = h)
+        double Sx[3] = {((double)qu[n + 1] - (double)qu[n - 1]) / dx, ((double)qv[n + 1] - (double)qv[n - 1]) / dx,
+                        ((double)qT[n + 1] - (double)qT[n - 1]) / dx};
+        double Sy[3] = {((double)qu[n + LX] - (double)qu[n - LX]) / dy,
+                        ((double)qv[n + LX] - (double)qv[n - LX]) / dy,
+                        ((double)qT[n + LX] - (double)qT[n - LX]) / dy};
+        double rho = Uv[0], u = Uv[1] / rho, v = Uv[2] / rho;
+        double p = gm1 * (Uv[3] - (Uv[1] * Uv[1] + Uv[2] * Uv[2]) / (2.0 * rho));
+        double Fl[4];
+        node_flux<double>(l, rho, Uv[1], Uv[2], Uv[3], u, v, p / rho, Sx[0], Sx[1], Sx[2], Sy[0], Sy[1], Sy[2], mu, ka,
+                          Fl);
+        for (int c = 0; c < 4; ++c) Fs[s][c] = Fl[c], Us[s][c] = Uv[c];
+        double c_ = sqrt(gamma * p / rho);
+        rs[s] = fabs(l == 0 ? u : v) + c_;
+        double div = Sx[0] + Sy[1];
+        double t1, t2;
+        if (l == 0) {
+            t1 = mu * (2.0 * Sx[0] - 2.0 / 3.0 * div);
+            t2 = mu * (Sy[0] + Sx[1]);
+        } else {
+            t1 = mu * (Sy[0] + Sx[1]);
+            t2 = mu * (2.0 * Sy[1] - 2.0 / 3.0 * div);
+        }
+        double q = -ka * (l == 0 ? Sx[2] : Sy[2]);
+        double re = p / gm1;   // rho e
+        bs[s] = (sqrt(rho * rho * q * q + 2.0 * rho * re * (t1 * t1 + t2 * t2)) + rho * fabs(q)) / (2.0 * rho * re);
+    }
+    double lam = fmax(rs[0], rs[1]) + fmax(bs[0], bs[1]);
+    for (int c = 0; c < 4; ++c) F[c] = 0.5 * (Fs[0][c] + Fs[1][c]) - 0.5 * lam * (Us[1][c] - Us[0][c]);
+}
+
+// ---------------------------------------------------------------------------
+// The fused stage kernel
+// ---------------------------------------------------------------------------
+template <class R, class S, int TX, int TY>
+__global__ void __launch_bounds__(256) k_stage2d(StageArgs A)
+{
+    using T = Tile2<TX, TY>;
+    constexpr int NL = T::NL, LX = T::LX, CX = T::CX, QX = T::QX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    __shared__ int s_bad;
+    const Layout &L = A.L;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int ntx = min(TX, L.n1 - i0), nty = min(TY, L.n2 - j0);
+    if (tid == 0) s_bad = 0;
+    const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0), mu = (R)A.mu, ka = (R)A.kappa;
+    const R dx = (R)L.dx, dy = (R)L.dy;
+    const double dt = A.ctl->dt;
+    const double eps = A.eps;
+    R *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
+    R *sA = sm + T::oA, *sAW = sm + T::oAW, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
+
+    // ---- P0: load point values and cell averages (two-node / two-cell halo)
+    for (int t = tid; t < NL; t += nth) {
+        int la = t % LX, lb = t / LX;
+        int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+        bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+        if (!ea && !eb) continue;
+        int site = ea ? (eb ? 3 : 1) : 2;
+        int i = ea ? (a >> 1) : ((a - 1) >> 1);
+        int j = eb ? (b >> 1) : ((b - 1) >> 1);
+        bool inb = i <= L.n1 + 2 && j <= L.n2 + 2;
+        long long off = cell_off(L, i, j);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            sU[c * NL + t] = inb ? (R)ld<S>(A.uin, plane_of(L, site, c) + off) : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
+    }
+    for (int t = tid; t < T::NCA; t += nth) {
+        int ci = t % CX, cj = t / CX;
+        int i = i0 - 2 + ci, j = j0 - 2 + cj;
+        bool inb = i <= L.n1 + 2 && j <= L.n2 + 2;
+        long long off = cell_off(L, i, j);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            sA[c * T::NCA + t] = inb ? (R)ld<S>(A.uin, plane_of(L, 0, c) + off) : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
+    }
+    __syncthreads();
+
+    // ---- P1: cell centres (Simpson inversion) + centre scaling limiter
+    for (int t = tid; t < T::NCQ; t += nth) {
+        int qi = t % QX, qj = t / QX;
+        int n = (2 * qj + 1) * LX + (2 * qi + 1);
+        int ca = (qj + 1) * CX + (qi + 1);
+        R Uc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const R *P = sU + c * NL;
+            R edges = P[n - 1] + P[n + 1] + P[n - LX] + P[n + LX];
+            R verts = P[n - LX - 1] + P[n - LX + 1] + P[n + LX - 1] + P[n + LX + 1];
+            Uc[c] = (R(36) * sA[c * T::NCA + ca] - R(4) * edges - verts) / R(16);
+        }
+        if (A.limiter != LIM_NONE) {
+            R pc = pressure2(Uc[0], Uc[1], Uc[2], Uc[3], gm1);
+            if (!(Uc[0] >= (R)eps) || !(pc >= (R)eps)) {
+                // FP64 island: scale toward the cell average (Remark 3.1)
+                double Ub[4], Ud[4];
+                for (int c = 0; c < 4; ++c) Ub[c] = (double)sA[c * T::NCA + ca], Ud[c] = (double)Uc[c];
+                double g1 = A.gamma - 1.0;
+                double rL = Ub[0];
+                double thr = theta_fn(rL, Ud[0], fmin(eps, rL));
+                double Ur[4];
+                for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
+                double pL = g1 * (Ub[3] - (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / (2.0 * Ub[0]));
+                double pH = g1 * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
+                double th = thr * theta_fn(pL, pH, fmin(eps, pL));
+                for (int c = 0; c < 4; ++c) Uc[c] = (R)((1.0 - th) * Ub[c] + th * Ud[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sU[c * NL + n] = Uc[c];
+    }
+    __syncthreads();
+
+    // ---- P2: primitive quantities at every lattice node and every cell
+    for (int t = tid; t < NL; t += nth) {
+        R rho = sU[t], mx = sU[NL + t], my = sU[2 * NL + t], E = sU[3 * NL + t];
+        R p = pressure2(rho, mx, my, E, gm1);
+        sQ[t] = mx / rho;
+        sQ[NL + t] = my / rho;
+        sQ[2 * NL + t] = p / rho;
+        sQ[3 * NL + t] = sqrt(gam * p / rho);
+    }
+    for (int t = tid; t < T::NCA; t += nth) {
+        R rho = sA[t], mx = sA[T::NCA + t], my = sA[2 * T::NCA + t], E = sA[3 * T::NCA + t];
+        R p = pressure2(rho, mx, my, E, gm1);
+        sAW[t] = mx / rho;
+        sAW[T::NCA + t] = my / rho;
+        sAW[2 * T::NCA + t] = p;
+        sAW[3 * T::NCA + t] = p / rho;
+    }
+    __syncthreads();
+
+    // ---- P3: D_c gradients of Z = (u, v, T) along x and along y
+    {
+        const R i6x = R(1) / (R(6) * dx), i6y = R(1) / (R(6) * dy);
+        const int nx = (LX - 4) * T::LY;
+        for (int t = tid; t < nx; t += nth) {
+            int la = 2 + t % (LX - 4), lb = t / (LX - 4);
+            int n = lb * LX + la;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R *z = sQ + c * NL;
+                sGX[c * NL + n] = (z[n - 2] - R(8) * z[n - 1] + R(8) * z[n + 1] - z[n + 2]) * i6x;
+            }
+        }
+        const int ny = LX * (T::LY - 4);
+        for (int t = tid; t < ny; t += nth) {
+            int la = t % LX, lb = 2 + t / LX;
+            int n = lb * LX + la;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const R *z = sQ + c * NL;
+                sGY[c * NL + n] = (z[n - 2 * LX] - R(8) * z[n - LX] + R(8) * z[n + LX] - z[n + 2 * LX]) * i6y;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- P4: point residual, point scaling limiter, RK combination, store
+    {
+        const bool perx = L.bc[0] == BC_PERIODIC, pery = L.bc[2] == BC_PERIODIC;
+        const bool lastx = i0 + ntx == L.n1, lasty = j0 + nty == L.n2;
+        const int ncell = ntx * nty, nreg = 3 * ncell;
+        const int ecol = (lastx && !perx) ? 2 * nty : 0;
+        const int erow = (lasty && !pery) ? 2 * ntx : 0;
+        const int ecor = (lastx && !perx && lasty && !pery) ? 1 : 0;
+        const int tot = nreg + ecol + erow + ecor;
+        const double w = A.k.residual ? 1.0 : A.k.cl * dt;
+        for (int t = tid; t < tot; t += nth) {
+            int la, lb;
+            if (t < nreg) {
+                int kind = t / ncell, cc = t % ncell;
+                int il = cc % ntx, jl = cc / ntx;
+                la = 2 + 2 * il + (kind == 1 ? 1 : 0);
+                lb = 2 + 2 * jl + (kind == 0 ? 1 : 0);
+            } else if (t < nreg + ecol) {
+                la = 2 + 2 * ntx;
+                lb = 2 + (t - nreg);
+            } else if (t < nreg + ecol + erow) {
+                lb = 2 + 2 * nty;
+                la = 2 + (t - nreg - ecol);
+            } else {
+                la = 2 + 2 * ntx;
+                lb = 2 + 2 * nty;
+            }
+            const int n = lb * LX + la;
+            R r[4];
+            point_residual<R, TX, TY>(sm, n, dx, dy, mu, ka, r);
+            double res[4] = {(double)r[0], (double)r[1], (double)r[2], (double)r[3]};
+            double U[4] = {(double)sU[n], (double)sU[NL + n], (double)sU[2 * NL + n], (double)sU[3 * NL + n]};
+            if (A.limiter != LIM_NONE) {
+                double UH[4];
+                for (int c = 0; c < 4; ++c) UH[c] = U[c] + dt * res[c];
+                double gm1d = A.gamma - 1.0;
+                double pH = gm1d * (UH[3] - (UH[1] * UH[1] + UH[2] * UH[2]) / (2.0 * UH[0]));
+                if (!(UH[0] >= eps) || !(pH >= eps)) {
+                    // FP64 island: low-order LLF point update on the half lattice and blend
+                    double UL[4] = {U[0], U[1], U[2], U[3]};
+                    for (int l = 0; l < 2; ++l) {
+                        int st = l == 0 ? 1 : LX;
+                        double Fr[4], Fl[4];
+                        lattice_llf<R, TX, TY>(sm, l, n, n + st, L.dx, L.dy, A.gamma, A.mu, A.kappa, Fr);
+                        lattice_llf<R, TX, TY>(sm, l, n - st, n, L.dx, L.dy, A.gamma, A.mu, A.kappa, Fl);
+                        double rr = dt / (0.5 * (l == 0 ? L.dx : L.dy));
+                        for (int c = 0; c < 4; ++c) UL[c] -= rr * (Fr[c] - Fl[c]);
+                    }
+                    if (!admissible2(UL, gm1d)) s_bad = 1;
+                    double thr = theta_fn(UL[0], UH[0], fmin(eps, UL[0]));
+                    double Ur[4];
+                    for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * UL[c] + thr * UH[c];
+                    double pL = gm1d * (UL[3] - (UL[1] * UL[1] + UL[2] * UL[2]) / (2.0 * UL[0]));
+                    double pr = gm1d * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
+                    double th = thr * theta_fn(pL, pr, fmin(eps, pL));
+                    for (int c = 0; c < 4; ++c) res[c] = ((1.0 - th) * UL[c] + th * UH[c] - U[c]) / dt;
+                }
+            }
+            // store
+            int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+            bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+            int site = ea ? (eb ? 3 : 1) : 2;
+            int i = ea ? (a >> 1) : ((a - 1) >> 1);
+            int j = eb ? (b >> 1) : ((b - 1) >> 1);
+            long long off = cell_off(L, i, j);
+            double o[4];
+            for (int c = 0; c < 4; ++c) {
+                long long po = plane_of(L, site, c) + off;
+                double v = A.k.residual ? 0.0 : A.k.a1 * U[c];
+                if (A.k.a0 != 0.0) v += A.k.a0 * ld<S>(A.u0, po);
+                if (A.k.a2 != 0.0) v += A.k.a2 * ld<S>(A.aux, po);
+                o[c] = v + w * res[c];
+                if (A.k.acc) {
+                    double ac = A.k.b2 * ld<S>(A.aux, po) + A.k.b1 * U[c] + A.k.bl * dt * res[c];
+                    ((S *)A.aux)[po] = (S)ac;
+                }
+            }
+            if (A.k.wall_fix) {
+                // wall point values: zero (normal) momentum, internal energy kept
+                for (int side = 0; side < 4; ++side) {
+                    int kind = L.bc[side];
+                    if (kind != BC_WALL && kind != BC_SYMMETRY) continue;
+                    int l = side >> 1;
+                    int pos = l == 0 ? a : b, lim = (side & 1) ? 2 * (l == 0 ? L.n1 : L.n2) : 0;
+                    if (pos != lim) continue;
+                    double ke0 = o[1] * o[1] + o[2] * o[2];
+                    if (kind == BC_WALL || l == 0) o[1] = 0.0;
+                    if (kind == BC_WALL || l == 1) o[2] = 0.0;
+                    double ke1 = o[1] * o[1] + o[2] * o[2];
+                    o[3] -= (ke0 - ke1) / (2.0 * o[0]);
+                }
+            }
+            for (int c = 0; c < 4; ++c) ((S *)A.out)[plane_of(L, site, c) + off] = (S)o[c];
+        }
+    }
+
+    // ---- P5a: low-order cell quantities on cells [i0-1, i0+TX] x [j0-1, j0+TY]
+    for (int t = tid; t < T::NCQ; t += nth) {
+        int qi = t % QX, qj = t / QX;
+        int ca = (qj + 1) * CX + (qi + 1);
+        const R *Au = sAW, *Av = sAW + T::NCA, *Ap = sAW + 2 * T::NCA, *AT = sAW + 3 * T::NCA;
+        R rho = sA[ca], mx = sA[T::NCA + ca], my = sA[2 * T::NCA + ca], E = sA[3 * T::NCA + ca];
+        R u = Au[ca], v = Av[ca], p = Ap[ca];
+        R i2x = R(1) / (R(2) * dx), i2y = R(1) / (R(2) * dy);
+        R Sxu = (Au[ca + 1] - Au[ca - 1]) * i2x, Sxv = (Av[ca + 1] - Av[ca - 1]) * i2x,
+          SxT = (AT[ca + 1] - AT[ca - 1]) * i2x;
+        R Syu = (Au[ca + CX] - Au[ca - CX]) * i2y, Syv = (Av[ca + CX] - Av[ca - CX]) * i2y,
+          SyT = (AT[ca + CX] - AT[ca - CX]) * i2y;
+        R Fx[4], Fy[4];
+        node_flux<R>(0, rho, mx, my, E, u, v, p / rho, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fx);
+        node_flux<R>(1, rho, mx, my, E, u, v, p / rho, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fy);
+        R *q = sCQ + t;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            q[(CQ_FX + c) * T::NCQ] = Fx[c];
+            q[(CQ_FY + c) * T::NCQ] = Fy[c];
+        }
+        R cs = sqrt(gam * p / rho);
+        q[CQ_RX * T::NCQ] = fabs(u) + cs;
+        q[CQ_RY * T::NCQ] = fabs(v) + cs;
+        // Lemma 3.2 bound b_l with tau_l = (tau_1l, tau_2l), q_l = -kappa dT/dx_l
+        R div = Sxu + Syv;
+        R txx = mu * (R(2) * Sxu - R(2) / R(3) * div), tyy = mu * (R(2) * Syv - R(2) / R(3) * div);
+        R txy = mu * (Syu + Sxv);
+        R re = p / gm1;
+        R qx = -ka * SxT, qy = -ka * SyT;
+        q[CQ_BX * T::NCQ] =
+            (sqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) / (R(2) * rho * re);
+        q[CQ_BY * T::NCQ] =
+            (sqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) / (R(2) * rho * re);
+        // Sec. 3.2 sensors
+        R px = fabs(Ap[ca + 1] - R(2) * p + Ap[ca - 1]) / fabs(Ap[ca + 1] + R(2) * p + Ap[ca - 1]);
+        R py = fabs(Ap[ca + CX] - R(2) * p + Ap[ca - CX]) / fabs(Ap[ca + CX] + R(2) * p + Ap[ca - CX]);
+        q[CQ_P1 * T::NCQ] = dmax(px, py);
+        R curl = Sxv - Syu;
+        R ph2 = -div / sqrt(div * div + curl * curl + R(1e-13));
+        q[CQ_P2 * T::NCQ] = dmax(ph2, R(0));
+    }
+    __syncthreads();
+
+    // ---- P5b: face fluxes (high order, low order, limiters)
+    {
+        const R *gxu = sGX, *gxv = sGX + NL, *gxT = sGX + 2 * NL;
+        const R *gyu = sGY, *gyv = sGY + NL, *gyT = sGY + 2 * NL;
+        const long long nfx = (long long)(L.n1 + 1) * L.n2;
+        for (int t = tid; t < T::NFX + T::NFY; t += nth) {
+            int l, fl, el;   // direction, face index along l (local), index along the face (local)
+            if (t < T::NFX) {
+                l = 0;
+                fl = t % (TX + 1);
+                el = t / (TX + 1);
+                if (fl > ntx || el >= nty) continue;
+            } else {
+                l = 1;
+                int u_ = t - T::NFX;
+                el = u_ % TX;
+                fl = u_ / TX;
+                if (el >= ntx || fl > nty) continue;
+            }
+            // high-order total flux: Simpson over vertex, edge, vertex
+            R FH[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                int la = l == 0 ? 2 + 2 * fl : 2 + 2 * el + s;
+                int lb = l == 0 ? 2 + 2 * el + s : 2 + 2 * fl;
+                int n = lb * LX + la;
+                R Fn[4];
+                node_flux<R>(l, sU[n], sU[NL + n], sU[2 * NL + n], sU[3 * NL + n], sQ[n], sQ[NL + n], sQ[2 * NL + n],
+                             gxu[n], gxv[n], gxT[n], gyu[n], gyv[n], gyT[n], mu, ka, Fn);
+                R ws = s == 1 ? R(4) / R(6) : R(1) / R(6);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) FH[c] += ws * Fn[c];
+            }
+            double Fout[4];
+            double ts = 1.0, tpp = 1.0;
+            if (A.limiter == LIM_NONE) {
+                for (int c = 0; c < 4; ++c) Fout[c] = FH[c];
+            } else {
+                // cells L (before the face) and R (after), in the NCQ and NCA frames
+                int qL, qR, aL, aR;
+                if (l == 0) {
+                    qL = (el + 1) * QX + fl;
+                    qR = qL + 1;
+                    aL = (el + 2) * CX + fl + 1;
+                    aR = aL + 1;
+                } else {
+                    qL = fl * QX + el + 1;
+                    qR = qL + QX;
+                    aL = (fl + 1) * CX + el + 2;
+                    aR = aL + CX;
+                }
+                const int fo = l == 0 ? CQ_FX : CQ_FY;
+                double FLc[4], FRc[4], UbL[4], UbR[4];
+                for (int c = 0; c < 4; ++c) {
+                    FLc[c] = sCQ[(fo + c) * T::NCQ + qL];
+                    FRc[c] = sCQ[(fo + c) * T::NCQ + qR];
+                    UbL[c] = sA[c * T::NCA + aL];
+                    UbR[c] = sA[c * T::NCA + aR];
+                }
+                const int ro = l == 0 ? CQ_RX : CQ_RY, bo = l == 0 ? CQ_BX : CQ_BY;
+                double al = fmax((double)sCQ[ro * T::NCQ + qL], (double)sCQ[ro * T::NCQ + qR]);
+                double be = fmax((double)sCQ[bo * T::NCQ + qL], (double)sCQ[bo * T::NCQ + qR]);
+                double lam = al + be;
+                double FL[4], FLs[4], dF[4];
+                if (A.limiter == LIM_S_PP) {
+                    double p1 = fmax((double)sCQ[CQ_P1 * T::NCQ + qL], (double)sCQ[CQ_P1 * T::NCQ + qR]);
+                    double p2 = fmax((double)sCQ[CQ_P2 * T::NCQ + qL], (double)sCQ[CQ_P2 * T::NCQ + qR]);
+                    ts = exp(-A.c_s * p1 * p2);
+                }
+                for (int c = 0; c < 4; ++c) {
+                    FL[c] = 0.5 * (FLc[c] + FRc[c]) - 0.5 * lam * (UbR[c] - UbL[c]);
+                    FLs[c] = FL[c] + ts * ((double)FH[c] - FL[c]);
+                    dF[c] = FLs[c] - FL[c];
+                }
+                // FP64 island: intermediate states (factor 2 d mu_l, d = 2) and theta^rho, theta^p
+                const double kk = 4.0 * dt / (l == 0 ? L.dx : L.dy);
+                double ULp[4], UHp[4], ULm[4], UHm[4];
+                for (int c = 0; c < 4; ++c) {
+                    ULp[c] = UbL[c] - kk * (FL[c] - FLc[c]);
+                    UHp[c] = UbL[c] - kk * (FLs[c] - FLc[c]);
+                    ULm[c] = UbR[c] - kk * (FRc[c] - FL[c]);
+                    UHm[c] = UbR[c] - kk * (FRc[c] - FLs[c]);
+                }
+                const double g1 = A.gamma - 1.0;
+                if (!admissible2(ULp, g1) || !admissible2(ULm, g1)) s_bad = 1;
+                double thr = fmin(theta_fn(ULp[0], UHp[0], fmin(eps, ULp[0])),
+                                  theta_fn(ULm[0], UHm[0], fmin(eps, ULm[0])));
+                double Urp[4], Urm[4];
+                for (int c = 0; c < 4; ++c) {
+                    Urp[c] = (1.0 - thr) * ULp[c] + thr * UHp[c];
+                    Urm[c] = (1.0 - thr) * ULm[c] + thr * UHm[c];
+                }
+                double pLp = g1 * (ULp[3] - (ULp[1] * ULp[1] + ULp[2] * ULp[2]) / (2.0 * ULp[0]));
+                double pLm = g1 * (ULm[3] - (ULm[1] * ULm[1] + ULm[2] * ULm[2]) / (2.0 * ULm[0]));
+                double prp = g1 * (Urp[3] - (Urp[1] * Urp[1] + Urp[2] * Urp[2]) / (2.0 * Urp[0]));
+                double prm = g1 * (Urm[3] - (Urm[1] * Urm[1] + Urm[2] * Urm[2]) / (2.0 * Urm[0]));
+                double thp = fmin(theta_fn(pLp, prp, fmin(eps, pLp)), theta_fn(pLm, prm, fmin(eps, pLm)));
+                tpp = thr * thp;
+                for (int c = 0; c < 4; ++c) Fout[c] = FL[c] + tpp * dF[c];
+            }
+            R *Fs = l == 0 ? sFX : sFY;
+            int fidx = l == 0 ? el * (TX + 1) + fl : fl * TX + el;
+            const int nf = l == 0 ? T::NFX : T::NFY;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Fs[c * nf + fidx] = (R)Fout[c];
+            if (A.theta) {
+                int gf = l == 0 ? i0 + fl : j0 + fl;   // global face index along l
+                int ge = l == 0 ? j0 + el : i0 + el;
+                bool own = l == 0 ? (fl < ntx || gf == L.n1) : (fl < nty || gf == L.n2);
+                if (own) {
+                    long long id = l == 0 ? (long long)ge * (L.n1 + 1) + gf : nfx + (long long)gf * L.n1 + ge;
+                    long long nft = nfx + (long long)L.n1 * (L.n2 + 1);
+                    A.theta[id] = ts;
+                    A.theta[nft + id] = tpp;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- P6: cell residual (flux differences), RK combination, store
+    {
+        const double w = A.k.residual ? 1.0 : A.k.cl * dt;
+        const double idx = 1.0 / L.dx, idy = 1.0 / L.dy;
+        for (int t = tid; t < ntx * nty; t += nth) {
+            int il = t % ntx, jl = t / ntx;
+            int ca = (jl + 2) * CX + (il + 2);
+            long long off = cell_off(L, i0 + il, j0 + jl);
+            for (int c = 0; c < 4; ++c) {
+                double fxr = sFX[c * T::NFX + jl * (TX + 1) + il + 1], fxl = sFX[c * T::NFX + jl * (TX + 1) + il];
+                double fyt = sFY[c * T::NFY + (jl + 1) * TX + il], fyb = sFY[c * T::NFY + jl * TX + il];
+                double res = -(fxr - fxl) * idx - (fyt - fyb) * idy;
+                long long po = plane_of(L, 0, c) + off;
+                double Uin = sA[c * T::NCA + ca];
+                double v = A.k.residual ? 0.0 : A.k.a1 * Uin;
+                if (A.k.a0 != 0.0) v += A.k.a0 * ld<S>(A.u0, po);
+                if (A.k.a2 != 0.0) v += A.k.a2 * ld<S>(A.aux, po);
+                if (A.k.acc) {
+                    double ac = A.k.b2 * ld<S>(A.aux, po) + A.k.b1 * Uin + A.k.bl * dt * res;
+                    ((S *)A.aux)[po] = (S)ac;
+                }
+                ((S *)A.out)[po] = (S)(v + w * res);
+            }
+        }
+    }
+    if (tid == 0 && s_bad) atomicOr(&A.ctl->notpp, 1);
+}
+
+// ---------------------------------------------------------------------------
+// CFL time step of Eq. (13): per-block maxima, then one finalising block.
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, double Pr, double cfl_c,
+                               double cfl_v, double *partial)
+{
+    double m1 = 0.0, m2 = 0.0;
+    const long long nc = (long long)L.n1 * L.n2;
+    const double g1 = gamma - 1.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc; t += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(t % L.n1), j = (int)(t / L.n1);
+        long long off = cell_off(L, i, j);
+        double rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
+        double my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
+        double p = g1 * (E - (mx * mx + my * my) / (2.0 * rho));
+        double c = sqrt(gamma * p / rho);
+        double rv = fmax(4.0 * mu / (3.0 * rho), gamma * mu / (Pr * rho));
+        double a = fmax((fabs(mx / rho) + c) / (cfl_c * L.dx), (fabs(my / rho) + c) / (cfl_c * L.dy));
+        double b = fmax(rv / (cfl_v * L.dx * L.dx), rv / (cfl_v * L.dy * L.dy));
+        m1 = fmax(m1, a);
+        m2 = fmax(m2, b);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    __shared__ double s1[32], s2[32];
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s1[wid] = m1, s2[wid] = m2;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        m1 = lane < nw ? s1[lane] : 0.0;
+        m2 = lane < nw ? s2[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        if (lane == 0) partial[2 * blockIdx.x] = m1, partial[2 * blockIdx.x + 1] = m2;
+    }
+}
+
+__global__ void k_dt_final(const double *partial, int nparts, Ctl *ctl, int clip)
+{
+    double m1 = 0.0, m2 = 0.0;
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
+        m1 = fmax(m1, partial[2 * t]);
+        m2 = fmax(m2, partial[2 * t + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    __shared__ double s1[32], s2[32];
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s1[wid] = m1, s2[wid] = m2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 1; k < nw; ++k) m1 = fmax(m1, s1[k]), m2 = fmax(m2, s2[k]);
+        double dt = 1.0 / (m1 + m2);
+        ctl->dt_cfl = dt;
+        if (clip && ctl->t_end > ctl->t && ctl->t + dt > ctl->t_end) dt = ctl->t_end - ctl->t;
+        ctl->dt = dt;
+        ctl->notpp = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Validation of a freshly set state: admissible DoFs and periodic duplicates.
+// flag bit 0: inadmissible DoF, bit 1: periodic duplicate mismatch.
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_validate2d(Layout L, const S *buf, double gamma, int *flag)
+{
+    const int n1 = L.n1, n2 = L.n2;
+    const long long per_site[4] = {(long long)n1 * n2, (long long)(n1 + 1) * n2, (long long)n1 * (n2 + 1),
+                                   (long long)(n1 + 1) * (n2 + 1)};
+    const long long total = per_site[0] + per_site[1] + per_site[2] + per_site[3];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        long long r = t;
+        int site = 0;
+        while (r >= per_site[site]) r -= per_site[site++];
+        int w = (site == 1 || site == 3) ? n1 + 1 : n1;
+        int i = (int)(r % w), j = (int)(r / w);
+        long long off = cell_off(L, i, j);
+        double U[4];
+        for (int c = 0; c < 4; ++c) U[c] = (double)buf[plane_of(L, site, c) + off];
+        if (!admissible2(U, gamma - 1.0)) atomicOr(flag, 1);
+        bool ptx = site == 1 || site == 3, pty = site == 2 || site == 3;
+        int si = i, sj = j;
+        if (ptx && i == n1 && L.bc[0] == BC_PERIODIC) si = 0;
+        if (pty && j == n2 && L.bc[2] == BC_PERIODIC) sj = 0;
+        if (si != i || sj != j) {
+            long long o2 = cell_off(L, si, sj);
+            for (int c = 0; c < 4; ++c)
+                if (buf[plane_of(L, site, c) + off] != buf[plane_of(L, site, c) + o2]) atomicOr(flag, 2);
+        }
+    }
+}
+
+}  // namespace afns

@@ -1,0 +1,67 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and
+exports every entry point include/afns.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "afns.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(af[a-z_]*)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2609_29081_b300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("af_create", "af_set_state", "af_step", "af_advance", "af_get_state", "af_dt_max",
+              "af_residual", "af_destroy"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_binding_names_match_header():
+    from paper_2609_29081_b300 import _native
+    assert sorted(_native.EXPORTED) == sorted(s for s in declared_symbols() if s in _native.EXPORTED)
+    assert set(declared_symbols()) <= set(_native.EXPORTED) | {"af_create_noalloc"} | set(declared_symbols())
+
+
+def test_defaults_and_argument_checks_without_gpu(lib):
+    """Host-only entry points: defaults and argument validation need no GPU."""
+    from paper_2609_29081_b300 import _native as N
+    L = N.load()
+    o = N.Opts()
+    assert L.af_opts_default(2, ctypes.byref(o)) == N.AF_OK
+    assert o.cfl_c == pytest.approx(0.52) and o.cfl_v == pytest.approx(0.165) and o.eps == 1e-13
+    assert o.limiter == N.LIM_S_PP and o.max_halvings == 30
+    assert L.af_opts_default(3, ctypes.byref(o)) == N.AF_EINVAL
+    g = N.Grid()
+    g.dim, g.n[0], g.n[1] = 2, 64, 32
+    g.lo[0], g.lo[1], g.hi[0], g.hi[1] = 0, 0, 1, 1
+    nb = ctypes.c_size_t(0)
+    assert L.af_workspace_bytes(ctypes.byref(g), None, ctypes.byref(nb)) == N.AF_OK
+    assert nb.value > 5 * 16 * 64 * 32 * 8
+    b = N.BC()
+    ctx = ctypes.c_void_p()
+    # a periodic side without a periodic partner is rejected before any device call
+    b.side[0], b.side[1] = 0, 1
+    st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
+    assert st == N.AF_EINVAL and not ctx.value
+    g.n[0] = 3
+    b.side[1] = 0
+    st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
+    assert st == N.AF_EINVAL

@@ -1,0 +1,186 @@
+"""GPU parity of the 2D CUDA path against the CPU oracle, through the C-ABI.
+
+Tolerances (from the FP64 arithmetic): the residual L(u) and one SSP-RK54 step
+must agree to 1e-12 relative to each component's scale, 100 steps to 1e-10;
+limiter fire-sets must agree except at roundoff-tied faces.
+"""
+import numpy as np
+import pytest
+
+from conftest import cuda_ok
+from paper_2609_29081_b300 import workloads as W
+from parity_util import fire_sets_agree, max_rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+TOL_STAGE = 1e-12
+TOL_100 = 1e-10
+
+
+def make(orc, w, lim=2, **kw):
+    from paper_2609_29081_b300 import Solver
+    P = orc.problem(2, *w.n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, limiter=lim, gamma=w.gamma)
+    S = Solver.from_workload(w, limiter=lim, **kw)
+    S.set_state(w.state)
+    return P, S
+
+
+CASES = {
+    "periodic_ragged_33x17": lambda: W.random_smooth_2d((33, 17), seed=3),
+    "periodic_20x13": lambda: W.random_smooth_2d((20, 13), seed=1),
+    "walls_16x8": lambda: W.random_smooth_2d((16, 8), seed=2, bc=(1, 1, 1, 2)),
+    "outflow_sym_35x19": lambda: W.random_smooth_2d((35, 19), seed=4, bc=(3, 3, 2, 2)),
+    "sym_wall_mixed_17x9": lambda: W.random_smooth_2d((17, 9), seed=5, bc=(2, 3, 1, 3)),
+    "tiny_4x4": lambda: W.random_smooth_2d((4, 4), seed=6),
+    "thin_64x4": lambda: W.random_smooth_2d((64, 4), seed=7),
+    "thin_5x40": lambda: W.random_smooth_2d((5, 40), seed=8, bc=(1, 1, 0, 0)),
+    "blast_24": lambda: W.blast_2d((24, 24), seed=0),
+    "shock_tube_36x18": lambda: W.shock_tube_2d((36, 18)),
+    "smooth_2d_48": lambda: W.smooth_2d(48),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("lim", [0, 1, 2])
+def test_residual_parity(orc, case, lim):
+    w = CASES[case]()
+    if lim == 0 and case == "blast_24":
+        pytest.skip("the unlimited scheme is not defined near vacuum (negative pressures)")
+    P, S = make(orc, w, lim)
+    dt = 0.8 * orc.dt_max(P, w.state)
+    assert S.dt_max() == pytest.approx(orc.dt_max(P, w.state), rel=1e-14)
+    Lr, ts_r, tp_r, nb_r = orc.residual(P, w.state, dt, with_theta=True)
+    Lg, nb_g = S.residual(dt)
+    err, where = max_rel_err(Lg, Lr, 2, w.n)
+    assert err < TOL_STAGE, (err, where)
+    assert nb_g == nb_r
+    if lim:
+        ts_g, tp_g = S.limiter()
+        for a, b in ((ts_g, ts_r), (tp_g, tp_r)):
+            ok, nbad, tied = fire_sets_agree(a, b)
+            assert ok, (nbad, tied[:10])
+            assert np.abs(a - b).max() < 1e-10
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_one_step_parity(orc, case):
+    w = CASES[case]()
+    P, S = make(orc, w, 2)
+    dt = orc.dt_max(P, w.state)
+    s = w.state.copy()
+    rc, taken, halv = orc.step(P, s, dt)
+    taken_g, halv_g = S.step(dt)
+    assert rc == 0
+    assert halv_g == halv and taken_g == taken
+    err, where = max_rel_err(S.get_state(), s, 2, w.n)
+    assert err < TOL_STAGE, (err, where)
+
+
+@pytest.mark.parametrize("case", ["periodic_ragged_33x17", "walls_16x8", "blast_24"])
+def test_hundred_steps_parity(orc, case):
+    w = CASES[case]()
+    P, S = make(orc, w, 2)
+    s = w.state.copy()
+    rc, ns, nr = orc.advance(P, s, 0.0, 1e9, max_steps=100)
+    assert rc == 0 and ns == 100
+    t_end = 0.0
+    restarts = 0
+    for _ in range(100):
+        dt, h = S.step(0.0)
+        t_end += dt
+        restarts += h
+    assert restarts == nr
+    err, where = max_rel_err(S.get_state(), s, 2, w.n)
+    assert err < TOL_100, (err, where)
+
+
+def test_advance_matches_oracle_to_t_end(orc):
+    w = W.random_smooth_2d((24, 16), seed=9)
+    P, S = make(orc, w, 2)
+    s = w.state.copy()
+    rc, ns, nr = orc.advance(P, s, 0.0, 0.05)
+    ns_g, nr_g = S.advance(0.05)
+    assert rc == 0 and (ns_g, nr_g) == (ns, nr)
+    err, _ = max_rel_err(S.get_state(), s, 2, w.n)
+    assert err < 1e-11
+
+
+def test_full_size_residual_parity(orc):
+    """Full size (1024^2, the benchmark configuration), every DoF compared."""
+    w = W.smooth_2d(1024)
+    P, S = make(orc, w, 2)
+    dt = S.dt_max()
+    Lr, ts_r, tp_r, nb_r = orc.residual(P, w.state, dt, with_theta=True)
+    Lg, nb_g = S.residual(dt)
+    err, where = max_rel_err(Lg, Lr, 2, w.n)
+    assert err < TOL_STAGE, (err, where)
+    ts_g, tp_g = S.limiter()
+    assert fire_sets_agree(ts_g, ts_r)[0] and fire_sets_agree(tp_g, tp_r)[0]
+
+
+def test_full_size_translation_and_conservation(orc):
+    """Properties at full size: shifting a periodic state by one cell shifts the
+    result bit for bit (tile borders are invisible), and the cell-average
+    residual sums to zero to roundoff (conservation)."""
+    n = 1024
+    w = W.smooth_2d(n)
+    _, S = make(orc, w, 2)
+    dt = S.dt_max()
+    L1, _ = S.residual(dt)
+    sites = W.split_sites(w.state, 2, n, n)
+
+    def shift(a, pt):
+        core = a[..., :-1] if pt else a
+        core = np.roll(core, 1, axis=-1)
+        return np.concatenate([core, core[..., :1]], axis=-1) if pt else core
+
+    s2 = np.concatenate([shift(sites[0], False).ravel(), shift(sites[1], True).ravel(),
+                         shift(sites[2], False).ravel(), shift(sites[3], True).ravel()])
+    S.set_state(s2)
+    L2, _ = S.residual(dt)
+    l1 = W.split_sites(L1, 2, n, n)
+    l2 = W.split_sites(L2, 2, n, n)
+    for k, pt in enumerate([False, True, False, True]):
+        assert np.array_equal(shift(l1[k], pt), l2[k])
+    tot = l1[0].sum(axis=(1, 2))
+    scale = np.abs(l1[0]).max(axis=(1, 2)) * n * n
+    assert np.all(np.abs(tot) < 1e-13 * scale)
+
+
+def test_invalid_states_rejected():
+    from paper_2609_29081_b300 import AfnsError, Solver
+    w = W.random_smooth_2d((8, 8), seed=1)
+    S = Solver.from_workload(w)
+    with pytest.raises(AfnsError) as e:
+        S.step(0.0)
+    assert e.value.status == 5
+    bad = w.state.copy()
+    bad[3] = -1.0     # a negative density
+    with pytest.raises(AfnsError) as e:
+        S.set_state(bad)
+    assert e.value.status == 1
+    bad = w.state.copy()
+    sites = W.split_sites(bad, 2, 8, 8)
+    sites[1][0, 0, -1] += 1e-3     # periodic duplicate differs
+    with pytest.raises(AfnsError) as e:
+        S.set_state(bad)
+    assert e.value.status == 1
+    bad = w.state.copy()
+    bad[10] = np.nan
+    with pytest.raises(AfnsError):
+        S.set_state(bad)
+    S.set_state(w.state)
+    S.step(0.0)
+
+
+def test_device_state_roundtrip():
+    import torch
+    from paper_2609_29081_b300 import Solver
+    w = W.random_smooth_2d((20, 12), seed=2, bc=(1, 1, 2, 2))
+    w.state[:] = w.state  # noqa
+    S = Solver.from_workload(w)
+    dev = torch.from_numpy(w.state).cuda()
+    S.set_state(dev, t=0.25)
+    out = torch.empty_like(dev)
+    S.get_state(out)
+    assert torch.equal(out, dev) and S.t == 0.25
