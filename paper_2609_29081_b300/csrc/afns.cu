@@ -22,6 +22,17 @@ cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, d
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st);
 cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st);
+cudaError_t launch_ghost1d_fp64(const Layout &L, double *buf, cudaStream_t st);
+cudaError_t launch_stage1d_fp64(const StageArgs &A, cudaStream_t st);
+cudaError_t launch_dt1d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
+                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
+cudaError_t launch_validate1d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st);
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, cudaStream_t st);
+cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
+cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
+                            double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
+cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st);
+cudaError_t launch_to_f64(const Layout &L, const float *src, double *dst, int use_lo, cudaStream_t st);
 
 __global__ void k_set_ctl(Ctl *ctl, double dt, double t, double t_end)
 {
@@ -65,6 +76,8 @@ struct afns_ctx {
     char *ws = nullptr;
     bool own_ws = false;
     void *U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // u^n, u1/u3/u5, u2/acc, u4, residual
+    double *stage64 = nullptr;   // FP64 staging state of the mixed path
+    bool mixed = false;
     Ctl *ctl = nullptr;
     Ctl *h_ctl = nullptr;   // pinned mirror
     double *partial = nullptr;
@@ -117,7 +130,7 @@ static void make_layout(const af_grid *g, const int *bc, Layout *L)
 }
 
 struct WsPlan {
-    size_t state, ctl, partial, theta, flag, total;
+    size_t state, stage64, ctl, partial, theta, flag, total;
     int nparts;
     size_t nfaces;
 };
@@ -134,7 +147,9 @@ static WsPlan plan_ws(const Layout &L, const af_opts *o)
     p.nfaces = L.dim == 2 ? (size_t)(L.n1 + 1) * L.n2 + (size_t)L.n1 * (L.n2 + 1) : (size_t)L.n1 + 1;
     p.theta = align256(sizeof(double) * 2 * p.nfaces);
     p.flag = align256(sizeof(int) * 4);
-    p.total = 5 * p.state + p.ctl + p.partial + p.theta + p.flag;
+    // the mixed path converts to / from the FP64 public layout through a staging state
+    p.stage64 = o->precision == AF_MIXED ? align256((size_t)L.nsite * L.nc * (size_t)L.plane * sizeof(double)) : 0;
+    p.total = 5 * p.state + p.stage64 + p.ctl + p.partial + p.theta + p.flag;
     return p;
 }
 
@@ -157,8 +172,8 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
     if (o->limiter < 0 || o->limiter > 2) return *why = "unknown limiter", AF_EINVAL;
     if (!(o->cfl_c > 0) || !(o->cfl_v > 0) || !(o->eps > 0) || o->max_halvings < 0)
         return *why = "bad CFL numbers, eps or max_halvings", AF_EINVAL;
-    if (g->dim == 1) return *why = "the 1D path is not available in this build", AF_EINVAL;
-    if (o->precision == AF_MIXED) return *why = "the mixed-precision path is not available in this build", AF_EINVAL;
+    if (o->precision == AF_MIXED && g->dim == 1)
+        return *why = "the mixed-precision path is two-dimensional only", AF_EINVAL;
     return AF_OK;
 }
 
@@ -241,6 +256,10 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     char *q = c->ws;
     c->state_bytes = p.state;
     for (int k = 0; k < 5; ++k) c->U[k] = q, q += p.state;
+    c->mixed = opts->precision == AF_MIXED;
+    c->L.comp = c->mixed ? 1 : 0;
+    c->stage64 = c->mixed ? (double *)q : nullptr;
+    q += p.stage64;
     c->ctl = (Ctl *)q;
     q += p.ctl;
     c->partial = (double *)q;
@@ -307,11 +326,47 @@ af_status af_sizes(const afns_ctx *c, size_t *cells, size_t *faces, size_t *site
 
 }  // extern "C"
 
-// Width/height of site s (2D).
+// Width/height of site s.
 static void site_dims(const afns_ctx *c, int s, int *w, int *h)
 {
+    if (c->dim == 1) {
+        *w = s == 1 ? c->n1 + 1 : c->n1;
+        *h = 1;
+        return;
+    }
     *w = (s == 1 || s == 3) ? c->n1 + 1 : c->n1;
     *h = (s == 2 || s == 3) ? c->n2 + 1 : c->n2;
+}
+
+// Kernel dispatch by dimension.
+static cudaError_t do_ghost(afns_ctx *c, void *buf)
+{
+    if (c->dim == 1) {
+        c->launches += 1;
+        return launch_ghost1d_fp64(c->L, (double *)buf, c->st);
+    }
+    c->launches += 2;
+    if (c->mixed) return launch_ghost2d_f32(c->L, (float *)buf, c->st);
+    return launch_ghost2d_fp64(c->L, (double *)buf, c->st);
+}
+
+static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
+{
+    c->launches += 1;
+    if (c->dim == 1) return launch_stage1d_fp64(A, c->st);
+    if (c->mixed) return launch_stage2d_mixed(A, c->opts.tile_x, c->opts.tile_y, c->st);
+    return launch_stage2d_fp64(A, c->opts.tile_x, c->opts.tile_y, c->st);
+}
+
+// Public FP64 site arrays <-> state buffer. The FP64 path copies directly; the
+// mixed path goes through the FP64 staging state and a conversion kernel.
+static af_status sites_in(afns_ctx *c, void *buf, double *const site[4], int on_device);
+static af_status sites_out(afns_ctx *c, void *buf, double *const site[4], int on_device, int use_lo);
+
+static cudaError_t do_validate(afns_ctx *c, const void *buf)
+{
+    if (c->dim == 1) return launch_validate1d_fp64(c->L, (const double *)buf, c->gamma, c->flag, c->st);
+    return launch_validate2d_fp64(c->L, (const double *)buf, c->gamma, c->flag, c->st);
 }
 
 // Copy between the public site arrays and a padded state buffer (dir 0: in, 1: out).
@@ -322,7 +377,7 @@ static af_status copy_sites(afns_ctx *c, void *buf, double *const site[4], int o
         int w, h;
         site_dims(c, s, &w, &h);
         for (int comp = 0; comp < c->L.nc; ++comp) {
-            double *dev = (double *)buf + plane_of(c->L, s, comp) + cell_off(c->L, 0, 0);
+            double *dev = (double *)buf + plane_of(c->L, s, comp) + (c->dim == 2 ? cell_off(c->L, 0, 0) : 2);
             double *host = site[s] + (size_t)comp * w * h;
             cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
             cudaError_t e = dir == 0 ? cudaMemcpy2DAsync(dev, c->L.pitch * sizeof(double), host, w * sizeof(double),
@@ -335,14 +390,31 @@ static af_status copy_sites(afns_ctx *c, void *buf, double *const site[4], int o
     return AF_OK;
 }
 
+static af_status sites_in(afns_ctx *c, void *buf, double *const site[4], int on_device)
+{
+    void *dst = c->mixed ? (void *)c->stage64 : buf;
+    af_status s = copy_sites(c, dst, site, on_device, 0);
+    if (s != AF_OK) return s;
+    cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
+    if (e == cudaSuccess) e = do_validate(c, dst);
+    if (e == cudaSuccess && c->mixed) e = launch_to_f32(c->L, c->stage64, (float *)buf, c->st);
+    return cuda_check(c, e, "state upload");
+}
+
+static af_status sites_out(afns_ctx *c, void *buf, double *const site[4], int on_device, int use_lo)
+{
+    if (!c->mixed) return copy_sites(c, buf, site, on_device, 1);
+    cudaError_t e = launch_to_f64(c->L, (const float *)buf, c->stage64, use_lo, c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "state conversion");
+    return copy_sites(c, c->stage64, site, on_device, 1);
+}
+
 extern "C" af_status af_set_state(afns_ctx *c, const double *const site[4], int on_device, double t)
 {
     if (!c || !site) return fail(c, AF_EINVAL, "null argument");
-    af_status s = copy_sites(c, c->U[0], const_cast<double *const *>(site), on_device, 0);
+    af_status s = sites_in(c, c->U[0], const_cast<double *const *>(site), on_device);
     if (s != AF_OK) return s;
-    cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
-    if (e == cudaSuccess) e = launch_validate2d_fp64(c->L, (const double *)c->U[0], c->gamma, c->flag, c->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    cudaError_t e = cudaMemcpyAsync(c->h_flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_check(c, e, "af_set_state");
     if (*c->h_flag & 1) return fail(c, AF_EINVAL, "state has a DoF outside G (rho <= 0, p <= 0 or not finite)");
@@ -356,9 +428,9 @@ extern "C" af_status af_get_state(afns_ctx *c, double *const site[4], int on_dev
 {
     if (!c || !site) return fail(c, AF_EINVAL, "null argument");
     if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
-    cudaError_t e = launch_ghost2d_fp64(c->L, (double *)c->U[0], c->st);
+    cudaError_t e = do_ghost(c, c->U[0]);
     if (e != cudaSuccess) return cuda_check(c, e, "ghost fill");
-    af_status s = copy_sites(c, c->U[0], site, on_device, 1);
+    af_status s = sites_out(c, c->U[0], site, on_device, 1);
     if (s != AF_OK) return s;
     e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_check(c, e, "af_get_state");
@@ -383,9 +455,8 @@ static StageArgs base_args(afns_ctx *c)
 // One fused stage: ghost fill of the input, then the stage kernel.
 static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &k, double *theta)
 {
-    cudaError_t e = launch_ghost2d_fp64(c->L, (double *)in, c->st);
+    cudaError_t e = do_ghost(c, in);
     if (e != cudaSuccess) return e;
-    c->launches += 2;
     StageArgs A = base_args(c);
     A.uin = in;
     A.u0 = c->U[0];
@@ -395,9 +466,8 @@ static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &
     A.k = k;
     bool prof = c->profiling && c->ev_used < 5;
     if (prof) cudaEventRecord(c->ev[c->ev_used][0], c->st);
-    e = launch_stage2d_fp64(A, c->opts.tile_x, c->opts.tile_y, c->st);
+    e = do_stage(c, A);
     if (prof) cudaEventRecord(c->ev[c->ev_used++][1], c->st);
-    c->launches += 1;
     c->stage_launches += 1;
     return e;
 }
@@ -475,6 +545,12 @@ static af_status step_from_ctl(afns_ctx *c, double *dt_taken, int *halvings)
 static cudaError_t launch_dt(afns_ctx *c, int clip)
 {
     c->launches += 2;
+    if (c->dim == 1)
+        return launch_dt1d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+                                c->partial, c->nparts, c->ctl, clip, c->st);
+    if (c->mixed)
+        return launch_dt2d_f32(c->L, (const float *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+                               c->partial, c->nparts, c->ctl, clip, c->st);
     return launch_dt2d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
                             c->partial, c->nparts, c->ctl, clip, c->st);
 }
@@ -540,9 +616,9 @@ extern "C" af_status af_residual(afns_ctx *c, double dt, double *const Lout[4], 
     StageCoef k{};
     k.residual = 1;
     cudaError_t e = run_stage(c, c->U[0], c->U[4], k, c->theta);
-    if (e == cudaSuccess) e = launch_ghost2d_fp64(c->L, (double *)c->U[4], c->st);   // periodic duplicates
+    if (e == cudaSuccess) e = do_ghost(c, c->U[4]);   // periodic duplicates
     if (e != cudaSuccess) return cuda_check(c, e, "residual");
-    af_status s = copy_sites(c, c->U[4], Lout, on_device, 1);
+    af_status s = sites_out(c, c->U[4], Lout, on_device, 0);
     if (s != AF_OK) return s;
     s = read_ctl(c);
     if (s != AF_OK) return s;

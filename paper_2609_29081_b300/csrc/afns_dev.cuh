@@ -127,4 +127,38 @@ __device__ __forceinline__ R dmin(R a, R b)
     return a < b ? a : b;
 }
 
+// --- float-float ("double-single") arithmetic for the compensated cell-average
+// accumulation of the mixed-precision path: a value is hi + lo with |lo| <= ulp(hi)/2.
+struct ff {
+    float h, l;
+};
+__device__ __forceinline__ ff ff_quick(float a, float b)
+{
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = ff_two_sum(a.h, b.h);
+    return ff_quick(s.h, s.l + a.l + b.l);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    return ff_quick(p, e);
+}
+__device__ __forceinline__ ff ff_from(double x)
+{
+    float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+
 }  // namespace afns

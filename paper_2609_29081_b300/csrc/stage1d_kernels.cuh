@@ -1,0 +1,410 @@
+// stage1d_kernels.cuh -- 1D device code of libafns: ghost fill, fused RK stage,
+// CFL reduction and validation for the 1D system (rho, rho u, E) of Sec. 2.1.
+//
+// Layout: planes (site, component) with site 0 = cell average, 1 = interface
+// point; element i at offset i + 2 (two ghost cells / points each side).
+// One CTA owns TX cells; its half lattice (points at even, centres at odd lattice
+// indices, two nodes of halo) lives in shared memory. Phases as in 2D:
+// load, centres (Sec. 2.1 Simpson inversion + Remark 3.1 scaling), primitives,
+// D_c gradients (Eq. (8)), point residual (Eq. (6b)) with the point scaling
+// limiter (Sec. 3.4) and RK combination, low-order cell quantities (Sec. 3.1,
+// 3.2), face fluxes with both limiters (Eqs. (19)-(22), Sec. 3.3), cell
+// residual (Eq. (6a)) and RK combination.
+#pragma once
+
+#include "stage2d.cuh"
+
+namespace afns {
+
+__host__ __device__ __forceinline__ long long off1(int i) { return (long long)i + 2; }
+
+template <int TX>
+struct Tile1 {
+    static constexpr int LX = 2 * TX + 5;     // lattice nodes with halo
+    static constexpr int CX = TX + 4;         // cells with 2 halo
+    static constexpr int QX = TX + 2;         // cells with 1 halo
+    static constexpr int NF = TX + 1;         // faces
+    static constexpr int oU = 0;              // 3 x LX
+    static constexpr int oQ = oU + 3 * LX;    // u, T, c
+    static constexpr int oG = oQ + 3 * LX;    // du/dx, dT/dx
+    static constexpr int oA = oG + 2 * LX;    // 3 x CX
+    static constexpr int oAW = oA + 3 * CX;   // u, p, T of averages
+    static constexpr int oCQ = oAW + 3 * CX;  // 7 x QX: F(3), rho_x, b_x, phi1, phi2
+    static constexpr int oF = oCQ + 7 * QX;   // 3 x NF
+    static constexpr int total = oF + 3 * NF;
+};
+
+template <class S>
+__global__ void k_ghost1d(Layout L, S *buf)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 10) return;
+    int site = t / 5, g = t % 5;
+    int i = g < 2 ? g - 2 : L.n1 + (g - 2);
+    int side;
+    int si = ghost_image(i, L.n1, site == 1, L.bc[0], L.bc[1], &side);
+    if (side < 0) return;
+    int kind = L.bc[side];
+    for (int c = 0; c < 3; ++c) {
+        S v = buf[plane_of(L, site, c) + off1(si)];
+        buf[plane_of(L, site, c) + off1(i)] = mirror_sign(kind, 0, c, 1) < 0 ? -v : v;
+    }
+}
+
+__device__ __forceinline__ bool admissible1(const double *U, double gm1)
+{
+    if (!(U[0] > 0.0)) return false;
+    double p = gm1 * (U[2] - U[1] * U[1] / (2.0 * U[0]));
+    return isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && p > 0.0;
+}
+
+// 1D LLF total flux between lattice nodes A < B (Sec. 3.4 low-order point update).
+template <class R, int TX>
+__device__ void lattice_llf1(const R *sm, int A, int B, double dx, double gamma, double mu, double ka, double F[3])
+{
+    using T = Tile1<TX>;
+    const R *U = sm + T::oU;
+    const R *qu = sm + T::oQ, *qT = qu + T::LX;
+    double Fs[2][3], Us[2][3], rs[2], bs[2];
+    const double gm1 = gamma - 1.0;
+    for (int s = 0; s < 2; ++s) {
+        int n = s == 0 ? A : B;
+        double Uv[3] = {(double)U[n], (double)U[T::LX + n], (double)U[2 * T::LX + n]};
+        double ux = ((double)qu[n + 1] - (double)qu[n - 1]) / dx;
+        double Tx = ((double)qT[n + 1] - (double)qT[n - 1]) / dx;
+        double rho = Uv[0], u = Uv[1] / rho;
+        double p = gm1 * (Uv[2] - Uv[1] * Uv[1] / (2.0 * rho));
+        double tau = 4.0 / 3.0 * mu * ux;
+        double q = -ka * Tx;
+        Fs[s][0] = Uv[1];
+        Fs[s][1] = Uv[1] * u + p - tau;
+        Fs[s][2] = (Uv[2] + p) * u - (u * tau - q);
+        for (int c = 0; c < 3; ++c) Us[s][c] = Uv[c];
+        rs[s] = fabs(u) + sqrt(gamma * p / rho);
+        double re = p / gm1;
+        bs[s] = (sqrt(rho * rho * q * q + 2.0 * rho * re * tau * tau) + rho * fabs(q)) / (2.0 * rho * re);
+    }
+    double lam = fmax(rs[0], rs[1]) + fmax(bs[0], bs[1]);
+    for (int c = 0; c < 3; ++c) F[c] = 0.5 * (Fs[0][c] + Fs[1][c]) - 0.5 * lam * (Us[1][c] - Us[0][c]);
+}
+
+template <class R, class S, int TX>
+__global__ void __launch_bounds__(128) k_stage1d(StageArgs A)
+{
+    using T = Tile1<TX>;
+    constexpr int LX = T::LX, CX = T::CX, QX = T::QX;
+    extern __shared__ __align__(16) unsigned char smem_raw1[];
+    R *sm = reinterpret_cast<R *>(smem_raw1);
+    __shared__ int s_bad;
+    const Layout &L = A.L;
+    const int i0 = blockIdx.x * TX;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int ntx = min(TX, L.n1 - i0);
+    if (tid == 0) s_bad = 0;
+    const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0), mu = (R)A.mu, ka = (R)A.kappa;
+    const R dx = (R)L.dx;
+    const double dt = A.ctl->dt;
+    const double eps = A.eps;
+    R *sU = sm + T::oU, *sQ = sm + T::oQ, *sG = sm + T::oG, *sA = sm + T::oA, *sAW = sm + T::oAW;
+    R *sCQ = sm + T::oCQ, *sF = sm + T::oF;
+
+    // P0: load
+    for (int t = tid; t < LX; t += nth) {
+        int a = 2 * i0 - 2 + t;
+        if (a & 1) continue;
+        int i = a >> 1;
+        bool inb = i <= L.n1 + 2;
+        for (int c = 0; c < 3; ++c)
+            sU[c * LX + t] = inb ? (R)ld<S>(A.uin, plane_of(L, 1, c) + off1(i)) : (c == 0 ? R(1) : c == 2 ? R(2.5) : R(0));
+    }
+    for (int t = tid; t < CX; t += nth) {
+        int i = i0 - 2 + t;
+        bool inb = i <= L.n1 + 2;
+        for (int c = 0; c < 3; ++c)
+            sA[c * CX + t] = inb ? (R)ld<S>(A.uin, plane_of(L, 0, c) + off1(i)) : (c == 0 ? R(1) : c == 2 ? R(2.5) : R(0));
+    }
+    __syncthreads();
+
+    // P1: centres U_i = (6 Ubar_i - (U_{i-1/2} + U_{i+1/2})) / 4 + scaling limiter
+    for (int t = tid; t < QX; t += nth) {
+        int n = 2 * t + 1, ca = t + 1;
+        R Uc[3];
+        for (int c = 0; c < 3; ++c) Uc[c] = (R(6) * sA[c * CX + ca] - (sU[c * LX + n - 1] + sU[c * LX + n + 1])) / R(4);
+        if (A.limiter != LIM_NONE) {
+            R pc = gm1 * (Uc[2] - Uc[1] * Uc[1] / (R(2) * Uc[0]));
+            if (!(Uc[0] >= (R)eps) || !(pc >= (R)eps)) {
+                double Ub[3], Ud[3], Ur[3];
+                for (int c = 0; c < 3; ++c) Ub[c] = (double)sA[c * CX + ca], Ud[c] = (double)Uc[c];
+                double g1 = A.gamma - 1.0;
+                double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
+                for (int c = 0; c < 3; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
+                double pL = g1 * (Ub[2] - Ub[1] * Ub[1] / (2.0 * Ub[0]));
+                double pH = g1 * (Ur[2] - Ur[1] * Ur[1] / (2.0 * Ur[0]));
+                double th = thr * theta_fn(pL, pH, fmin(eps, pL));
+                for (int c = 0; c < 3; ++c) Uc[c] = (R)((1.0 - th) * Ub[c] + th * Ud[c]);
+            }
+        }
+        for (int c = 0; c < 3; ++c) sU[c * LX + n] = Uc[c];
+    }
+    __syncthreads();
+
+    // P2: primitives
+    for (int t = tid; t < LX; t += nth) {
+        R rho = sU[t], m = sU[LX + t], E = sU[2 * LX + t];
+        R p = gm1 * (E - m * m / (R(2) * rho));
+        sQ[t] = m / rho;
+        sQ[LX + t] = p / rho;
+        sQ[2 * LX + t] = sqrt(gam * p / rho);
+    }
+    for (int t = tid; t < CX; t += nth) {
+        R rho = sA[t], m = sA[CX + t], E = sA[2 * CX + t];
+        R p = gm1 * (E - m * m / (R(2) * rho));
+        sAW[t] = m / rho;
+        sAW[CX + t] = p;
+        sAW[2 * CX + t] = p / rho;
+    }
+    __syncthreads();
+
+    // P3: D_c gradients of u and T
+    {
+        const R i6x = R(1) / (R(6) * dx);
+        for (int t = tid + 2; t < LX - 2; t += nth) {
+            for (int c = 0; c < 2; ++c) {
+                const R *z = sQ + c * LX;
+                sG[c * LX + t] = (z[t - 2] - R(8) * z[t - 1] + R(8) * z[t + 1] - z[t + 2]) * i6x;
+            }
+        }
+    }
+    __syncthreads();
+
+    // P4: point residual (Eq. (6b)), scaling limiter, combination, store
+    {
+        const bool last = i0 + ntx == L.n1, per = L.bc[0] == BC_PERIODIC;
+        const int tot = ntx + ((last && !per) ? 1 : 0);
+        const double w = A.k.residual ? 1.0 : A.k.cl * dt;
+        const R inv6 = R(1) / (R(6) * dx), i3h2 = R(1) / (R(3) * dx * dx), mu43 = R(4) / R(3) * mu;
+        const R *qu = sQ, *qT = sQ + LX, *qc = sQ + 2 * LX;
+        for (int t = tid; t < tot; t += nth) {
+            const int n = 2 + 2 * t;
+            R al = 0;
+            for (int k = -2; k <= 2; ++k) al = dmax(al, fabs(qu[n + k]) + qc[n + k]);
+            R f[3] = {0, 0, 0};
+            for (int k = -2; k <= 2; ++k) {
+                int m = n + k;
+                R rho = sU[m], mm = sU[LX + m], E = sU[2 * LX + m];
+                R p = rho * qT[m], u = qu[m];
+                R wc = (R)kDC[k + 2], w4 = al * (R)kD4[k + 2];
+                f[0] += wc * mm + w4 * rho;
+                f[1] += wc * (mm * u + p) + w4 * mm;
+                f[2] += wc * ((E + p) * u) + w4 * E;
+            }
+            R r0 = -f[0] * inv6, r1 = -f[1] * inv6, r2 = -f[2] * inv6;
+            R d2u = 0, d2T = 0, eq = 0;
+            for (int k = -2; k <= 2; ++k) {
+                d2u += (R)kD2[k + 2] * qu[n + k];
+                d2T += (R)kD2[k + 2] * qT[n + k];
+                R bu = 0;
+                for (int q = -2; q <= 2; ++q) bu += (R)kB[k + 2][q + 2] * qu[n + q];
+                eq += mu43 * qu[n + k] * bu;
+            }
+            r1 += mu43 * d2u * i3h2;
+            r2 += ka * d2T * i3h2 + R(4) / (dx * dx) * eq;
+            double res[3] = {(double)r0, (double)r1, (double)r2};
+            double U[3] = {(double)sU[n], (double)sU[LX + n], (double)sU[2 * LX + n]};
+            if (A.limiter != LIM_NONE) {
+                double UH[3];
+                for (int c = 0; c < 3; ++c) UH[c] = U[c] + dt * res[c];
+                double gd = A.gamma - 1.0;
+                double pH = gd * (UH[2] - UH[1] * UH[1] / (2.0 * UH[0]));
+                if (!(UH[0] >= eps) || !(pH >= eps)) {
+                    double UL[3] = {U[0], U[1], U[2]}, Fr[3], Fl[3];
+                    lattice_llf1<R, TX>(sm, n, n + 1, L.dx, A.gamma, A.mu, A.kappa, Fr);
+                    lattice_llf1<R, TX>(sm, n - 1, n, L.dx, A.gamma, A.mu, A.kappa, Fl);
+                    double rr = dt / (0.5 * L.dx);
+                    for (int c = 0; c < 3; ++c) UL[c] -= rr * (Fr[c] - Fl[c]);
+                    if (!admissible1(UL, gd)) s_bad = 1;
+                    double thr = theta_fn(UL[0], UH[0], fmin(eps, UL[0]));
+                    double Ur[3];
+                    for (int c = 0; c < 3; ++c) Ur[c] = (1.0 - thr) * UL[c] + thr * UH[c];
+                    double pL = gd * (UL[2] - UL[1] * UL[1] / (2.0 * UL[0]));
+                    double pr = gd * (Ur[2] - Ur[1] * Ur[1] / (2.0 * Ur[0]));
+                    double th = thr * theta_fn(pL, pr, fmin(eps, pL));
+                    for (int c = 0; c < 3; ++c) res[c] = ((1.0 - th) * UL[c] + th * UH[c] - U[c]) / dt;
+                }
+            }
+            int i = i0 + t;
+            double o[3];
+            for (int c = 0; c < 3; ++c) {
+                long long po = plane_of(L, 1, c) + off1(i);
+                double v = A.k.residual ? 0.0 : A.k.a1 * U[c];
+                if (A.k.a0 != 0.0) v += A.k.a0 * ld<S>(A.u0, po);
+                if (A.k.a2 != 0.0) v += A.k.a2 * ld<S>(A.aux, po);
+                o[c] = v + w * res[c];
+                if (A.k.acc) ((S *)A.aux)[po] = (S)(A.k.b2 * ld<S>(A.aux, po) + A.k.b1 * U[c] + A.k.bl * dt * res[c]);
+            }
+            if (A.k.wall_fix) {
+                for (int side = 0; side < 2; ++side) {
+                    int kind = L.bc[side];
+                    if (kind != BC_WALL && kind != BC_SYMMETRY) continue;
+                    if (i != (side ? L.n1 : 0)) continue;
+                    double ke0 = o[1] * o[1];
+                    o[1] = 0.0;
+                    o[2] -= ke0 / (2.0 * o[0]);
+                }
+            }
+            for (int c = 0; c < 3; ++c) ((S *)A.out)[plane_of(L, 1, c) + off1(i)] = (S)o[c];
+        }
+    }
+
+    // P5a: low-order cell quantities on cells [i0-1, i0+TX]
+    for (int t = tid; t < QX; t += nth) {
+        int ca = t + 1;
+        const R *Au = sAW, *Ap = sAW + CX, *AT = sAW + 2 * CX;
+        R rho = sA[ca], m = sA[CX + ca], E = sA[2 * CX + ca];
+        R u = Au[ca], p = Ap[ca];
+        R i2x = R(1) / (R(2) * dx);
+        R ux = (Au[ca + 1] - Au[ca - 1]) * i2x, Tx = (AT[ca + 1] - AT[ca - 1]) * i2x;
+        R tau = R(4) / R(3) * mu * ux, q = -ka * Tx;
+        R *Q = sCQ + t;
+        Q[0] = m;
+        Q[QX] = m * u + p - tau;
+        Q[2 * QX] = (E + p) * u - (u * tau - q);
+        Q[3 * QX] = fabs(u) + sqrt(gam * p / rho);
+        R re = p / gm1;
+        Q[4 * QX] = (sqrt(rho * rho * q * q + R(2) * rho * re * tau * tau) + rho * fabs(q)) / (R(2) * rho * re);
+        Q[5 * QX] = fabs(Ap[ca + 1] - R(2) * p + Ap[ca - 1]) / fabs(Ap[ca + 1] + R(2) * p + Ap[ca - 1]);
+        R ph2 = -ux / sqrt(ux * ux + R(1e-13));
+        Q[6 * QX] = dmax(ph2, R(0));
+    }
+    __syncthreads();
+
+    // P5b: faces f in [i0, i0 + ntx]
+    for (int t = tid; t <= ntx; t += nth) {
+        const int n = 2 + 2 * t;
+        R rho = sU[n], m = sU[LX + n], E = sU[2 * LX + n];
+        R u = sQ[n], p = rho * sQ[LX + n];
+        R ux = sG[n], Tx = sG[LX + n];
+        R tau = R(4) / R(3) * mu * ux;
+        R FH[3] = {m, m * u + p - tau, (E + p) * u - (u * tau + ka * Tx)};
+        double Fo[3], ts = 1.0, tpp = 1.0;
+        if (A.limiter == LIM_NONE) {
+            for (int c = 0; c < 3; ++c) Fo[c] = FH[c];
+        } else {
+            const int qL = t, qR = t + 1, aL = t + 1, aR = t + 2;
+            double FLc[3], FRc[3], UbL[3], UbR[3];
+            for (int c = 0; c < 3; ++c) {
+                FLc[c] = sCQ[c * QX + qL];
+                FRc[c] = sCQ[c * QX + qR];
+                UbL[c] = sA[c * CX + aL];
+                UbR[c] = sA[c * CX + aR];
+            }
+            double lam = fmax((double)sCQ[3 * QX + qL], (double)sCQ[3 * QX + qR]) +
+                         fmax((double)sCQ[4 * QX + qL], (double)sCQ[4 * QX + qR]);
+            if (A.limiter == LIM_S_PP) {
+                double p1 = fmax((double)sCQ[5 * QX + qL], (double)sCQ[5 * QX + qR]);
+                double p2 = fmax((double)sCQ[6 * QX + qL], (double)sCQ[6 * QX + qR]);
+                ts = exp(-A.c_s * p1 * p2);
+            }
+            double FL[3], FLs[3], dF[3];
+            for (int c = 0; c < 3; ++c) {
+                FL[c] = 0.5 * (FLc[c] + FRc[c]) - 0.5 * lam * (UbR[c] - UbL[c]);
+                FLs[c] = FL[c] + ts * ((double)FH[c] - FL[c]);
+                dF[c] = FLs[c] - FL[c];
+            }
+            const double kk = 2.0 * dt / L.dx, g1 = A.gamma - 1.0;
+            double ULp[3], UHp[3], ULm[3], UHm[3];
+            for (int c = 0; c < 3; ++c) {
+                ULp[c] = UbL[c] - kk * (FL[c] - FLc[c]);
+                UHp[c] = UbL[c] - kk * (FLs[c] - FLc[c]);
+                ULm[c] = UbR[c] - kk * (FRc[c] - FL[c]);
+                UHm[c] = UbR[c] - kk * (FRc[c] - FLs[c]);
+            }
+            if (!admissible1(ULp, g1) || !admissible1(ULm, g1)) s_bad = 1;
+            double thr = fmin(theta_fn(ULp[0], UHp[0], fmin(eps, ULp[0])), theta_fn(ULm[0], UHm[0], fmin(eps, ULm[0])));
+            double Urp[3], Urm[3];
+            for (int c = 0; c < 3; ++c) {
+                Urp[c] = (1.0 - thr) * ULp[c] + thr * UHp[c];
+                Urm[c] = (1.0 - thr) * ULm[c] + thr * UHm[c];
+            }
+            double pLp = g1 * (ULp[2] - ULp[1] * ULp[1] / (2.0 * ULp[0]));
+            double pLm = g1 * (ULm[2] - ULm[1] * ULm[1] / (2.0 * ULm[0]));
+            double prp = g1 * (Urp[2] - Urp[1] * Urp[1] / (2.0 * Urp[0]));
+            double prm = g1 * (Urm[2] - Urm[1] * Urm[1] / (2.0 * Urm[0]));
+            double thp = fmin(theta_fn(pLp, prp, fmin(eps, pLp)), theta_fn(pLm, prm, fmin(eps, pLm)));
+            tpp = thr * thp;
+            for (int c = 0; c < 3; ++c) Fo[c] = FL[c] + tpp * dF[c];
+        }
+        for (int c = 0; c < 3; ++c) sF[c * T::NF + t] = (R)Fo[c];
+        if (A.theta && (t < ntx || i0 + t == L.n1)) {
+            A.theta[i0 + t] = ts;
+            A.theta[L.n1 + 1 + i0 + t] = tpp;
+        }
+    }
+    __syncthreads();
+
+    // P6: cell residual, combination, store
+    {
+        const double w = A.k.residual ? 1.0 : A.k.cl * dt, idx = 1.0 / L.dx;
+        for (int t = tid; t < ntx; t += nth) {
+            for (int c = 0; c < 3; ++c) {
+                double res = -((double)sF[c * T::NF + t + 1] - (double)sF[c * T::NF + t]) * idx;
+                long long po = plane_of(L, 0, c) + off1(i0 + t);
+                double Uin = sA[c * CX + t + 2];
+                double v = A.k.residual ? 0.0 : A.k.a1 * Uin;
+                if (A.k.a0 != 0.0) v += A.k.a0 * ld<S>(A.u0, po);
+                if (A.k.a2 != 0.0) v += A.k.a2 * ld<S>(A.aux, po);
+                if (A.k.acc) ((S *)A.aux)[po] = (S)(A.k.b2 * ld<S>(A.aux, po) + A.k.b1 * Uin + A.k.bl * dt * res);
+                ((S *)A.out)[po] = (S)(v + w * res);
+            }
+        }
+    }
+    if (tid == 0 && s_bad) atomicOr(&A.ctl->notpp, 1);
+}
+
+template <class S>
+__global__ void k_dt_partial1d(Layout L, const S *buf, double gamma, double mu, double Pr, double cfl_c, double cfl_v,
+                               double *partial)
+{
+    double m1 = 0.0, m2 = 0.0;
+    const double g1 = gamma - 1.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n1; i += gridDim.x * blockDim.x) {
+        double rho = buf[plane_of(L, 0, 0) + off1(i)], m = buf[plane_of(L, 0, 1) + off1(i)];
+        double E = buf[plane_of(L, 0, 2) + off1(i)];
+        double p = g1 * (E - m * m / (2.0 * rho));
+        double c = sqrt(gamma * p / rho);
+        double rv = fmax(4.0 * mu / (3.0 * rho), gamma * mu / (Pr * rho));
+        m1 = fmax(m1, (fabs(m / rho) + c) / (cfl_c * L.dx));
+        m2 = fmax(m2, rv / (cfl_v * L.dx * L.dx));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    __shared__ double s1[32], s2[32];
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s1[wid] = m1, s2[wid] = m2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 1; k < nw; ++k) m1 = fmax(m1, s1[k]), m2 = fmax(m2, s2[k]);
+        partial[2 * blockIdx.x] = m1;
+        partial[2 * blockIdx.x + 1] = m2;
+    }
+}
+
+template <class S>
+__global__ void k_validate1d(Layout L, const S *buf, double gamma, int *flag)
+{
+    int total = L.n1 + L.n1 + 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int site = t < L.n1 ? 0 : 1, i = t < L.n1 ? t : t - L.n1;
+        double U[3];
+        for (int c = 0; c < 3; ++c) U[c] = (double)buf[plane_of(L, site, c) + off1(i)];
+        if (!admissible1(U, gamma - 1.0)) atomicOr(flag, 1);
+        if (site == 1 && i == L.n1 && L.bc[0] == BC_PERIODIC)
+            for (int c = 0; c < 3; ++c)
+                if (buf[plane_of(L, 1, c) + off1(i)] != buf[plane_of(L, 1, c) + off1(0)]) atomicOr(flag, 2);
+    }
+}
+
+}  // namespace afns

@@ -52,6 +52,12 @@ cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, d
     return cudaGetLastError();
 }
 
+cudaError_t launch_dt_final(const double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st)
+{
+    k_dt_final<<<1, 256, 0, st>>>(partial, nparts, ctl, clip);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st) { return launch_ghost2d<double>(L, buf, st); }
 
 cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st)
@@ -59,6 +65,68 @@ cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double ga
     long long total = (long long)(L.n1 + 1) * (L.n2 + 1) * 4;
     int blocks = (int)std::min<long long>((total + 255) / 256, 148 * 16);
     k_validate2d<double><<<blocks, 256, 0, st>>>(L, buf, gamma, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace afns
+
+// ---------------------------------------------------------------------------
+// Mixed precision: FP32 stencils and storage, FP64 islands, float-float averages
+// ---------------------------------------------------------------------------
+namespace afns {
+
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, cudaStream_t st)
+{
+    (void)tx;
+    (void)ty;
+    return launch_stage2d_t<float, float, 16, 8>(A, st);
+}
+
+cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st) { return launch_ghost2d<float>(L, buf, st); }
+
+cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
+                            double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st)
+{
+    k_dt_partial2d<float><<<nparts, 256, 0, st>>>(L, buf, gamma, mu, Pr, cfl_c, cfl_v, partial);
+    return launch_dt_final(partial, nparts, ctl, clip, st);
+}
+
+// FP64 state planes -> FP32 planes; the cell-average planes (the first nc) also
+// get their rounding residue in the compensation planes that follow the nplanes.
+__global__ void k_to_f32(const double *src, float *dst, long long plane, int nplanes, int nc)
+{
+    long long total = plane * nplanes;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        double x = src[e];
+        float h = __double2float_rn(x);
+        dst[e] = h;
+        long long p = e / plane;
+        if (p < nc) dst[(long long)nplanes * plane + e] = __double2float_rn(x - (double)h);
+    }
+}
+
+__global__ void k_to_f64(const float *src, double *dst, long long plane, int nplanes, int nc, int use_lo)
+{
+    long long total = plane * nplanes;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        double x = (double)src[e];
+        long long p = e / plane;
+        if (use_lo && p < nc) x += (double)src[(long long)nplanes * plane + e];
+        dst[e] = x;
+    }
+}
+
+cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st)
+{
+    int np = L.nsite * L.nc;
+    k_to_f32<<<148 * 8, 256, 0, st>>>(src, dst, L.plane, np, L.nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f64(const Layout &L, const float *src, double *dst, int use_lo, cudaStream_t st)
+{
+    int np = L.nsite * L.nc;
+    k_to_f64<<<148 * 8, 256, 0, st>>>(src, dst, L.plane, np, L.nc, use_lo);
     return cudaGetLastError();
 }
 

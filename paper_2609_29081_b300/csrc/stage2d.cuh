@@ -70,6 +70,18 @@ __device__ __constant__ static const double kM[4][4] = {
     {0.0, -1.0 / 24.0, 1.0 / 6.0, -1.0 / 8.0},
 };
 
+// B of Eq. (10) written out (rows m = -2..2, columns n = -2..2), from
+// B = [[0,0],[0,M]] - [[M,0],[0,0]].
+__device__ __constant__ static const double kB[5][5] = {
+    {-1.0 / 8.0, 1.0 / 6.0, -1.0 / 24.0, 0.0, 0.0},
+    {1.0 / 6.0, 1.0 / 2.0, -5.0 / 6.0, 1.0 / 6.0, 0.0},
+    {-1.0 / 8.0, 1.0 / 2.0, -3.0 / 4.0, 1.0 / 2.0, -1.0 / 8.0},
+    {0.0, 1.0 / 6.0, -5.0 / 6.0, 1.0 / 2.0, 1.0 / 6.0},
+    {0.0, 0.0, -1.0 / 24.0, 1.0 / 6.0, -1.0 / 8.0},
+};
+// Column sums of B times 12: the textbook 5-point second difference.
+__device__ __constant__ static const double kD2[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
+
 template <class S>
 __device__ __forceinline__ double ld(const void *base, long long off)
 {
@@ -83,6 +95,27 @@ __device__ __forceinline__ R pressure2(R rho, R mx, R my, R E, R gm1)
     return gm1 * (E - (mx * mx + my * my) / (R(2) * rho));
 }
 
+// Gate of the FP64 islands: is a state V, computed in precision R from terms of
+// magnitude at most mag[c] per component, certainly at or above eps in density and
+// pressure? In FP64 this is the exact test. In FP32 the test keeps margins far
+// above the rounding error of the terms (density 1e-2 of its term magnitude,
+// pressure 1e-3 of its term magnitude), so "true" implies the FP64 answer; a
+// "false" only sends the state to the FP64 island, which decides exactly.
+template <class R>
+__device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1, double eps)
+{
+    if constexpr (sizeof(R) == 8) {
+        double p = gm1 * (V[3] - (V[1] * V[1] + V[2] * V[2]) / (2.0 * V[0]));
+        return V[0] >= eps && p >= eps;
+    } else {
+        if (!(V[0] > 1e-2f * mag[0] + (float)eps)) return false;
+        float ke = (V[1] * V[1] + V[2] * V[2]) / (2.f * V[0]);
+        float p = gm1 * (V[3] - ke);
+        float m2 = mag[1] * mag[1] + mag[2] * mag[2];
+        return p > 1e-3f * gm1 * (mag[3] + m2 / V[0]) + (float)eps;
+    }
+}
+
 // Is U admissible (finite, rho > 0, p > 0)? Evaluated in FP64.
 __device__ __forceinline__ bool admissible2(const double *U, double gm1)
 {
@@ -90,6 +123,42 @@ __device__ __forceinline__ bool admissible2(const double *U, double gm1)
     double p = gm1 * (U[3] - (U[1] * U[1] + U[2] * U[2]) / (2.0 * U[0]));
     bool fin = isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
     return fin && p > 0.0;
+}
+
+// Monolithic positivity limiter of one face in FP64 (Sec. 3.3). Inputs: the total
+// low-order fluxes F_{l,i} of the cells left (FLc) and right (FRc) of the face, their
+// averages, the LLF speed lam of Eq. (19), theta_s and the high-order flux FH;
+// kk = 2 d dt / dx_l. Returns the limited flux F^L + theta^rho theta^p theta_s (FH - F^L),
+// theta^rho theta^p, and sets *bad when a low-order state U^{L,+-} leaves G.
+__device__ __forceinline__ void face_pp_fp64(const double FLc[4], const double FRc[4], const double UbL[4],
+                                             const double UbR[4], double lam, double ts, const double FH[4],
+                                             double kk, double g1, double eps, double Fout[4], double *tpp,
+                                             bool *bad)
+{
+    double FL[4], FLs[4], dF[4], ULp[4], UHp[4], ULm[4], UHm[4];
+    for (int c = 0; c < 4; ++c) {
+        FL[c] = 0.5 * (FLc[c] + FRc[c]) - 0.5 * lam * (UbR[c] - UbL[c]);
+        FLs[c] = FL[c] + ts * (FH[c] - FL[c]);
+        dF[c] = FLs[c] - FL[c];
+        ULp[c] = UbL[c] - kk * (FL[c] - FLc[c]);
+        UHp[c] = UbL[c] - kk * (FLs[c] - FLc[c]);
+        ULm[c] = UbR[c] - kk * (FRc[c] - FL[c]);
+        UHm[c] = UbR[c] - kk * (FRc[c] - FLs[c]);
+    }
+    if (!admissible2(ULp, g1) || !admissible2(ULm, g1)) *bad = true;
+    double thr = fmin(theta_fn(ULp[0], UHp[0], fmin(eps, ULp[0])), theta_fn(ULm[0], UHm[0], fmin(eps, ULm[0])));
+    double Urp[4], Urm[4];
+    for (int c = 0; c < 4; ++c) {
+        Urp[c] = (1.0 - thr) * ULp[c] + thr * UHp[c];
+        Urm[c] = (1.0 - thr) * ULm[c] + thr * UHm[c];
+    }
+    double pLp = g1 * (ULp[3] - (ULp[1] * ULp[1] + ULp[2] * ULp[2]) / (2.0 * ULp[0]));
+    double pLm = g1 * (ULm[3] - (ULm[1] * ULm[1] + ULm[2] * ULm[2]) / (2.0 * ULm[0]));
+    double prp = g1 * (Urp[3] - (Urp[1] * Urp[1] + Urp[2] * Urp[2]) / (2.0 * Urp[0]));
+    double prm = g1 * (Urm[3] - (Urm[1] * Urm[1] + Urm[2] * Urm[2]) / (2.0 * Urm[0]));
+    double thp = fmin(theta_fn(pLp, prp, fmin(eps, pLp)), theta_fn(pLm, prm, fmin(eps, pLm)));
+    *tpp = thr * thp;
+    for (int c = 0; c < 4; ++c) Fout[c] = FL[c] + *tpp * dF[c];
 }
 
 }  // namespace afns
