@@ -156,6 +156,38 @@ af_status af_get_profile(afns_ctx *ctx, double *stage_ms, long long *stage_launc
 
 const char *af_last_error(const afns_ctx *ctx);
 
+/* ------------------------------------------------------------------------- */
+/* Batched problems: many independent 2D problems of uneven grid sizes and     */
+/* gas parameters advanced together, one persistent stage kernel per RK stage  */
+/* over a (problem, tile) work list. Every problem keeps its own CFL step      */
+/* (Eq. (13)) and its own restart (Remark 3.2): a rejected step keeps u^n and  */
+/* is recomputed with dt/2 in the next batch step while the other problems     */
+/* move on. A batch step never waits for the host, so it is captured once in a */
+/* CUDA graph and replayed. Problems are 2D; precision and limiter come from    */
+/* opts (NULL = paper defaults with AF_MIXED).                                  */
+/* ------------------------------------------------------------------------- */
+typedef struct afb_ctx afb_ctx;
+
+af_status afb_workspace_bytes(int nprob, const af_grid *grids, const af_opts *opts, size_t *bytes);
+/* grids, gamma, mu, Pr, bcs: arrays of nprob entries. Workspace as in af_create. */
+af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const double *mu, const double *Pr,
+                     const af_bc *bcs, const af_opts *opts, void *cuda_stream, void *workspace,
+                     size_t workspace_bytes, afb_ctx **out);
+af_status afb_destroy(afb_ctx *ctx);
+/* Per-problem state in the 2D site layout of af_set_state (validated likewise). */
+af_status afb_set_state(afb_ctx *ctx, int i, const double *const site[4], int on_device, double t);
+af_status afb_get_state(afb_ctx *ctx, int i, double *const site[4], int on_device, double *t);
+/* Autotuner: times the candidate tile shapes, CTA sizes and work-list orders on
+ * the current states (restored afterwards) and keeps the fastest. */
+af_status afb_tune(afb_ctx *ctx, int *tile_x, int *tile_y, int *threads, int *schedule);
+/* Issue nsteps batch steps (asynchronous; use_graph = replay the captured step). */
+af_status afb_step_all(afb_ctx *ctx, int nsteps, int use_graph);
+/* Per-problem counters: accepted steps, rejected (restarted) steps, failure flag, time. */
+af_status afb_stats(afb_ctx *ctx, int i, int *accepted, int *restarts, int *failed, double *t);
+/* Wait for the batch; *launches_per_step = kernels issued per batch step. */
+af_status afb_sync(afb_ctx *ctx, long long *launches_per_step);
+const char *afb_last_error(const afb_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

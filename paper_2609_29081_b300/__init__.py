@@ -9,7 +9,7 @@ from . import workloads  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("Solver", "AfnsError", "load", "FP64", "MIXED", "LIM_NONE", "LIM_PP", "LIM_S_PP"):
+    if name in ("Solver", "AfnsError", "load", "FP64", "MIXED", "LIM_NONE", "LIM_PP", "LIM_S_PP", "BatchSolver"):
         from . import _native
         return getattr(_native, name)
     raise AttributeError(name)

@@ -223,3 +223,132 @@ class Solver:
         ms, ns, nl = ctypes.c_double(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
         self._check(self.lib.af_get_profile(self.ctx, ctypes.byref(ms), ctypes.byref(ns), ctypes.byref(nl)))
         return {"stage_ms": ms.value, "stage_launches": ns.value, "launches": nl.value}
+
+
+BATCH_EXPORTED = ["afb_workspace_bytes", "afb_create", "afb_destroy", "afb_set_state", "afb_get_state", "afb_tune",
+                  "afb_step_all", "afb_stats", "afb_sync", "afb_last_error"]
+
+
+def _load_batch():
+    L = load()
+    if getattr(L, "_batch_ready", False):
+        return L
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    P4 = ctypes.c_void_p * 4
+    L.afb_workspace_bytes.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.afb_create.argtypes = [ctypes.c_int, vp, dp, dp, dp, vp, vp, vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.afb_destroy.argtypes = [vp]
+    L.afb_set_state.argtypes = [vp, ctypes.c_int, P4, ctypes.c_int, ctypes.c_double]
+    L.afb_get_state.argtypes = [vp, ctypes.c_int, P4, ctypes.c_int, dp]
+    L.afb_tune.argtypes = [vp, ip, ip, ip, ip]
+    L.afb_step_all.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.afb_stats.argtypes = [vp, ctypes.c_int, ip, ip, ip, dp]
+    L.afb_sync.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.afb_last_error.argtypes = [vp]
+    L.afb_last_error.restype = ctypes.c_char_p
+    for f in BATCH_EXPORTED:
+        if f != "afb_last_error":
+            getattr(L, f).restype = ctypes.c_int
+    L._batch_ready = True
+    return L
+
+
+class BatchSolver:
+    """Many independent 2D problems (workloads.Workload list) on cuda:0."""
+
+    def __init__(self, wls, precision=MIXED, limiter=LIM_S_PP, stream=None, **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libafns needs a CUDA GPU; none is available")
+        self.torch = torch
+        self.lib = _load_batch()
+        self.wls = list(wls)
+        n = len(self.wls)
+        grids = (Grid * n)()
+        bcs = (BC * n)()
+        gam = (ctypes.c_double * n)(*[w.gamma for w in self.wls])
+        mu = (ctypes.c_double * n)(*[w.mu for w in self.wls])
+        pr = (ctypes.c_double * n)(*[w.Pr for w in self.wls])
+        for k, w in enumerate(self.wls):
+            assert w.dim == 2
+            grids[k].dim = 2
+            grids[k].n[0], grids[k].n[1] = w.n
+            grids[k].lo[0], grids[k].lo[1] = w.lo
+            grids[k].hi[0], grids[k].hi[1] = w.hi
+            for s in range(4):
+                bcs[k].side[s] = w.bc[s]
+        self.opts = default_opts(2, precision, limiter, **opts)
+        nb = ctypes.c_size_t(0)
+        self._check(self.lib.afb_workspace_bytes(n, ctypes.cast(grids, ctypes.c_void_p),
+                                                 ctypes.cast(ctypes.byref(self.opts), ctypes.c_void_p),
+                                                 ctypes.byref(nb)))
+        self.ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        base = (self.ws.data_ptr() + 255) // 256 * 256
+        # a stream of its own: a CUDA graph cannot be captured on the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        ctx = ctypes.c_void_p()
+        self._check(self.lib.afb_create(n, ctypes.cast(grids, ctypes.c_void_p), gam, mu, pr,
+                                        ctypes.cast(bcs, ctypes.c_void_p),
+                                        ctypes.cast(ctypes.byref(self.opts), ctypes.c_void_p),
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.c_void_p(base), nb.value,
+                                        ctypes.byref(ctx)))
+        self.ctx = ctx
+
+    def _check(self, st):
+        if st != AF_OK:
+            c = getattr(self, "ctx", None)
+            msg = self.lib.afb_last_error(c) if c else b""
+            raise AfnsError(st, (msg or b"").decode())
+        return st
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.afb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, i, buf):
+        shapes = workloads.site_shapes(2, *self.wls[i].n)
+        P4 = ctypes.c_void_p * 4
+        p = P4()
+        base = buf.ctypes.data
+        o = 0
+        for k, shp in enumerate(shapes):
+            p[k] = base + 8 * o
+            o += int(np.prod(shp))
+        assert o == buf.size
+        return p
+
+    def set_state(self, i, state, t=0.0):
+        s = np.ascontiguousarray(state, dtype=np.float64)
+        self._check(self.lib.afb_set_state(self.ctx, i, self._ptrs(i, s), 0, t))
+
+    def get_state(self, i):
+        out = np.empty(workloads.state_len(2, *self.wls[i].n))
+        t = ctypes.c_double(0)
+        self._check(self.lib.afb_get_state(self.ctx, i, self._ptrs(i, out), 0, ctypes.byref(t)))
+        return out, t.value
+
+    def tune(self):
+        v = [ctypes.c_int(0) for _ in range(4)]
+        self._check(self.lib.afb_tune(self.ctx, *[ctypes.byref(x) for x in v]))
+        return {"tile_x": v[0].value, "tile_y": v[1].value, "threads": v[2].value, "schedule": v[3].value}
+
+    def step_all(self, nsteps=1, graph=True):
+        self._check(self.lib.afb_step_all(self.ctx, nsteps, int(graph)))
+
+    def sync(self):
+        n = ctypes.c_longlong(0)
+        self._check(self.lib.afb_sync(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def stats(self, i):
+        a, r, f, t = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+        self._check(self.lib.afb_stats(self.ctx, i, ctypes.byref(a), ctypes.byref(r), ctypes.byref(f),
+                                       ctypes.byref(t)))
+        return {"accepted": a.value, "restarts": r.value, "failed": f.value, "t": t.value}

@@ -107,6 +107,7 @@ static af_status fail(afns_ctx *c, af_status s, const std::string &m)
 static af_status cuda_check(afns_ctx *c, cudaError_t e, const char *where)
 {
     if (e == cudaSuccess) return AF_OK;
+    cudaGetLastError();   // clear the runtime's record of the error so it is not reported again later
     return fail(c, AF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 

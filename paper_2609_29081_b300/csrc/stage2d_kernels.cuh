@@ -219,16 +219,16 @@ __device__ void lattice_llf(const R *sm, int l, int A, int B, double dx, double 
 // ---------------------------------------------------------------------------
 // The fused stage kernel
 // ---------------------------------------------------------------------------
+// One tile (bx, by) of one problem; the single-problem kernel runs one tile per
+// CTA, the batched persistent kernel loops over (problem, tile) work items.
 template <class R, class S, int TX, int TY>
-__global__ void __launch_bounds__(256) k_stage2d(StageArgs A)
+__device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R *sm)
 {
     using T = Tile2<TX, TY>;
     constexpr int NL = T::NL, LX = T::LX, CX = T::CX, QX = T::QX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sm = reinterpret_cast<R *>(smem_raw);
     __shared__ int s_bad;
     const Layout &L = A.L;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i0 = bx * TX, j0 = by * TY;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int ntx = min(TX, L.n1 - i0), nty = min(TY, L.n2 - j0);
     if (tid == 0) s_bad = 0;
@@ -712,6 +712,13 @@ __global__ void __launch_bounds__(256) k_stage2d(StageArgs A)
     if (tid == 0 && s_bad) atomicOr(&A.ctl->notpp, 1);
 }
 
+template <class R, class S, int TX, int TY>
+__global__ void __launch_bounds__(256) k_stage2d(StageArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<R, S, TX, TY>(A, blockIdx.x, blockIdx.y, reinterpret_cast<R *>(smem_raw));
+}
+
 // ---------------------------------------------------------------------------
 // CFL time step of Eq. (13): per-block maxima, then one finalising block.
 // ---------------------------------------------------------------------------
@@ -755,7 +762,7 @@ __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, 
     }
 }
 
-__global__ void k_dt_final(const double *partial, int nparts, Ctl *ctl, int clip)
+static __global__ void k_dt_final(const double *partial, int nparts, Ctl *ctl, int clip)
 {
     double m1 = 0.0, m2 = 0.0;
     for (int t = threadIdx.x; t < nparts; t += blockDim.x) {

@@ -34,6 +34,9 @@ class Workload:
     state: np.ndarray = field(repr=False)
     steps: int = 0          # nominal step count of the configuration (0: run to t_end)
 
+    def __post_init__(self):
+        periodize(self.state, self.dim, self.n, self.bc)
+
     @property
     def cells(self) -> int:
         return int(np.prod(self.n[: self.dim]))
@@ -58,6 +61,23 @@ def split_sites(state, dim, n1, n2=1):
 
 def state_len(dim, n1, n2=1):
     return sum(int(np.prod(s)) for s in site_shapes(dim, n1, n2))
+
+
+def periodize(state, dim, n, bc):
+    """Make the duplicated last face of every periodic direction an exact copy of
+    the first (sampling sin at 0 and at the period differs in the last bits)."""
+    sites = split_sites(state, dim, *n)
+    if dim == 1:
+        if bc[0] == BC_PERIODIC:
+            sites[1][:, -1] = sites[1][:, 0]
+        return state
+    if bc[0] == BC_PERIODIC:
+        for k in (1, 3):
+            sites[k][:, :, -1] = sites[k][:, :, 0]
+    if bc[2] == BC_PERIODIC:
+        for k in (2, 3):
+            sites[k][:, -1, :] = sites[k][:, 0, :]
+    return state
 
 
 def _to_cons(gamma, rho, vel, p):
@@ -246,3 +266,77 @@ def blast_2d(n=(32, 32), seed=0, mu=1e-3, Pr=0.72, gamma=1.4, rho_min=1e-6, p_mi
     s = project(2, tuple(n), lo, hi, gamma, f)
     return Workload("blast_2d_%dx%d_s%d" % (n[0], n[1], seed), 2, tuple(n), lo, hi, gamma, mu, Pr,
                     (BC_PERIODIC,) * 4, 0.0, s)
+
+
+def _sep_sin(k1, k2, ph, x, y):
+    """sin(k1 x + k2 y + ph) on the grid x (columns) by y (rows), as outer products."""
+    return np.outer(np.cos(k2 * y + ph), np.sin(k1 * x)) + np.outer(np.sin(k2 * y + ph), np.cos(k1 * x))
+
+
+def project_separable(n, L, gamma, field_fn, quad=3):
+    """Packed state of a field given by field_fn(x1d, y1d) -> (rho, u, v, p) 2D
+    arrays on the tensor grid x1d (columns) by y1d (rows). Cell averages by
+    quad-point Gauss-Legendre per direction."""
+    n1, n2 = n
+    dx, dy = L[0] / n1, L[1] / n2
+    gx, gw = np.polynomial.legendre.leggauss(quad)
+    gw = gw / 2.0
+    xc = (np.arange(n1) + 0.5) * dx
+    yc = (np.arange(n2) + 0.5) * dy
+    xf = np.arange(n1 + 1) * dx
+    yf = np.arange(n2 + 1) * dy
+
+    def cons(x, y):
+        rho, u, v, p = field_fn(x, y)
+        return np.array([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+    avg = np.zeros((4, n2, n1))
+    for qy in range(quad):
+        for qx in range(quad):
+            avg += gw[qx] * gw[qy] * cons(xc + 0.5 * dx * gx[qx], yc + 0.5 * dy * gx[qy])
+    return np.concatenate([avg.ravel(), cons(xf, yc).ravel(), cons(xc, yf).ravel(), cons(xf, yf).ravel()])
+
+
+def batch_problems(nprob=256, seed=5, sizes=(64, 96, 128, 192, 256, 384, 512), blast_frac=0.25, gamma=1.4,
+                   Pr=0.72):
+    """Batched workload: nprob independent periodic problems on [0,1]^2 with grid
+    sides drawn from `sizes` (uneven, seeded), mu log-uniform in [1e-4, 1e-2],
+    background rho = 1, p = 1/gamma (sound speed 1), mean flow of Mach U[0.1, 3] at
+    a random angle plus an 8-mode Fourier velocity perturbation (total amplitude
+    0.05); a fraction blast_frac are near-vacuum Gaussian blasts instead
+    (rho = 1e-6 + g, p = 1e-8 + g, g = exp(-r^2 / (2 sigma^2)), sigma = 1/16)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    nblast = int(round(blast_frac * nprob))
+    blast_ids = set(rng.choice(nprob, size=nblast, replace=False).tolist())
+    for p in range(nprob):
+        n = (int(rng.choice(sizes)), int(rng.choice(sizes)))
+        mu = float(10 ** rng.uniform(-4, -2))
+        if p in blast_ids:
+            cx, cy = rng.uniform(0.3, 0.7, size=2)
+            sig = 1.0 / 16.0
+
+            def f(x, y, cx=cx, cy=cy, sig=sig):
+                g = np.outer(np.exp(-(y - cy) ** 2 / (2 * sig * sig)), np.exp(-(x - cx) ** 2 / (2 * sig * sig)))
+                z = np.zeros_like(g)
+                return 1e-6 + g, z, z, 1e-8 + g
+            name = "blast"
+        else:
+            mach = rng.uniform(0.1, 3.0)
+            ang = rng.uniform(0, 2 * np.pi)
+            U0, V0 = mach * np.cos(ang), mach * np.sin(ang)
+            modes = fourier_modes(int(rng.integers(1 << 30)))
+
+            def f(x, y, U0=U0, V0=V0, modes=modes):
+                du = np.zeros((len(y), len(x)))
+                dv = np.zeros((len(y), len(x)))
+                for k1, k2, p1, p2, a in modes:
+                    du += a * _sep_sin(2 * np.pi * k1, 2 * np.pi * k2, p1, x, y)
+                    dv += a * _sep_sin(2 * np.pi * k1, 2 * np.pi * k2, p2 + np.pi / 2, x, y)
+                one = np.ones_like(du)
+                return one, U0 + du, V0 + dv, one / gamma
+            name = "flow"
+        s = project_separable(n, (1.0, 1.0), gamma, f)
+        out.append(Workload("batch%03d_%s_%dx%d" % (p, name, n[0], n[1]), 2, n, (0.0, 0.0), (1.0, 1.0), gamma, mu,
+                            Pr, (BC_PERIODIC,) * 4, 0.0, s))
+    return out
