@@ -56,6 +56,53 @@ struct Tile2 {
     static constexpr int total = oFY + 4 * NFY;
 };
 
+// Per-tile constants in the compute precision, derived once per tile by one
+// thread (the mixed path then runs no FP64 instruction outside its islands).
+template <class R>
+struct TileConst {
+    R gam, gm1, mu, ka, dx, dy, dt, eps, cs;
+    R kkx, kky;          // 2 d dt / dx_l with d = 2 (Sec. 3.3 intermediate states)
+    R w;                 // weight of L in the stage output (cl dt, or 1 in residual mode)
+    R a0, a1, a2, b1, b2, bldt;
+    // float-float weights of the compensated cell-average update (mixed path)
+    ff fa0, fa1, fa2, fwx, fwy, fb1, fb2, fbx, fby;
+    R idx, idy;
+};
+
+template <class R>
+__device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs &A, double dt)
+{
+    t.gam = (R)A.gamma;
+    t.gm1 = (R)(A.gamma - 1.0);
+    t.mu = (R)A.mu;
+    t.ka = (R)A.kappa;
+    t.dx = (R)A.L.dx;
+    t.dy = (R)A.L.dy;
+    t.dt = (R)dt;
+    t.eps = (R)A.eps;
+    t.cs = (R)A.c_s;
+    t.kkx = (R)(4.0 * dt / A.L.dx);
+    t.kky = (R)(4.0 * dt / A.L.dy);
+    t.w = (R)(A.k.residual ? 1.0 : A.k.cl * dt);
+    t.a0 = (R)A.k.a0;
+    t.a1 = (R)A.k.a1;
+    t.a2 = (R)A.k.a2;
+    t.b1 = (R)A.k.b1;
+    t.b2 = (R)A.k.b2;
+    t.bldt = (R)(A.k.bl * dt);
+    t.fa0 = ff_from(A.k.a0);
+    t.fa1 = ff_from(A.k.a1);
+    t.fa2 = ff_from(A.k.a2);
+    t.fwx = ff_from(A.k.cl * dt / A.L.dx);
+    t.fwy = ff_from(A.k.cl * dt / A.L.dy);
+    t.fb1 = ff_from(A.k.b1);
+    t.fb2 = ff_from(A.k.b2);
+    t.fbx = ff_from(A.k.bl * dt / A.L.dx);
+    t.fby = ff_from(A.k.bl * dt / A.L.dy);
+    t.idx = (R)(1.0 / A.L.dx);
+    t.idy = (R)(1.0 / A.L.dy);
+}
+
 // Low-order cell quantity slots
 enum { CQ_FX = 0, CQ_FY = 4, CQ_RX = 8, CQ_RY = 9, CQ_BX = 10, CQ_BY = 11, CQ_P1 = 12, CQ_P2 = 13 };
 
@@ -102,17 +149,17 @@ __device__ __forceinline__ R pressure2(R rho, R mx, R my, R E, R gm1)
 // pressure 1e-3 of its term magnitude), so "true" implies the FP64 answer; a
 // "false" only sends the state to the FP64 island, which decides exactly.
 template <class R>
-__device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1, double eps)
+__device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1, R eps)
 {
     if constexpr (sizeof(R) == 8) {
         double p = gm1 * (V[3] - (V[1] * V[1] + V[2] * V[2]) / (2.0 * V[0]));
         return V[0] >= eps && p >= eps;
     } else {
-        if (!(V[0] > 1e-2f * mag[0] + (float)eps)) return false;
+        if (!(V[0] > 1e-2f * mag[0] + eps)) return false;
         float ke = (V[1] * V[1] + V[2] * V[2]) / (2.f * V[0]);
         float p = gm1 * (V[3] - ke);
         float m2 = mag[1] * mag[1] + mag[2] * mag[2];
-        return p > 1e-3f * gm1 * (mag[3] + m2 / V[0]) + (float)eps;
+        return p > 1e-3f * gm1 * (mag[3] + m2 / V[0]) + eps;
     }
 }
 

@@ -232,10 +232,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
     const int tid = threadIdx.x, nth = blockDim.x;
     const int ntx = min(TX, L.n1 - i0), nty = min(TY, L.n2 - j0);
     if (tid == 0) s_bad = 0;
-    const R gam = (R)A.gamma, gm1 = (R)(A.gamma - 1.0), mu = (R)A.mu, ka = (R)A.kappa;
-    const R dx = (R)L.dx, dy = (R)L.dy;
+    __shared__ TileConst<R> tc;
     const double dt = A.ctl->dt;
     const double eps = A.eps;
+    if (tid == 0) tile_const_init<R>(tc, A, dt);
     R *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
     R *sA = sm + T::oA, *sAW = sm + T::oAW, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
 
@@ -252,7 +252,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         long long off = cell_off(L, i, j);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            sU[c * NL + t] = inb ? (R)ld<S>(A.uin, plane_of(L, site, c) + off) : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
+            sU[c * NL + t] = inb ? (R)((const S *)A.uin)[plane_of(L, site, c) + off]
+                                 : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
     }
     for (int t = tid; t < T::NCA; t += nth) {
         int ci = t % CX, cj = t / CX;
@@ -261,9 +262,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         long long off = cell_off(L, i, j);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            sA[c * T::NCA + t] = inb ? (R)ld<S>(A.uin, plane_of(L, 0, c) + off) : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
+            sA[c * T::NCA + t] = inb ? (R)((const S *)A.uin)[plane_of(L, 0, c) + off]
+                                     : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
     }
     __syncthreads();
+    const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka, dx = tc.dx, dy = tc.dy;
 
     // ---- P1: cell centres (Simpson inversion) + centre scaling limiter
     for (int t = tid; t < T::NCQ; t += nth) {
@@ -286,7 +289,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 mag[c] = R(4) * (fabs(sA[c * T::NCA + ca]) + fabs(P[n - 1]) + fabs(P[n + 1]) + fabs(P[n - LX]) +
                                  fabs(P[n + LX]));
             }
-            if (!surely_above(Uc, mag, gm1, eps)) {
+            if (!surely_above(Uc, mag, gm1, tc.eps)) {
                 // FP64 island: the centre in FP64 (same expression), then the scaling
                 // toward the cell average of Remark 3.1 if it is below epsilon
                 double Ub[4], Ud[4];
@@ -401,10 +404,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 R UHr[4], mag[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    UHr[c] = Un[c] + (R)dt * r[c];
-                    mag[c] = fabs(Un[c]) + fabs((R)dt * r[c]);
+                    UHr[c] = Un[c] + tc.dt * r[c];
+                    mag[c] = fabs(Un[c]) + fabs(tc.dt * r[c]);
                 }
-                if (!surely_above(UHr, mag, gm1, eps)) {
+                if (!surely_above(UHr, mag, gm1, tc.eps)) {
                     // FP64 island: exact test, then the low-order LLF point update on
                     // the half lattice and the Theta blend of Sec. 3.4
                     double Ud[4], UH[4];
@@ -440,16 +443,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
             int j = eb ? (b >> 1) : ((b - 1) >> 1);
             long long off = cell_off(L, i, j);
             S o[4];
-            const S ws = (S)w;
+            const S ws = tc.w;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 long long po = plane_of(L, site, c) + off;
-                S v = A.k.residual ? S(0) : (S)A.k.a1 * U[c];
-                if (A.k.a0 != 0.0) v += (S)A.k.a0 * ((const S *)A.u0)[po];
-                if (A.k.a2 != 0.0) v += (S)A.k.a2 * ((const S *)A.aux)[po];
+                S v = A.k.residual ? S(0) : tc.a1 * U[c];
+                if (A.k.a0 != 0.0) v += tc.a0 * ((const S *)A.u0)[po];
+                if (A.k.a2 != 0.0) v += tc.a2 * ((const S *)A.aux)[po];
                 o[c] = v + ws * res[c];
                 if (A.k.acc)
-                    ((S *)A.aux)[po] = (S)A.k.b2 * ((const S *)A.aux)[po] + (S)A.k.b1 * U[c] + (S)(A.k.bl * dt) * res[c];
+                    ((S *)A.aux)[po] = tc.b2 * ((const S *)A.aux)[po] + tc.b1 * U[c] + tc.bldt * res[c];
             }
             if (A.k.wall_fix) {
                 // wall point values: zero (normal) momentum, internal energy kept
@@ -548,8 +551,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
 #pragma unroll
                 for (int c = 0; c < 4; ++c) FH[c] += ws * Fn[c];
             }
-            double Fout[4];
-            double ts = 1.0, tpp = 1.0;
+            R Fout[4];
+            R tsr = R(1), tppr = R(1);
             if (A.limiter == LIM_NONE) {
                 for (int c = 0; c < 4; ++c) Fout[c] = FH[c];
             } else {
@@ -578,19 +581,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 }
                 const R lam = dmax(sCQ[ro * T::NCQ + qL], sCQ[ro * T::NCQ + qR]) +
                               dmax(sCQ[bo * T::NCQ + qL], sCQ[bo * T::NCQ + qR]);
-                R tsr = R(1);
                 if (A.limiter == LIM_S_PP) {
                     R p1 = dmax(sCQ[CQ_P1 * T::NCQ + qL], sCQ[CQ_P1 * T::NCQ + qR]);
                     R p2 = dmax(sCQ[CQ_P2 * T::NCQ + qL], sCQ[CQ_P2 * T::NCQ + qR]);
-                    tsr = exp(-(R)A.c_s * p1 * p2);
+                    tsr = exp(-tc.cs * p1 * p2);
                 }
-                ts = (double)tsr;
                 bool done = false;
                 if constexpr (sizeof(R) == 4) {
                     // FP32 screen: when all four intermediate states of Eq. (20) and
                     // Sec. 3.3 are surely above epsilon, theta^rho = theta^p = 1 and no
                     // low-order state leaves G, so the FP64 island is skipped.
-                    const R kk = (R)(4.0 * dt / (l == 0 ? L.dx : L.dy));
+                    const R kk = l == 0 ? tc.kkx : tc.kky;
                     R FL[4], FLs[4], mag[4], ULp[4], UHp[4], ULm[4], UHm[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -603,8 +604,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                         ULm[c] = UbR[c] - kk * (FRc[c] - FL[c]);
                         UHm[c] = UbR[c] - kk * (FRc[c] - FLs[c]);
                     }
-                    if (surely_above(ULp, mag, gm1, eps) && surely_above(UHp, mag, gm1, eps) &&
-                        surely_above(ULm, mag, gm1, eps) && surely_above(UHm, mag, gm1, eps)) {
+                    if (surely_above(ULp, mag, gm1, tc.eps) && surely_above(UHp, mag, gm1, tc.eps) &&
+                        surely_above(ULm, mag, gm1, tc.eps) && surely_above(UHm, mag, gm1, tc.eps)) {
 #pragma unroll
                         for (int c = 0; c < 4; ++c) Fout[c] = FLs[c];
                         done = true;
@@ -612,21 +613,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 }
                 if (!done) {
                     // FP64 island: intermediate states (factor 2 d mu_l, d = 2), theta^rho, theta^p
-                    double FLcd[4], FRcd[4], UbLd[4], UbRd[4], FHd[4];
+                    double FLcd[4], FRcd[4], UbLd[4], UbRd[4], FHd[4], Fd[4], tppd = 1.0;
                     for (int c = 0; c < 4; ++c) {
                         FLcd[c] = FLc[c], FRcd[c] = FRc[c], UbLd[c] = UbL[c], UbRd[c] = UbR[c], FHd[c] = FH[c];
                     }
                     bool bad = false;
-                    face_pp_fp64(FLcd, FRcd, UbLd, UbRd, (double)lam, ts, FHd, 4.0 * dt / (l == 0 ? L.dx : L.dy),
-                                 A.gamma - 1.0, eps, Fout, &tpp, &bad);
+                    face_pp_fp64(FLcd, FRcd, UbLd, UbRd, (double)lam, (double)tsr, FHd,
+                                 4.0 * dt / (l == 0 ? L.dx : L.dy), A.gamma - 1.0, eps, Fd, &tppd, &bad);
                     if (bad) s_bad = 1;
+                    for (int c = 0; c < 4; ++c) Fout[c] = (R)Fd[c];
+                    tppr = (R)tppd;
                 }
             }
             R *Fs = l == 0 ? sFX : sFY;
             int fidx = l == 0 ? el * (TX + 1) + fl : fl * TX + el;
             const int nf = l == 0 ? T::NFX : T::NFY;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) Fs[c * nf + fidx] = (R)Fout[c];
+            for (int c = 0; c < 4; ++c) Fs[c * nf + fidx] = Fout[c];
             if (A.theta) {
                 int gf = l == 0 ? i0 + fl : j0 + fl;   // global face index along l
                 int ge = l == 0 ? j0 + el : i0 + el;
@@ -634,8 +637,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 if (own) {
                     long long id = l == 0 ? (long long)ge * (L.n1 + 1) + gf : nfx + (long long)gf * L.n1 + ge;
                     long long nft = nfx + (long long)L.n1 * (L.n2 + 1);
-                    A.theta[id] = ts;
-                    A.theta[nft + id] = tpp;
+                    A.theta[id] = (double)tsr;
+                    A.theta[nft + id] = (double)tppr;
                 }
             }
         }
@@ -670,11 +673,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         // mixed precision: cell averages are stored as hi + lo (float-float); the
         // flux differences are formed exactly and the combination is compensated,
         // so the update is conservative to far below FP32 roundoff
-        const float fidx = (float)(1.0 / L.dx), fidy = (float)(1.0 / L.dy);
-        const ff a0 = ff_from(A.k.a0), a1 = ff_from(A.k.a1), a2 = ff_from(A.k.a2);
-        const ff wx = ff_from(A.k.cl * dt / L.dx), wy = ff_from(A.k.cl * dt / L.dy);
-        const ff b1 = ff_from(A.k.b1), b2 = ff_from(A.k.b2);
-        const ff bx = ff_from(A.k.bl * dt / L.dx), by = ff_from(A.k.bl * dt / L.dy);
+        const float fidx = tc.idx, fidy = tc.idy;
+        const ff a0 = tc.fa0, a1 = tc.fa1, a2 = tc.fa2, wx = tc.fwx, wy = tc.fwy;
+        const ff b1 = tc.fb1, b2 = tc.fb2, bx = tc.fbx, by = tc.fby;
         float *out = (float *)A.out;
         const float *uin = (const float *)A.uin, *u0 = (const float *)A.u0;
         float *aux = (float *)A.aux;
