@@ -156,6 +156,37 @@ af_status af_get_profile(afns_ctx *ctx, double *stage_ms, long long *stage_launc
 
 const char *af_last_error(const afns_ctx *ctx);
 
+/*
+ * Allocation-free CFL step (the paper has no counterpart of this call).
+ *
+ * af_dt_max_noalloc computes the time step of Eq. (13) for a 2D FP64 state that
+ * the caller already holds on the device, without allocating any device memory.
+ * It serves callers that cannot call cudaMalloc: code whose device memory is all
+ * owned by a host framework's pool allocator, or that runs where an allocation
+ * (with the device-wide synchronisation it can imply) is not allowed.
+ *  grid, gamma, mu, Pr: as for af_create (grid->dim must be 2).
+ *  opts: NULL = af_opts_default(2); only cfl_c and cfl_v are used.
+ *  avg_dev: device pointer to the cell averages in the layout of site[0] of
+ *    af_set_state, avg[4][n2][n1]; the caller owns it.
+ *  dt_dev: device pointer that receives one double; the caller owns it.
+ *  cuda_stream: the two kernels of the call are issued there, asynchronously;
+ *    nothing is synchronised (read dt_dev after the stream has reached it).
+ * Scratch: one file-scope device array inside the library, two doubles per chunk
+ * of AF_NOALLOC_CHUNK cells for at most AF_NOALLOC_MAX_CHUNKS chunks (256 KiB).
+ * Every GPU that loads the library holds it until the process exits. Grids with
+ * more than AF_NOALLOC_CHUNK * AF_NOALLOC_MAX_CHUNKS cells (67,108,864) are
+ * rejected with AF_EINVAL before anything is launched. The first call on a device
+ * looks up the array's device address for that device (once); make that first
+ * call before any stream capture. Every call writes each slot it later reads, so
+ * nothing needs clearing between calls; but all calls share the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.
+ */
+#define AF_NOALLOC_CHUNK 4096
+#define AF_NOALLOC_MAX_CHUNKS 16384
+af_status af_dt_max_noalloc(const af_grid *grid, double gamma, double mu, double Pr, const af_opts *opts,
+                            const double *avg_dev, double *dt_dev, void *cuda_stream);
+
 /* ------------------------------------------------------------------------- */
 /* Batched problems: many independent 2D problems of uneven grid sizes and     */
 /* gas parameters advanced together, one persistent stage kernel per RK stage  */
