@@ -375,7 +375,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         const int erow = (lasty && !pery) ? 2 * ntx : 0;
         const int ecor = (lastx && !perx && lasty && !pery) ? 1 : 0;
         const int tot = nreg + ecol + erow + ecor;
-        const double w = A.k.residual ? 1.0 : A.k.cl * dt;
         for (int t = tid; t < tot; t += nth) {
             int la, lb;
             if (t < nreg) {
@@ -730,18 +729,43 @@ __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, 
     double m1 = 0.0, m2 = 0.0;
     const long long nc = (long long)L.n1 * L.n2;
     const double g1 = gamma - 1.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc; t += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(t % L.n1), j = (int)(t / L.n1);
-        long long off = cell_off(L, i, j);
-        double rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
-        double my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
-        double p = g1 * (E - (mx * mx + my * my) / (2.0 * rho));
-        double c = sqrt(gamma * p / rho);
-        double rv = fmax(4.0 * mu / (3.0 * rho), gamma * mu / (Pr * rho));
-        double a = fmax((fabs(mx / rho) + c) / (cfl_c * L.dx), (fabs(my / rho) + c) / (cfl_c * L.dy));
-        double b = fmax(rv / (cfl_v * L.dx * L.dx), rv / (cfl_v * L.dy * L.dy));
-        m1 = fmax(m1, a);
-        m2 = fmax(m2, b);
+    if constexpr (sizeof(S) == 4) {
+        // mixed path: FP32 arithmetic with one reciprocal per cell (the step size
+        // needs no more than FP32 accuracy); maxima merged in FP64 below
+        const float gf = (float)gamma, g1f = (float)g1, muf = (float)mu;
+        const float rvc = fmaxf(4.f / 3.f, (float)(gamma / Pr)) * muf;
+        const float ix = (float)(1.0 / (cfl_c * L.dx)), iy = (float)(1.0 / (cfl_c * L.dy));
+        const float vx = (float)(1.0 / (cfl_v * L.dx * L.dx)), vy = (float)(1.0 / (cfl_v * L.dy * L.dy));
+        float f1 = 0.f, f2 = 0.f;
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
+             t += (long long)gridDim.x * blockDim.x) {
+            int i = (int)(t % L.n1), j = (int)(t / L.n1);
+            long long off = cell_off(L, i, j);
+            float rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
+            float my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
+            float r = 1.f / rho, u = mx * r, v = my * r;
+            float p = g1f * (E - 0.5f * (mx * u + my * v));
+            float c = sqrtf(gf * p * r);
+            f1 = fmaxf(f1, fmaxf((fabsf(u) + c) * ix, (fabsf(v) + c) * iy));
+            f2 = fmaxf(f2, rvc * r * fmaxf(vx, vy));
+        }
+        m1 = f1;
+        m2 = f2;
+    } else {
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
+             t += (long long)gridDim.x * blockDim.x) {
+            int i = (int)(t % L.n1), j = (int)(t / L.n1);
+            long long off = cell_off(L, i, j);
+            double rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
+            double my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
+            double p = g1 * (E - (mx * mx + my * my) / (2.0 * rho));
+            double c = sqrt(gamma * p / rho);
+            double rv = fmax(4.0 * mu / (3.0 * rho), gamma * mu / (Pr * rho));
+            double a = fmax((fabs(mx / rho) + c) / (cfl_c * L.dx), (fabs(my / rho) + c) / (cfl_c * L.dy));
+            double b = fmax(rv / (cfl_v * L.dx * L.dx), rv / (cfl_v * L.dy * L.dy));
+            m1 = fmax(m1, a);
+            m2 = fmax(m2, b);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
