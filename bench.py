@@ -251,6 +251,7 @@ def main():
     with torch.cuda.stream(stream):
         S = Solver.from_workload(w, precision=prec, stream=stream)
         S.set_state(w.state)
+        tuned = S.tune()
         for _ in range(args.warmup):
             S.step(0.0)
         torch.cuda.synchronize()
@@ -329,7 +330,7 @@ def main():
                                    % (args.n, args.n),
                        "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (state %.0f MB per buffer, 5 buffers)" % (state_bytes / 1e6),
-                       "restarts": restarts},
+                       "restarts": restarts, "tuned": tuned},
             "roofline": roofline, "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes},

@@ -140,6 +140,15 @@ af_status af_residual(afns_ctx *ctx, double dt, double *const L[4], int on_devic
  */
 af_status af_get_limiter(afns_ctx *ctx, double *theta_s, double *theta_pp);
 
+/*
+ * Autotuner of the 2D stage kernel launch (tile width 16 or 32 cells, 256 or 128
+ * threads per CTA; 32-wide tiles only in AF_MIXED): times each candidate on
+ * residual evaluations of the current state (the state is not changed) and keeps
+ * the fastest for the following steps. Results do not depend on the choice.
+ * Needs a state (AF_ESTATE otherwise). Outputs may be NULL.
+ */
+af_status af_tune(afns_ctx *ctx, int *tile_x, int *threads);
+
 /* Number of cells n1*n2 and of faces (sizes of the arrays above). */
 af_status af_sizes(const afns_ctx *ctx, size_t *cells, size_t *faces, size_t *site_elems4);
 

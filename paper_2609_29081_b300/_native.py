@@ -23,7 +23,8 @@ LIM_NONE, LIM_PP, LIM_S_PP = 0, 1, 2
 
 EXPORTED = ["af_opts_default", "af_workspace_bytes", "af_create", "af_destroy", "af_set_state",
             "af_get_state", "af_dt_max", "af_step", "af_advance", "af_residual", "af_get_limiter",
-            "af_sizes", "af_set_profiling", "af_get_profile", "af_last_error"]
+            "af_sizes", "af_set_profiling", "af_get_profile", "af_tune", "af_dt_max_noalloc",
+            "af_last_error"]
 
 
 class AfnsError(RuntimeError):
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH):
     L.af_residual.argtypes = [vp, ctypes.c_double, P4, ctypes.c_int, ip]
     L.af_get_limiter.argtypes = [vp, vp, vp]
     L.af_sizes.argtypes = [vp, sp, sp, sp]
+    L.af_tune.argtypes = [vp, ip, ip]
+    L.af_dt_max_noalloc.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     L.af_set_profiling.argtypes = [vp, ctypes.c_int]
     L.af_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.af_last_error.argtypes = [vp]
@@ -215,6 +218,11 @@ class Solver:
         self._check(self.lib.af_get_limiter(self.ctx, ts.ctypes.data_as(ctypes.c_void_p),
                                             tp.ctypes.data_as(ctypes.c_void_p)))
         return ts, tp
+
+    def tune(self):
+        tx, th = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.af_tune(self.ctx, ctypes.byref(tx), ctypes.byref(th)))
+        return {"tile_x": tx.value, "threads": th.value}
 
     def set_profiling(self, on=True):
         self._check(self.lib.af_set_profiling(self.ctx, int(on)))

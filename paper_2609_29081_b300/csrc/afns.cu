@@ -17,7 +17,7 @@
 #include "stage2d.cuh"
 
 namespace afns {
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, cudaStream_t st);
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, cudaStream_t st);
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st);
@@ -27,7 +27,7 @@ cudaError_t launch_stage1d_fp64(const StageArgs &A, cudaStream_t st);
 cudaError_t launch_dt1d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_validate1d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st);
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, cudaStream_t st);
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, cudaStream_t st);
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
@@ -78,6 +78,8 @@ struct afns_ctx {
     void *U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // u^n, u1/u3/u5, u2/acc, u4, residual
     double *stage64 = nullptr;   // FP64 staging state of the mixed path
     bool mixed = false;
+    int tile_x = 16;             // 2D tile width (16, or 32 in the mixed path)
+    int threads = 256;           // threads per CTA of the stage kernel
     Ctl *ctl = nullptr;
     Ctl *h_ctl = nullptr;   // pinned mirror
     double *partial = nullptr;
@@ -260,6 +262,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->mixed = opts->precision == AF_MIXED;
     c->L.comp = c->mixed ? 1 : 0;
     c->stage64 = c->mixed ? (double *)q : nullptr;
+    c->tile_x = (c->mixed && opts->tile_x == 32) ? 32 : 16;
     q += p.stage64;
     c->ctl = (Ctl *)q;
     q += p.ctl;
@@ -355,8 +358,8 @@ static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
 {
     c->launches += 1;
     if (c->dim == 1) return launch_stage1d_fp64(A, c->st);
-    if (c->mixed) return launch_stage2d_mixed(A, c->opts.tile_x, c->opts.tile_y, c->st);
-    return launch_stage2d_fp64(A, c->opts.tile_x, c->opts.tile_y, c->st);
+    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->threads, c->st);
+    return launch_stage2d_fp64(A, c->tile_x, c->threads, c->st);
 }
 
 // Public FP64 site arrays <-> state buffer. The FP64 path copies directly; the
@@ -660,5 +663,56 @@ extern "C" af_status af_get_profile(afns_ctx *c, double *stage_ms, long long *st
     if (stage_ms) *stage_ms = c->stage_ms;
     if (stage_launches) *stage_launches = c->stage_launches;
     if (launches) *launches = c->launches;
+    return AF_OK;
+}
+
+// Autotuner of the 2D stage kernel: times each candidate launch configuration
+// (tile width, threads per CTA) on residual evaluations of the current state,
+// which leave the state untouched, and keeps the fastest. Results do not depend
+// on the configuration (every face and node is computed by the same arithmetic).
+extern "C" af_status af_tune(afns_ctx *c, int *tile_x, int *threads)
+{
+    if (!c) return AF_EINVAL;
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    if (c->dim == 2) {
+        struct Cand {
+            int tx, th;
+        };
+        const Cand cands[] = {{16, 256}, {16, 128}, {32, 256}, {32, 128}};
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+            return cuda_check(c, cudaGetLastError(), "tune events");
+        float best = 1e30f;
+        Cand pick{c->tile_x, c->threads};
+        int prof = c->profiling;
+        c->profiling = 0;
+        cudaError_t e = cudaSuccess;
+        k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, c->t);
+        e = launch_dt(c, 0);
+        StageCoef k{};
+        k.residual = 1;
+        for (const Cand &cd : cands) {
+            if (e != cudaSuccess) break;
+            if (cd.tx == 32 && !c->mixed) continue;
+            c->tile_x = cd.tx;
+            c->threads = cd.th;
+            e = run_stage(c, c->U[0], c->U[4], k, nullptr);   // warm-up (sets the shared-memory limit)
+            if (e == cudaSuccess) e = cudaEventRecord(a, c->st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run_stage(c, c->U[0], c->U[4], k, nullptr);
+            if (e == cudaSuccess) e = cudaEventRecord(b, c->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && ms < best) best = ms, pick = cd;
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        c->profiling = prof;
+        c->tile_x = pick.tx;
+        c->threads = pick.th;
+        if (e != cudaSuccess) return cuda_check(c, e, "tune");
+    }
+    if (tile_x) *tile_x = c->tile_x;
+    if (threads) *threads = c->threads;
     return AF_OK;
 }

@@ -170,7 +170,7 @@ __global__ void k_batch_ghost(BatchProb *probs, int in_idx, int pass)
 
 // --- the persistent stage kernel over the work list
 template <class R, class S, int TX, int TY>
-__global__ void __launch_bounds__(256) k_batch_stage(BatchArgs B)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_stage(BatchArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem_batch[];
     R *sm = reinterpret_cast<R *>(smem_batch);

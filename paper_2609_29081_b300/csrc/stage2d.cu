@@ -21,7 +21,7 @@ cudaError_t launch_ghost2d(const Layout &L, S *buf, cudaStream_t st)
 }
 
 template <class R, class S, int TX, int TY>
-cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st)
+cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st, int threads = 256)
 {
     using T = Tile2<TX, TY>;
     size_t smem = sizeof(R) * (size_t)T::total;
@@ -33,15 +33,16 @@ cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st)
         attr_set = true;
     }
     dim3 grid((A.L.n1 + TX - 1) / TX, (A.L.n2 + TY - 1) / TY);
-    k_stage2d<R, S, TX, TY><<<grid, 256, smem, st>>>(A);
+    k_stage2d<R, S, TX, TY><<<grid, threads, smem, st>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, cudaStream_t st)
+// Tile shapes: FP64 16x8 only (the 32x8 FP64 tile exceeds shared memory); FP32
+// 16x8 or 32x8. threads: 256 or 128 per CTA (every phase loops over its items).
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, cudaStream_t st)
 {
     (void)tx;
-    (void)ty;
-    return launch_stage2d_t<double, double, 16, 8>(A, st);
+    return launch_stage2d_t<double, double, 16, 8>(A, st, threads > 0 ? threads : 256);
 }
 
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
@@ -75,11 +76,10 @@ cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double ga
 // ---------------------------------------------------------------------------
 namespace afns {
 
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, cudaStream_t st)
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, cudaStream_t st)
 {
-    (void)tx;
-    (void)ty;
-    return launch_stage2d_t<float, float, 16, 8>(A, st);
+    if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, st, threads > 0 ? threads : 256);
+    return launch_stage2d_t<float, float, 16, 8>(A, st, threads > 0 ? threads : 256);
 }
 
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st) { return launch_ghost2d<float>(L, buf, st); }

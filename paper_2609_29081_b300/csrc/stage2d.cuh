@@ -67,6 +67,11 @@ struct TileConst {
     // float-float weights of the compensated cell-average update (mixed path)
     ff fa0, fa1, fa2, fwx, fwy, fb1, fb2, fbx, fby;
     R idx, idy;
+    int ua0, ua2;        // the combination reads u^n / the auxiliary state
+    R i6[2];             // 1 / (6 dx_l): D_c and the FVS stencils
+    R i3h2[2];           // 1 / (3 dx_l^2): (4 / dx_l^2) times the 1/12 of the column sums
+    R f4h2[2];           // 4 / dx_l^2: prefactor of Eq. (9)
+    R i2[2];             // 1 / (2 dx_l): central differences of the cell averages
 };
 
 template <class R>
@@ -101,6 +106,15 @@ __device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs
     t.fby = ff_from(A.k.bl * dt / A.L.dy);
     t.idx = (R)(1.0 / A.L.dx);
     t.idy = (R)(1.0 / A.L.dy);
+    t.ua0 = A.k.a0 != 0.0;
+    t.ua2 = A.k.a2 != 0.0;
+    const double h[2] = {A.L.dx, A.L.dy};
+    for (int l = 0; l < 2; ++l) {
+        t.i6[l] = (R)(1.0 / (6.0 * h[l]));
+        t.i3h2[l] = (R)(1.0 / (3.0 * h[l] * h[l]));
+        t.f4h2[l] = (R)(4.0 / (h[l] * h[l]));
+        t.i2[l] = (R)(1.0 / (2.0 * h[l]));
+    }
 }
 
 // Low-order cell quantity slots
@@ -156,10 +170,12 @@ __device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1
         return V[0] >= eps && p >= eps;
     } else {
         if (!(V[0] > 1e-2f * mag[0] + eps)) return false;
-        float ke = (V[1] * V[1] + V[2] * V[2]) / (2.f * V[0]);
+        // a screen with percent-level margins: the fast reciprocal (2 ulp) suffices
+        const float ir = __fdividef(1.f, V[0]);
+        float ke = 0.5f * (V[1] * V[1] + V[2] * V[2]) * ir;
         float p = gm1 * (V[3] - ke);
         float m2 = mag[1] * mag[1] + mag[2] * mag[2];
-        return p > 1e-3f * gm1 * (mag[3] + m2 / V[0]) + eps;
+        return p > 1e-3f * gm1 * (mag[3] + m2 * ir) + eps;
     }
 }
 

@@ -54,7 +54,7 @@ __global__ void k_ghost2d(Layout L, S *buf, int pass)
 // Point-value residual of Eq. (12) at lattice node n of the shared tile.
 // ---------------------------------------------------------------------------
 template <class R, int TX, int TY>
-__device__ __forceinline__ void point_residual(const R *sm, int n, R dx, R dy, R mu, R ka, R res[4])
+__device__ __forceinline__ void point_residual(const R *sm, int n, const TileConst<R> &tc, R res[4])
 {
     using T = Tile2<TX, TY>;
     constexpr int NL = T::NL, LX = T::LX;
@@ -62,13 +62,13 @@ __device__ __forceinline__ void point_residual(const R *sm, int n, R dx, R dy, R
     const R *qu = sm + T::oQ, *qv = qu + NL, *qT = qv + NL, *qc = qT + NL;
     const R *gxu = sm + T::oGX, *gxv = gxu + NL;
     const R *gyu = sm + T::oGY, *gyv = gyu + NL;
+    const R mu = tc.mu, ka = tc.ka;
     res[0] = res[1] = res[2] = res[3] = R(0);
     const R mu43 = R(4) / R(3) * mu, mu23 = R(2) / R(3) * mu;
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
         const int st = l == 0 ? 1 : LX;
-        const R h = l == 0 ? dx : dy;
-        const R inv6h = R(1) / (R(6) * h);
+        const R inv6h = tc.i6[l];
         // --- inviscid: D_+ F^+ + D_- F^- = [sum_k dc_k F_k + alpha d4_k U_k] / (6 h)
         R al = R(0);
 #pragma unroll
@@ -117,10 +117,10 @@ __device__ __forceinline__ void point_residual(const R *sm, int n, R dx, R dy, R
             }
             eq += c1 * qu[m] * bu + c2 * qv[m] * bv;
         }
-        const R i3h2 = R(1) / (R(3) * h * h);   // (4/dx^2)/12
+        const R i3h2 = tc.i3h2[l];   // (4/dx^2)/12
         res[1] += c1 * d2u * i3h2;
         res[2] += c2 * d2v * i3h2;
-        res[3] += ka * d2T * i3h2 + R(4) / (h * h) * eq;
+        res[3] += ka * d2T * i3h2 + tc.f4h2[l] * eq;
         // --- viscous, mixed: D_c^{(l)}(K_lm D_c^{(m)} Z), m != l
         R g1 = 0, g2 = 0, g3 = 0;
 #pragma unroll
@@ -322,27 +322,31 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
     __syncthreads();
 
     // ---- P2: primitive quantities at every lattice node and every cell
+    // one reciprocal of rho per node: u = m_x / rho, v = m_y / rho, p = (gamma-1)(E - (m.u)/2), T = p / rho
     for (int t = tid; t < NL; t += nth) {
         R rho = sU[t], mx = sU[NL + t], my = sU[2 * NL + t], E = sU[3 * NL + t];
-        R p = pressure2(rho, mx, my, E, gm1);
-        sQ[t] = mx / rho;
-        sQ[NL + t] = my / rho;
-        sQ[2 * NL + t] = p / rho;
-        sQ[3 * NL + t] = sqrt(gam * p / rho);
+        R r = R(1) / rho, u = mx * r, v = my * r;
+        R p = gm1 * (E - R(0.5) * (mx * u + my * v));
+        R Tn = p * r;
+        sQ[t] = u;
+        sQ[NL + t] = v;
+        sQ[2 * NL + t] = Tn;
+        sQ[3 * NL + t] = sqrt(gam * Tn);
     }
     for (int t = tid; t < T::NCA; t += nth) {
         R rho = sA[t], mx = sA[T::NCA + t], my = sA[2 * T::NCA + t], E = sA[3 * T::NCA + t];
-        R p = pressure2(rho, mx, my, E, gm1);
-        sAW[t] = mx / rho;
-        sAW[T::NCA + t] = my / rho;
+        R r = R(1) / rho, u = mx * r, v = my * r;
+        R p = gm1 * (E - R(0.5) * (mx * u + my * v));
+        sAW[t] = u;
+        sAW[T::NCA + t] = v;
         sAW[2 * T::NCA + t] = p;
-        sAW[3 * T::NCA + t] = p / rho;
+        sAW[3 * T::NCA + t] = p * r;
     }
     __syncthreads();
 
     // ---- P3: D_c gradients of Z = (u, v, T) along x and along y
     {
-        const R i6x = R(1) / (R(6) * dx), i6y = R(1) / (R(6) * dy);
+        const R i6x = tc.i6[0], i6y = tc.i6[1];
         const int nx = (LX - 4) * T::LY;
         for (int t = tid; t < nx; t += nth) {
             int la = 2 + t % (LX - 4), lb = t / (LX - 4);
@@ -394,7 +398,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
             }
             const int n = lb * LX + la;
             R r[4];
-            point_residual<R, TX, TY>(sm, n, dx, dy, mu, ka, r);
+            point_residual<R, TX, TY>(sm, n, tc, r);
             // the RK combination of point values runs in the storage precision S
             const R Un[4] = {sU[n], sU[NL + n], sU[2 * NL + n], sU[3 * NL + n]};
             S res[4] = {(S)r[0], (S)r[1], (S)r[2], (S)r[3]};
@@ -447,8 +451,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
             for (int c = 0; c < 4; ++c) {
                 long long po = plane_of(L, site, c) + off;
                 S v = A.k.residual ? S(0) : tc.a1 * U[c];
-                if (A.k.a0 != 0.0) v += tc.a0 * ((const S *)A.u0)[po];
-                if (A.k.a2 != 0.0) v += tc.a2 * ((const S *)A.aux)[po];
+                if (tc.ua0) v += tc.a0 * ((const S *)A.u0)[po];
+                if (tc.ua2) v += tc.a2 * ((const S *)A.aux)[po];
                 o[c] = v + ws * res[c];
                 if (A.k.acc)
                     ((S *)A.aux)[po] = tc.b2 * ((const S *)A.aux)[po] + tc.b1 * U[c] + tc.bldt * res[c];
@@ -480,21 +484,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         const R *Au = sAW, *Av = sAW + T::NCA, *Ap = sAW + 2 * T::NCA, *AT = sAW + 3 * T::NCA;
         R rho = sA[ca], mx = sA[T::NCA + ca], my = sA[2 * T::NCA + ca], E = sA[3 * T::NCA + ca];
         R u = Au[ca], v = Av[ca], p = Ap[ca];
-        R i2x = R(1) / (R(2) * dx), i2y = R(1) / (R(2) * dy);
+        const R i2x = tc.i2[0], i2y = tc.i2[1];
         R Sxu = (Au[ca + 1] - Au[ca - 1]) * i2x, Sxv = (Av[ca + 1] - Av[ca - 1]) * i2x,
           SxT = (AT[ca + 1] - AT[ca - 1]) * i2x;
         R Syu = (Au[ca + CX] - Au[ca - CX]) * i2y, Syv = (Av[ca + CX] - Av[ca - CX]) * i2y,
           SyT = (AT[ca + CX] - AT[ca - CX]) * i2y;
         R Fx[4], Fy[4];
-        node_flux<R>(0, rho, mx, my, E, u, v, p / rho, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fx);
-        node_flux<R>(1, rho, mx, my, E, u, v, p / rho, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fy);
+        const R Tc = AT[ca];
+        node_flux<R>(0, rho, mx, my, E, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fx);
+        node_flux<R>(1, rho, mx, my, E, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fy);
         R *q = sCQ + t;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             q[(CQ_FX + c) * T::NCQ] = Fx[c];
             q[(CQ_FY + c) * T::NCQ] = Fy[c];
         }
-        R cs = sqrt(gam * p / rho);
+        R cs = sqrt(gam * Tc);
         q[CQ_RX * T::NCQ] = fabs(u) + cs;
         q[CQ_RY * T::NCQ] = fabs(v) + cs;
         // Lemma 3.2 bound b_l with tau_l = (tau_1l, tau_2l), q_l = -kappa dT/dx_l
@@ -503,10 +508,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         R txy = mu * (Syu + Sxv);
         R re = p / gm1;
         R qx = -ka * SxT, qy = -ka * SyT;
-        q[CQ_BX * T::NCQ] =
-            (sqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) / (R(2) * rho * re);
-        q[CQ_BY * T::NCQ] =
-            (sqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) / (R(2) * rho * re);
+        const R ib = R(1) / (R(2) * rho * re);
+        q[CQ_BX * T::NCQ] = (sqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) * ib;
+        q[CQ_BY * T::NCQ] = (sqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) * ib;
         // Sec. 3.2 sensors
         R px = fabs(Ap[ca + 1] - R(2) * p + Ap[ca - 1]) / fabs(Ap[ca + 1] + R(2) * p + Ap[ca - 1]);
         R py = fabs(Ap[ca + CX] - R(2) * p + Ap[ca - CX]) / fabs(Ap[ca + CX] + R(2) * p + Ap[ca - CX]);
@@ -695,8 +699,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 const ff inc = ff_add(ff_mul(wx, dxf), ff_mul(wy, dyf));
                 const ff ui = {(float)sA[c * T::NCA + ca], uin[pl]};
                 ff v = ff_mul(a1, ui);
-                if (A.k.a0 != 0.0) v = ff_add(v, ff_mul(a0, ff{u0[po], u0[pl]}));
-                if (A.k.a2 != 0.0) v = ff_add(v, ff_mul(a2, ff{aux[po], aux[pl]}));
+                if (tc.ua0) v = ff_add(v, ff_mul(a0, ff{u0[po], u0[pl]}));
+                if (tc.ua2) v = ff_add(v, ff_mul(a2, ff{aux[po], aux[pl]}));
                 if (A.k.acc) {
                     ff ac = ff_add(ff_mul(b2, ff{aux[po], aux[pl]}), ff_mul(b1, ui));
                     ac = ff_add(ac, ff_add(ff_mul(bx, dxf), ff_mul(by, dyf)));
@@ -713,7 +717,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
 }
 
 template <class R, class S, int TX, int TY>
-__global__ void __launch_bounds__(256) k_stage2d(StageArgs A)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_stage2d(StageArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     stage_tile<R, S, TX, TY>(A, blockIdx.x, blockIdx.y, reinterpret_cast<R *>(smem_raw));

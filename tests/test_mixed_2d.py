@@ -68,6 +68,27 @@ def test_mixed_ten_steps_against_fp64_oracle(orc, case):
     assert l1_rel(g, s, w.n) < 2e-6
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_launch_configuration_does_not_change_results(prec):
+    """Tile width and CTA size (autotuned) change no bit of the result."""
+    from paper_2609_29081_b300 import MIXED, FP64, Solver
+    w = W.random_smooth_2d((70, 37), seed=13, bc=(1, 1, 2, 3))
+    p = MIXED if prec == "mixed" else FP64
+    outs = []
+    for tx in ((16, 32) if prec == "mixed" else (16,)):
+        S = Solver.from_workload(w, precision=p, tile_x=tx)
+        S.set_state(w.state)
+        r0, _ = S.residual(1e-3)
+        cfg = S.tune()
+        r1, _ = S.residual(1e-3)
+        assert np.array_equal(r0, r1), cfg
+        for _ in range(3):
+            S.step(0.0)
+        outs.append(S.get_state())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
 def test_mixed_conserves_and_stays_positive():
     """Compensated cell averages: mass, momentum, energy conserved to 1e-12 on a
     periodic grid after 50 steps; a near-vacuum blast keeps positivity."""
