@@ -33,7 +33,71 @@ UNIT = "cell-stage updates/s"
 N_CELLS = 1024
 # FP64 peak of one B300 (TFLOP/s): the published dense FP64 rate of the part
 # (the FP64 pipe is 1/64 of the FP32 rate on sm_103); see the design doc for its derivation.
-FP64_PEAK_TFLOPS = 1.25
+# B300: 148 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.032 GHz (max SM clock)
+FP64_DERIVED_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+# 148 SMs x 128 FP32 lanes x 2 flops x 2.032 GHz
+FP32_DERIVED_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# DRAM bytes (read + write) per stage launch from ncu, with the digest of the
+# kernel sources they were taken on; reported only while the sources match.
+MEASURED_TRAFFIC = {}
+
+
+def kernel_digest(precision):
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2609_29081_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.startswith("stage2d") or f == "afns_dev.cuh":
+            h.update(open(os.path.join(d, f), "rb").read())
+    return precision + ":" + h.hexdigest()[:16]
+
+
+def measure_alu_peaks():
+    """FP64 and FP32 FMA-chain throughput measured on this GPU (TFLOP/s)."""
+    from paper_2609_29081_b300._native import FP64, MIXED, alu_peak
+    out = {}
+    for name, p in (("fp64", FP64), ("fp32", MIXED)):
+        try:
+            out[name] = alu_peak(p)
+        except Exception:
+            out[name] = None
+    return out
+
+
+def stage_roofline(precision, cells, stage_ms, peaks, alu_pk):
+    """Roofline of the stage kernel: the slower of the algorithmic HBM bytes at
+    the measured copy bandwidth and the algorithmic flops at the measured FMA
+    rate (FP64 path: FP64 flops; mixed path: FP32 flops, 256 B per cell-stage)."""
+    sec = stage_ms / 1e3
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "of measured: MEASURED_PEAKS.json hbm_gbs" if hbm else "of fallback: 6400 GB/s"
+    hbm = hbm or 6400.0
+    key = "fp64" if precision == "fp64" else "fp32"
+    derived = FP64_DERIVED_TFLOPS if precision == "fp64" else FP32_DERIVED_TFLOPS
+    alu = alu_pk.get(key)
+    alu_src = "of measured: %s FMA chains on this GPU (af_alu_peak)" % key.upper() if alu else \
+        "of derived: unit counts x 2.032 GHz"
+    alu = alu or derived
+    bpc = BYTES_PER_CELL_STAGE_FP64 if precision == "fp64" else BYTES_PER_CELL_STAGE_MIXED
+    t_hbm = bpc * cells / (hbm * 1e9)
+    t_alu = FLOPS_PER_CELL_STAGE * cells / (alu * 1e12)
+    dig = kernel_digest(precision)
+    traffic = MEASURED_TRAFFIC.get(dig)
+    kern = "k_stage2d<double>" if precision == "fp64" else "k_stage2d<float>"
+    common = {"traffic": traffic, "kernel": kern, "kernel_digest": dig,
+              "hbm_frac": t_hbm / sec, "alu_frac": t_alu / sec,
+              "alu_peak_tflops": alu, "alu_peak_source": alu_src,
+              "alu_peak_derived_tflops": derived, "hbm_peak_gbs": hbm}
+    if t_alu >= t_hbm:
+        achieved = FLOPS_PER_CELL_STAGE * cells / sec / 1e12
+        r = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s", "frac": achieved / alu,
+             "work_per_cell": "%d flops" % FLOPS_PER_CELL_STAGE, "peak_source": alu_src}
+    else:
+        achieved = bpc * cells / sec / 1e9
+        r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+             "work_per_cell": "%d bytes" % bpc, "peak_source": hbm_src}
+    r.update(common)
+    return r
 
 
 def load_peaks():
@@ -42,6 +106,22 @@ def load_peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+PREHEAT_S = 0.3
+
+
+def preheat(step, warmup):
+    """Run `warmup` untimed steps, then keep stepping (untimed) until the device
+    has been busy for PREHEAT_S seconds; returns the number of steps run."""
+    import torch
+    t0 = time.perf_counter()
+    n = 0
+    while n < warmup or time.perf_counter() - t0 < PREHEAT_S:
+        step()
+        n += 1
+    torch.cuda.synchronize()
+    return n
 
 
 def clocks_start():
@@ -163,15 +243,14 @@ def batch_arm(args, dist, rank, ws):
     for i, w in enumerate(wls):
         B.set_state(i, w.state)
     cfg = B.tune()
-    B.step_all(args.warmup)
-    B.sync()
-    acc0 = [B.stats(i)["accepted"] for i in range(len(wls))]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     cp, cpath = clocks_start()
     time.sleep(0.4)
+    warm_done = preheat(lambda: (B.step_all(1, graph=True), B.sync()), args.warmup)
+    acc0 = [B.stats(i)["accepted"] for i in range(len(wls))]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(B.stream)
     B.step_all(args.steps, graph=True)
     ev1.record(B.stream)
@@ -210,7 +289,7 @@ def batch_arm(args, dist, rank, ws):
             "config": {"workload": "batched: %d periodic 2D problems, sides from {64..512}, mu log-uniform "
                                    "[1e-4,1e-2], Mach 0.1-3, 25%% near-vacuum blasts (seed 5)" % len(wls),
                        "cells": int(sum(w.cells for w in wls)), "tuned": cfg, "restarts": restarts,
-                       "graph": True},
+                       "graph": True, "warmup_steps_run": warm_done},
             "clocks": clocks, "gpu_launches": nlaunch * args.steps,
             "fp64_one_by_one": {"value": one_cells / (one_ms / 1e3), "unit": UNIT,
                                 "sample": "first 16 problems, 2 FP64 steps each, one problem at a time"}}
@@ -252,16 +331,17 @@ def main():
         S = Solver.from_workload(w, precision=prec, stream=stream)
         S.set_state(w.state)
         tuned = S.tune()
-        for _ in range(args.warmup):
-            S.step(0.0)
-        torch.cuda.synchronize()
-        S.set_profiling(True)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        alu_pk = measure_alu_peaks()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         cp, cpath = clocks_start()
         time.sleep(0.4)
+        # warm-up right before the timed region: W steps, then more untimed steps
+        # until the GPU has been busy for PREHEAT_S (clocks up after the idle sleep)
+        warm_done = preheat(lambda: S.step(0.0), args.warmup)
+        S.set_profiling(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         restarts = 0
         for _ in range(args.steps):
@@ -306,21 +386,7 @@ def main():
         return
     peaks = load_peaks()
     stage_ms = prof["stage_ms"] / max(prof["stage_launches"], 1)
-    # algorithmic work per launch (one stage over all cells), see the design doc
-    if args.precision == "fp64":
-        flops_per_cell = FLOPS_PER_CELL_STAGE
-        achieved = flops_per_cell * cells / (stage_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "k_stage2d<double>", "work_per_cell": flops_per_cell,
-                    "peak_source": "published FP64 rate of B300 (not in MEASURED_PEAKS.json)"}
-    else:
-        bpc = BYTES_PER_CELL_STAGE_MIXED
-        achieved = bpc * cells / (stage_ms / 1e3) / 1e9
-        pk = peaks.get("hbm_gbs", 6400.0)
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
-                    "traffic": None, "kernel": "k_stage2d<float>", "work_per_cell": bpc,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    roofline = stage_roofline(args.precision, cells, stage_ms, peaks, alu_pk)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
@@ -330,7 +396,7 @@ def main():
                                    % (args.n, args.n),
                        "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (state %.0f MB per buffer, 5 buffers)" % (state_bytes / 1e6),
-                       "restarts": restarts, "tuned": tuned},
+                       "restarts": restarts, "tuned": tuned, "warmup_steps_run": warm_done},
             "roofline": roofline, "clocks": clocks,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes},
@@ -355,6 +421,7 @@ def main():
 # 4 compensation words per stage on average over the five SSP-RK54 stages).
 FLOPS_PER_CELL_STAGE = 3000
 BYTES_PER_CELL_STAGE_MIXED = 256
+BYTES_PER_CELL_STAGE_FP64 = 410
 
 
 if __name__ == "__main__":

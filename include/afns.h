@@ -191,6 +191,17 @@ const char *af_last_error(const afns_ctx *ctx);
  * calls that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.
  */
+/*
+ * Measured FMA throughput of the current device (the paper has no counterpart):
+ * the ALU roofline denominator of the stage kernels. precision AF_MIXED times
+ * FP32 FMA chains, AF_FP64 FP64 FMA chains (8 independent chains per thread,
+ * 8 CTAs of 256 threads per SM, one warm-up launch, then one launch timed with
+ * CUDA events on a stream of its own). *tflops receives 2 x FMAs / second / 1e12.
+ * Allocates and frees a small device buffer; synchronises its own stream.
+ * Returns AF_EINVAL for a bad argument, AF_ECUDA if a CUDA call failed.
+ */
+af_status af_alu_peak(int precision, double *tflops);
+
 #define AF_NOALLOC_CHUNK 4096
 #define AF_NOALLOC_MAX_CHUNKS 16384
 af_status af_dt_max_noalloc(const af_grid *grid, double gamma, double mu, double Pr, const af_opts *opts,

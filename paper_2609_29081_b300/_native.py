@@ -24,7 +24,7 @@ LIM_NONE, LIM_PP, LIM_S_PP = 0, 1, 2
 EXPORTED = ["af_opts_default", "af_workspace_bytes", "af_create", "af_destroy", "af_set_state",
             "af_get_state", "af_dt_max", "af_step", "af_advance", "af_residual", "af_get_limiter",
             "af_sizes", "af_set_profiling", "af_get_profile", "af_tune", "af_dt_max_noalloc",
-            "af_last_error"]
+            "af_alu_peak", "af_last_error"]
 
 
 class AfnsError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.af_sizes.argtypes = [vp, sp, sp, sp]
     L.af_tune.argtypes = [vp, ip, ip]
     L.af_dt_max_noalloc.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+    L.af_alu_peak.argtypes = [ctypes.c_int, dp]
     L.af_set_profiling.argtypes = [vp, ctypes.c_int]
     L.af_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     L.af_last_error.argtypes = [vp]
@@ -87,6 +88,16 @@ def load(path: str = LIB_PATH):
             getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def alu_peak(precision) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (FP32 for MIXED,
+    FP64 for FP64): the ALU roofline denominator of the stage kernels."""
+    v = ctypes.c_double(0.0)
+    rc = load().af_alu_peak(precision, ctypes.byref(v))
+    if rc != AF_OK:
+        raise AfnsError("af_alu_peak failed (status %d)" % rc)
+    return v.value
 
 
 def default_opts(dim, precision=FP64, limiter=LIM_S_PP, **kw) -> Opts:

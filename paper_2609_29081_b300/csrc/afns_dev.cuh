@@ -161,4 +161,32 @@ __device__ __forceinline__ ff ff_from(double x)
     return {h, __double2float_rn(x - (double)h)};
 }
 
+// --- asynchronous global -> shared copies of single 4- or 8-byte elements
+// (cp.async): a thread issues all its tile loads without waiting on any, then
+// one wait and a barrier publish them. The host-compiler pass of this header
+// (never executed on the GPU) copies synchronously.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *dst_shared, const T *src_global)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+#ifdef __CUDA_ARCH__
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src_global) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src_global) : "memory");
+#else
+    *dst_shared = *src_global;
+#endif
+}
+
+// Wait until every cp.async this thread issued has landed in shared memory
+// (other threads see them after the next barrier).
+__device__ __forceinline__ void cp_async_wait_all()
+{
+#ifdef __CUDA_ARCH__
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+#endif
+}
+
 }  // namespace afns

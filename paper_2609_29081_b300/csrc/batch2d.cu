@@ -169,11 +169,11 @@ __global__ void k_batch_ghost(BatchProb *probs, int in_idx, int pass)
 }
 
 // --- the persistent stage kernel over the work list
-template <class R, class S, int TX, int TY>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_stage(BatchArgs B)
+template <class R, class S, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, NTH>()) k_batch_stage(BatchArgs B)
 {
-    extern __shared__ __align__(16) unsigned char smem_batch[];
-    R *sm = reinterpret_cast<R *>(smem_batch);
+    extern __shared__ __align__(32) unsigned char smem_batch[];
+    V4<R> *sm = reinterpret_cast<V4<R> *>(smem_batch);
     for (int item = blockIdx.x; item < B.nitems; item += gridDim.x) {
         const int p = B.item_p[item];
         const BatchProb &P = B.probs[p];
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_batch_stage(Bat
         A.eps = B.eps;
         A.c_s = B.c_s;
         A.limiter = B.limiter;
-        stage_tile<R, S, TX, TY>(A, tile % P.tiles_x, tile / P.tiles_x, sm);
+        stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm);
         __syncthreads();
     }
 }
@@ -311,13 +311,31 @@ static const TileCfg kCandidates[] = {
     {16, 8, 256, 0}, {16, 8, 128, 0}, {16, 8, 256, 1}, {16, 8, 128, 1}, {32, 8, 256, 0}, {32, 8, 256, 1},
 };
 
-template <int TX, int TY>
-static size_t stage_smem(bool mixed)
-{
-    return (mixed ? sizeof(float) : sizeof(double)) * (size_t)Tile2<TX, TY>::total;
-}
-
 static int tile_index(int tx) { return tx == 32 ? 1 : 0; }
+
+// Persistent grid of the stage kernel for a configuration: one wave of resident
+// CTAs (SM count x CTAs per SM). Sets the dynamic shared-memory limit; called
+// outside any stream capture.
+template <class R, class S, int TX, int TY, int NTH>
+static cudaError_t batch_stage_grid_n(int nitems, int *grid)
+{
+    size_t smem = Tile2<TX, TY>::template bytes<R>();
+    cudaError_t e = cudaFuncSetAttribute(k_batch_stage<R, S, TX, TY, NTH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // the whole unified L1 as shared memory, so that the occupancy computed
+    // below is the one the launches get
+    e = cudaFuncSetAttribute(k_batch_stage<R, S, TX, TY, NTH>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 148, per_sm = 1;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<R, S, TX, TY, NTH>, NTH, smem);
+    if (e != cudaSuccess) return e;
+    *grid = std::max(1, std::min(nitems, nsm * std::max(per_sm, 1)));
+    return cudaSuccess;
+}
 
 // Persistent grid of the stage kernel for a configuration: one wave of resident
 // CTAs (SM count x CTAs per SM). Sets the dynamic shared-memory limit; called
@@ -325,24 +343,16 @@ static int tile_index(int tx) { return tx == 32 ? 1 : 0; }
 template <class R, class S, int TX, int TY>
 static cudaError_t batch_stage_grid(int threads, int nitems, int *grid)
 {
-    size_t smem = sizeof(R) * (size_t)Tile2<TX, TY>::total;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_batch_stage<R, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 148, per_sm = 1;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_stage<R, S, TX, TY>, threads, smem);
-    if (e != cudaSuccess) return e;
-    *grid = std::max(1, std::min(nitems, nsm * std::max(per_sm, 1)));
-    return cudaSuccess;
+    if (threads == 128) return batch_stage_grid_n<R, S, TX, TY, 128>(nitems, grid);
+    return batch_stage_grid_n<R, S, TX, TY, 256>(nitems, grid);
 }
 
 template <class R, class S, int TX, int TY>
 static cudaError_t launch_batch_stage_t(const BatchArgs &B, int threads, int grid, cudaStream_t st)
 {
-    size_t smem = sizeof(R) * (size_t)Tile2<TX, TY>::total;
-    k_batch_stage<R, S, TX, TY><<<grid, threads, smem, st>>>(B);
+    size_t smem = Tile2<TX, TY>::template bytes<R>();
+    if (threads == 128) k_batch_stage<R, S, TX, TY, 128><<<grid, 128, smem, st>>>(B);
+    else k_batch_stage<R, S, TX, TY, 256><<<grid, 256, smem, st>>>(B);
     return cudaGetLastError();
 }
 

@@ -20,21 +20,34 @@ cudaError_t launch_ghost2d(const Layout &L, S *buf, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <class R, class S, int TX, int TY>
-cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st, int threads = 256)
+template <class R, class S, int TX, int TY, int NTH>
+cudaError_t launch_stage2d_n(const StageArgs &A, cudaStream_t st)
 {
     using T = Tile2<TX, TY>;
-    size_t smem = sizeof(R) * (size_t)T::total;
+    size_t smem = T::template bytes<R>();
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage2d<R, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_stage2d<R, S, TX, TY, NTH>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        // the whole unified L1 as shared memory: without a preference the driver
+        // may pick a smaller carveout and fit fewer tiles per SM
+        e = cudaFuncSetAttribute(k_stage2d<R, S, TX, TY, NTH>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((A.L.n1 + TX - 1) / TX, (A.L.n2 + TY - 1) / TY);
-    k_stage2d<R, S, TX, TY><<<grid, threads, smem, st>>>(A);
+    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A);
     return cudaGetLastError();
+}
+
+// threads: 128 or 256 per CTA (a compile-time constant of the kernel)
+template <class R, class S, int TX, int TY>
+cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st, int threads = 256)
+{
+    if (threads == 128) return launch_stage2d_n<R, S, TX, TY, 128>(A, st);
+    return launch_stage2d_n<R, S, TX, TY, 256>(A, st);
 }
 
 // Tile shapes: FP64 16x8 only (the 32x8 FP64 tile exceeds shared memory); FP32

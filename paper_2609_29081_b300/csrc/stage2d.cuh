@@ -43,17 +43,26 @@ struct Tile2 {
     static constexpr int CX = TX + 4, CY = TY + 4, NCA = CX * CY;   // cells with 2 halo
     static constexpr int QX = TX + 2, QY = TY + 2, NCQ = QX * QY;   // cells with 1 halo
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-    // shared-memory offsets in units of the compute type
-    static constexpr int oU = 0;                 // 4 x NL conservative
-    static constexpr int oQ = oU + 4 * NL;       // u, v, T, c
-    static constexpr int oGX = oQ + 4 * NL;      // d/dx of u, v, T
-    static constexpr int oGY = oGX + 3 * NL;     // d/dy of u, v, T
-    static constexpr int oA = oGY + 3 * NL;      // 4 x NCA cell averages
-    static constexpr int oAW = oA + 4 * NCA;     // u, v, p, T of cell averages
-    static constexpr int oCQ = oAW + 4 * NCA;    // 14 x NCQ low-order cell quantities
-    static constexpr int oFX = oCQ + 14 * NCQ;   // 4 x NFX limited x-face fluxes
-    static constexpr int oFY = oFX + 4 * NFX;    // 4 x NFY limited y-face fluxes
-    static constexpr int total = oFY + 4 * NFY;
+    // shared-memory offsets in units of V4 (one node / cell / face record)
+    static constexpr int oU = 0;                 // NL  x (rho, rho u, rho v, E)
+    static constexpr int oQ = oU + NL;           // NL  x (u, v, T, c)
+    static constexpr int oGX = oQ + NL;          // NL  x d/dx (u, v, T, -)
+    static constexpr int oGY = oGX + NL;         // NL  x d/dy (u, v, T, -)
+    static constexpr int oA = oGY + NL;          // NCA x cell averages
+    static constexpr int oAW = oA + NCA;         // NCA x (u, v, p, T) of the averages
+    static constexpr int oCQ = oAW + NCA;        // NCQ x 4 records of low-order cell quantities
+    static constexpr int oFX = oCQ + 4 * NCQ;    // NFX x limited x-face flux
+    static constexpr int oFY = oFX + NFX;        // NFY x limited y-face flux
+    static constexpr int total = oFY + NFY;      // in V4 records
+    template <class R>
+    static constexpr size_t bytes() { return (size_t)total * 4 * sizeof(R); }
+};
+
+// Four values of one lattice node, cell or face, stored together so that one
+// vector instruction moves them (16-byte shared-memory accesses in FP32).
+template <class R>
+struct alignas(4 * sizeof(R)) V4 {
+    R x, y, z, w;
 };
 
 // Per-tile constants in the compute precision, derived once per tile by one
@@ -117,8 +126,9 @@ __device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs
     }
 }
 
-// Low-order cell quantity slots
-enum { CQ_FX = 0, CQ_FY = 4, CQ_RX = 8, CQ_RY = 9, CQ_BX = 10, CQ_BY = 11, CQ_P1 = 12, CQ_P2 = 13 };
+// Records of the low-order cell quantities (4 consecutive V4 per cell):
+// [0] total flux F_x, [1] total flux F_y, [2] (rho_x, rho_y, b_x, b_y), [3] (phi1, phi2, -, -)
+enum { CQ_FX = 0, CQ_FY = 1, CQ_RB = 2, CQ_PH = 3 };
 
 // D_c weights (x 1/(6 dx)) and fourth-difference weights of (D_+ - D_-)/2 (x 1/(6 dx))
 __device__ __constant__ static const double kDC[5] = {1.0, -8.0, 0.0, 8.0, -1.0};

@@ -15,7 +15,7 @@ template <class S>
 __global__ void k_ghost2d(Layout L, S *buf, int pass)
 {
     const int nsite = 4;
-    // x pass: (site, row j in [-0, n2], ghost column g in 0..4)
+    // x pass: (site, row j in [0, n2], ghost column g in 0..4)
     // y pass: (site, column i in [-2, n1+2], ghost row g in 0..4)
     int span = pass == 0 ? (L.n2 + 1) : (L.n1 + 5);
     int total = nsite * span * 5;
@@ -50,50 +50,54 @@ __global__ void k_ghost2d(Layout L, S *buf, int pass)
     }
 }
 
+template <class R>
+__device__ __forceinline__ R comp(const V4<R> &v, int c)
+{
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+
 // ---------------------------------------------------------------------------
 // Point-value residual of Eq. (12) at lattice node n of the shared tile.
+// sU: conservative, sQ: (u, v, T, c), sGX / sGY: D_c gradients of (u, v, T).
 // ---------------------------------------------------------------------------
 template <class R, int TX, int TY>
-__device__ __forceinline__ void point_residual(const R *sm, int n, const TileConst<R> &tc, R res[4])
+__device__ __forceinline__ void point_residual(const V4<R> *sm, int n, const TileConst<R> &tc, R res[4])
 {
     using T = Tile2<TX, TY>;
-    constexpr int NL = T::NL, LX = T::LX;
-    const R *U0 = sm + T::oU, *U1 = U0 + NL, *U2 = U1 + NL, *U3 = U2 + NL;
-    const R *qu = sm + T::oQ, *qv = qu + NL, *qT = qv + NL, *qc = qT + NL;
-    const R *gxu = sm + T::oGX, *gxv = gxu + NL;
-    const R *gyu = sm + T::oGY, *gyv = gyu + NL;
+    constexpr int LX = T::LX;
+    const V4<R> *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
     const R mu = tc.mu, ka = tc.ka;
     res[0] = res[1] = res[2] = res[3] = R(0);
     const R mu43 = R(4) / R(3) * mu, mu23 = R(2) / R(3) * mu;
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
         const int st = l == 0 ? 1 : LX;
-        const R inv6h = tc.i6[l];
+        V4<R> q[5], u[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            q[k] = sQ[n + (k - 2) * st];
+            u[k] = sU[n + (k - 2) * st];
+        }
         // --- inviscid: D_+ F^+ + D_- F^- = [sum_k dc_k F_k + alpha d4_k U_k] / (6 h)
         R al = R(0);
 #pragma unroll
-        for (int k = -2; k <= 2; ++k) {
-            int m = n + k * st;
-            R vel = l == 0 ? qu[m] : qv[m];
-            al = dmax(al, fabs(vel) + qc[m]);
-        }
+        for (int k = 0; k < 5; ++k) al = dmax(al, fabs(l == 0 ? q[k].x : q[k].y) + q[k].w);
         R f0 = 0, f1 = 0, f2 = 0, f3 = 0;
 #pragma unroll
-        for (int k = -2; k <= 2; ++k) {
-            int m = n + k * st;
-            R rho = U0[m], mx = U1[m], my = U2[m], E = U3[m];
-            R p = rho * qT[m];
-            R ul = l == 0 ? qu[m] : qv[m];
-            R F0 = l == 0 ? mx : my;
-            R F1 = mx * ul + (l == 0 ? p : R(0));
-            R F2 = my * ul + (l == 1 ? p : R(0));
-            R F3 = (E + p) * ul;
-            R wc = (R)kDC[k + 2], w4 = al * (R)kD4[k + 2];
-            f0 += wc * F0 + w4 * rho;
-            f1 += wc * F1 + w4 * mx;
-            f2 += wc * F2 + w4 * my;
-            f3 += wc * F3 + w4 * E;
+        for (int k = 0; k < 5; ++k) {
+            const R p = u[k].x * q[k].z;   // rho T
+            const R ul = l == 0 ? q[k].x : q[k].y;
+            const R F0 = l == 0 ? u[k].y : u[k].z;
+            const R F1 = u[k].y * ul + (l == 0 ? p : R(0));
+            const R F2 = u[k].z * ul + (l == 1 ? p : R(0));
+            const R F3 = (u[k].w + p) * ul;
+            const R wc = (R)kDC[k], w4 = al * (R)kD4[k];
+            f0 += wc * F0 + w4 * u[k].x;
+            f1 += wc * F1 + w4 * u[k].y;
+            f2 += wc * F2 + w4 * u[k].z;
+            f3 += wc * F3 + w4 * u[k].w;
         }
+        const R inv6h = tc.i6[l];
         res[0] -= f0 * inv6h;
         res[1] -= f1 * inv6h;
         res[2] -= f2 * inv6h;
@@ -103,19 +107,18 @@ __device__ __forceinline__ void point_residual(const R *sm, int n, const TileCon
         const R c2 = l == 0 ? mu : mu43;   // K_ll entry on v
         R d2u = 0, d2v = 0, d2T = 0, eq = 0;
 #pragma unroll
-        for (int k = -2; k <= 2; ++k) {
-            int m = n + k * st;
-            d2u += (R)kD2[k + 2] * qu[m];
-            d2v += (R)kD2[k + 2] * qv[m];
-            d2T += (R)kD2[k + 2] * qT[m];
+        for (int m = 0; m < 5; ++m) {
+            d2u += (R)kD2[m] * q[m].x;
+            d2v += (R)kD2[m] * q[m].y;
+            d2T += (R)kD2[m] * q[m].z;
             R bu = 0, bv = 0;
 #pragma unroll
-            for (int q = -2; q <= 2; ++q) {
-                if (kB[k + 2][q + 2] == 0.0) continue;
-                bu += (R)kB[k + 2][q + 2] * qu[n + q * st];
-                bv += (R)kB[k + 2][q + 2] * qv[n + q * st];
+            for (int nn = 0; nn < 5; ++nn) {
+                if (kB[m][nn] == 0.0) continue;
+                bu += (R)kB[m][nn] * q[nn].x;
+                bv += (R)kB[m][nn] * q[nn].y;
             }
-            eq += c1 * qu[m] * bu + c2 * qv[m] * bv;
+            eq += c1 * q[m].x * bu + c2 * q[m].y * bv;
         }
         const R i3h2 = tc.i3h2[l];   // (4/dx^2)/12
         res[1] += c1 * d2u * i3h2;
@@ -124,20 +127,19 @@ __device__ __forceinline__ void point_residual(const R *sm, int n, const TileCon
         // --- viscous, mixed: D_c^{(l)}(K_lm D_c^{(m)} Z), m != l
         R g1 = 0, g2 = 0, g3 = 0;
 #pragma unroll
-        for (int k = -2; k <= 2; ++k) {
-            if (k == 0) continue;
-            int m = n + k * st;
-            R wc = (R)kDC[k + 2];
+        for (int k = 0; k < 5; ++k) {
+            if (k == 2) continue;
+            const R wc = (R)kDC[k];
             if (l == 0) {   // K_12 d_y Z
-                R uy = gyu[m], vy = gyv[m];
-                g1 += wc * (-mu23 * vy);
-                g2 += wc * (mu * uy);
-                g3 += wc * (mu * qv[m] * uy - mu23 * qu[m] * vy);
+                const V4<R> gy = sGY[n + (k - 2)];
+                g1 += wc * (-mu23 * gy.y);
+                g2 += wc * (mu * gy.x);
+                g3 += wc * (mu * q[k].y * gy.x - mu23 * q[k].x * gy.y);
             } else {        // K_21 d_x Z
-                R ux = gxu[m], vx = gxv[m];
-                g1 += wc * (mu * vx);
-                g2 += wc * (-mu23 * ux);
-                g3 += wc * (-mu23 * qv[m] * ux + mu * qu[m] * vx);
+                const V4<R> gx = sGX[n + (k - 2) * LX];
+                g1 += wc * (mu * gx.y);
+                g2 += wc * (-mu23 * gx.x);
+                g3 += wc * (-mu23 * q[k].y * gx.x + mu * q[k].x * gx.y);
             }
         }
         res[1] += g1 * inv6h;
@@ -173,24 +175,24 @@ __device__ __forceinline__ void node_flux(int l, R rho, R mx, R my, R E, R u, R 
 // lattice (point low-order update, Sec. 3.4 reading): Eq. (19) with S from
 // central differences on the lattice. FP64.
 template <class R, int TX, int TY>
-__device__ void lattice_llf(const R *sm, int l, int A, int B, double dx, double dy, double gamma, double mu,
+__device__ void lattice_llf(const V4<R> *sm, int l, int A, int B, double dx, double dy, double gamma, double mu,
                             double ka, double F[4])
 {
     using T = Tile2<TX, TY>;
-    constexpr int NL = T::NL, LX = T::LX;
-    const R *U = sm + T::oU;
-    const R *qu = sm + T::oQ, *qv = qu + NL, *qT = qv + NL;
+    constexpr int LX = T::LX;
+    const V4<R> *sU = sm + T::oU, *sQ = sm + T::oQ;
     double Fs[2][4], Us[2][4], rs[2], bs[2];
     const double gm1 = gamma - 1.0;
     for (int s = 0; s < 2; ++s) {
-        int n = s == 0 ? A : B;
-        double Uv[4] = {(double)U[n], (double)U[NL + n], (double)U[2 * NL + n], (double)U[3 * NL + n]};
+        const int n = s == 0 ? A : B;
+        const V4<R> un = sU[n];
+        double Uv[4] = {(double)un.x, (double)un.y, (double)un.z, (double)un.w};
+        const V4<R> qe = sQ[n + 1], qw = sQ[n - 1], qn = sQ[n + LX], qs = sQ[n - LX];
         // S: central differences on the lattice (spacing h/2, so 2 * (h/2) = h)
-        double Sx[3] = {((double)qu[n + 1] - (double)qu[n - 1]) / dx, ((double)qv[n + 1] - (double)qv[n - 1]) / dx,
-                        ((double)qT[n + 1] - (double)qT[n - 1]) / dx};
-        double Sy[3] = {((double)qu[n + LX] - (double)qu[n - LX]) / dy,
-                        ((double)qv[n + LX] - (double)qv[n - LX]) / dy,
-                        ((double)qT[n + LX] - (double)qT[n - LX]) / dy};
+        double Sx[3] = {((double)qe.x - (double)qw.x) / dx, ((double)qe.y - (double)qw.y) / dx,
+                        ((double)qe.z - (double)qw.z) / dx};
+        double Sy[3] = {((double)qn.x - (double)qs.x) / dy, ((double)qn.y - (double)qs.y) / dy,
+                        ((double)qn.z - (double)qs.z) / dy};
         double rho = Uv[0], u = Uv[1] / rho, v = Uv[2] / rho;
         double p = gm1 * (Uv[3] - (Uv[1] * Uv[1] + Uv[2] * Uv[2]) / (2.0 * rho));
         double Fl[4];
@@ -221,91 +223,101 @@ __device__ void lattice_llf(const R *sm, int l, int A, int B, double dx, double 
 // ---------------------------------------------------------------------------
 // One tile (bx, by) of one problem; the single-problem kernel runs one tile per
 // CTA, the batched persistent kernel loops over (problem, tile) work items.
-template <class R, class S, int TX, int TY>
-__device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R *sm)
+template <class R, class S, int TX, int TY, int NTH>
+__device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm)
 {
     using T = Tile2<TX, TY>;
+    using Q4 = V4<R>;
     constexpr int NL = T::NL, LX = T::LX, CX = T::CX, QX = T::QX;
     __shared__ int s_bad;
+    __shared__ TileConst<R> tc;
     const Layout &L = A.L;
     const int i0 = bx * TX, j0 = by * TY;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int tid = threadIdx.x;
+    constexpr int nth = NTH;
     const int ntx = min(TX, L.n1 - i0), nty = min(TY, L.n2 - j0);
-    if (tid == 0) s_bad = 0;
-    __shared__ TileConst<R> tc;
     const double dt = A.ctl->dt;
     const double eps = A.eps;
-    if (tid == 0) tile_const_init<R>(tc, A, dt);
-    R *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
-    R *sA = sm + T::oA, *sAW = sm + T::oAW, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
+    if (tid == 0) {
+        s_bad = 0;
+        tile_const_init<R>(tc, A, dt);
+    }
+    Q4 *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
+    Q4 *sA = sm + T::oA, *sAW = sm + T::oAW, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
+    const S *uin = (const S *)A.uin;
+    const Q4 benign = {R(1), R(0), R(0), R(2.5)};
 
-    // ---- P0: load point values and cell averages (two-node / two-cell halo)
+    // ---- P0: load point values and cell averages (two-node / two-cell halo),
+    // asynchronously: every load of the thread is in flight before the one wait
+    static_assert(sizeof(R) == sizeof(S), "tile and storage precision are the same");
     for (int t = tid; t < NL; t += nth) {
-        int la = t % LX, lb = t / LX;
-        int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
-        bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+        const int la = t % LX, lb = t / LX;
+        const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+        const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
         if (!ea && !eb) continue;
-        int site = ea ? (eb ? 3 : 1) : 2;
-        int i = ea ? (a >> 1) : ((a - 1) >> 1);
-        int j = eb ? (b >> 1) : ((b - 1) >> 1);
-        bool inb = i <= L.n1 + 2 && j <= L.n2 + 2;
-        long long off = cell_off(L, i, j);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            sU[c * NL + t] = inb ? (R)((const S *)A.uin)[plane_of(L, site, c) + off]
-                                 : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
+        const int site = ea ? (eb ? 3 : 1) : 2;
+        const int i = ea ? (a >> 1) : ((a - 1) >> 1);
+        const int j = eb ? (b >> 1) : ((b - 1) >> 1);
+        if (i <= L.n1 + 2 && j <= L.n2 + 2) {
+            const S *g = uin + plane_of(L, site, 0) + cell_off(L, i, j);
+            cp_async_elem(&sU[t].x, g);
+            cp_async_elem(&sU[t].y, g + L.plane);
+            cp_async_elem(&sU[t].z, g + 2 * L.plane);
+            cp_async_elem(&sU[t].w, g + 3 * L.plane);
+        } else {
+            sU[t] = benign;
+        }
     }
     for (int t = tid; t < T::NCA; t += nth) {
-        int ci = t % CX, cj = t / CX;
-        int i = i0 - 2 + ci, j = j0 - 2 + cj;
-        bool inb = i <= L.n1 + 2 && j <= L.n2 + 2;
-        long long off = cell_off(L, i, j);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            sA[c * T::NCA + t] = inb ? (R)((const S *)A.uin)[plane_of(L, 0, c) + off]
-                                     : (c == 0 ? R(1) : c == 3 ? R(2.5) : R(0));
+        const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
+        if (i <= L.n1 + 2 && j <= L.n2 + 2) {
+            const S *g = uin + plane_of(L, 0, 0) + cell_off(L, i, j);
+            cp_async_elem(&sA[t].x, g);
+            cp_async_elem(&sA[t].y, g + L.plane);
+            cp_async_elem(&sA[t].z, g + 2 * L.plane);
+            cp_async_elem(&sA[t].w, g + 3 * L.plane);
+        } else {
+            sA[t] = benign;
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
-    const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka, dx = tc.dx, dy = tc.dy;
+    const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka;
 
-    // ---- P1: cell centres (Simpson inversion) + centre scaling limiter
+    // ---- P1: cell centres (Simpson inversion, Sec. 2.2) + centre scaling limiter (Remark 3.1)
     for (int t = tid; t < T::NCQ; t += nth) {
-        int qi = t % QX, qj = t / QX;
-        int n = (2 * qj + 1) * LX + (2 * qi + 1);
-        int ca = (qj + 1) * CX + (qi + 1);
+        const int qi = t % QX, qj = t / QX;
+        const int n = (2 * qj + 1) * LX + (2 * qi + 1);
+        const Q4 ab = sA[(qj + 1) * CX + (qi + 1)];
+        const Q4 e0 = sU[n - 1], e1 = sU[n + 1], e2 = sU[n - LX], e3 = sU[n + LX];
+        const Q4 v0 = sU[n - LX - 1], v1 = sU[n - LX + 1], v2 = sU[n + LX - 1], v3 = sU[n + LX + 1];
         R Uc[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const R *P = sU + c * NL;
-            R edges = P[n - 1] + P[n + 1] + P[n - LX] + P[n + LX];
-            R verts = P[n - LX - 1] + P[n - LX + 1] + P[n + LX - 1] + P[n + LX + 1];
-            Uc[c] = (R(36) * sA[c * T::NCA + ca] - R(4) * edges - verts) / R(16);
+            const R edges = comp(e0, c) + comp(e1, c) + comp(e2, c) + comp(e3, c);
+            const R verts = comp(v0, c) + comp(v1, c) + comp(v2, c) + comp(v3, c);
+            Uc[c] = (R(36) * comp(ab, c) - R(4) * edges - verts) / R(16);
         }
         if (A.limiter != LIM_NONE) {
             R mag[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const R *P = sU + c * NL;
-                mag[c] = R(4) * (fabs(sA[c * T::NCA + ca]) + fabs(P[n - 1]) + fabs(P[n + 1]) + fabs(P[n - LX]) +
-                                 fabs(P[n + LX]));
-            }
+            for (int c = 0; c < 4; ++c)
+                mag[c] = R(4) * (fabs(comp(ab, c)) + fabs(comp(e0, c)) + fabs(comp(e1, c)) + fabs(comp(e2, c)) +
+                                 fabs(comp(e3, c)));
             if (!surely_above(Uc, mag, gm1, tc.eps)) {
                 // FP64 island: the centre in FP64 (same expression), then the scaling
                 // toward the cell average of Remark 3.1 if it is below epsilon
                 double Ub[4], Ud[4];
                 for (int c = 0; c < 4; ++c) {
-                    const R *P = sU + c * NL;
-                    double edges = (double)P[n - 1] + (double)P[n + 1] + (double)P[n - LX] + (double)P[n + LX];
-                    double verts = (double)P[n - LX - 1] + (double)P[n - LX + 1] + (double)P[n + LX - 1] +
-                                   (double)P[n + LX + 1];
-                    Ub[c] = (double)sA[c * T::NCA + ca];
+                    double edges = (double)comp(e0, c) + (double)comp(e1, c) + (double)comp(e2, c) + (double)comp(e3, c);
+                    double verts = (double)comp(v0, c) + (double)comp(v1, c) + (double)comp(v2, c) + (double)comp(v3, c);
+                    Ub[c] = (double)comp(ab, c);
                     Ud[c] = (36.0 * Ub[c] - 4.0 * edges - verts) / 16.0;
                 }
                 double g1 = A.gamma - 1.0;
                 double pc = g1 * (Ud[3] - (Ud[1] * Ud[1] + Ud[2] * Ud[2]) / (2.0 * Ud[0]));
                 if (!(Ud[0] >= eps) || !(pc >= eps)) {
-                    double rL = Ub[0];
-                    double thr = theta_fn(rL, Ud[0], fmin(eps, rL));
+                    double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
                     double Ur[4];
                     for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
                     double pL = g1 * (Ub[3] - (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / (2.0 * Ub[0]));
@@ -316,61 +328,48 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 for (int c = 0; c < 4; ++c) Uc[c] = (R)Ud[c];
             }
         }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) sU[c * NL + n] = Uc[c];
+        sU[n] = Q4{Uc[0], Uc[1], Uc[2], Uc[3]};
     }
     __syncthreads();
 
-    // ---- P2: primitive quantities at every lattice node and every cell
-    // one reciprocal of rho per node: u = m_x / rho, v = m_y / rho, p = (gamma-1)(E - (m.u)/2), T = p / rho
+    // ---- P2: primitive quantities at every lattice node and every cell; one
+    // reciprocal of rho each: u = m_x/rho, v = m_y/rho, p = (gamma-1)(E - m.u/2), T = p/rho
     for (int t = tid; t < NL; t += nth) {
-        R rho = sU[t], mx = sU[NL + t], my = sU[2 * NL + t], E = sU[3 * NL + t];
-        R r = R(1) / rho, u = mx * r, v = my * r;
-        R p = gm1 * (E - R(0.5) * (mx * u + my * v));
-        R Tn = p * r;
-        sQ[t] = u;
-        sQ[NL + t] = v;
-        sQ[2 * NL + t] = Tn;
-        sQ[3 * NL + t] = sqrt(gam * Tn);
+        const Q4 U = sU[t];
+        const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
+        const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
+        const R Tn = p * r;
+        sQ[t] = Q4{u, v, Tn, sqrt(gam * Tn)};
     }
     for (int t = tid; t < T::NCA; t += nth) {
-        R rho = sA[t], mx = sA[T::NCA + t], my = sA[2 * T::NCA + t], E = sA[3 * T::NCA + t];
-        R r = R(1) / rho, u = mx * r, v = my * r;
-        R p = gm1 * (E - R(0.5) * (mx * u + my * v));
-        sAW[t] = u;
-        sAW[T::NCA + t] = v;
-        sAW[2 * T::NCA + t] = p;
-        sAW[3 * T::NCA + t] = p * r;
+        const Q4 U = sA[t];
+        const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
+        const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
+        sAW[t] = Q4{u, v, p, p * r};
     }
     __syncthreads();
 
-    // ---- P3: D_c gradients of Z = (u, v, T) along x and along y
+    // ---- P3: D_c gradients (Eq. (8)) of Z = (u, v, T) along x and along y
     {
         const R i6x = tc.i6[0], i6y = tc.i6[1];
         const int nx = (LX - 4) * T::LY;
         for (int t = tid; t < nx; t += nth) {
-            int la = 2 + t % (LX - 4), lb = t / (LX - 4);
-            int n = lb * LX + la;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const R *z = sQ + c * NL;
-                sGX[c * NL + n] = (z[n - 2] - R(8) * z[n - 1] + R(8) * z[n + 1] - z[n + 2]) * i6x;
-            }
+            const int n = (t / (LX - 4)) * LX + 2 + t % (LX - 4);
+            const Q4 a = sQ[n - 2], b = sQ[n - 1], c = sQ[n + 1], d = sQ[n + 2];
+            sGX[n] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6x, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6x,
+                        (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6x, R(0)};
         }
         const int ny = LX * (T::LY - 4);
         for (int t = tid; t < ny; t += nth) {
-            int la = t % LX, lb = 2 + t / LX;
-            int n = lb * LX + la;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const R *z = sQ + c * NL;
-                sGY[c * NL + n] = (z[n - 2 * LX] - R(8) * z[n - LX] + R(8) * z[n + LX] - z[n + 2 * LX]) * i6y;
-            }
+            const int n = (2 + t / LX) * LX + t % LX;
+            const Q4 a = sQ[n - 2 * LX], b = sQ[n - LX], c = sQ[n + LX], d = sQ[n + 2 * LX];
+            sGY[n] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6y, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6y,
+                        (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6y, R(0)};
         }
     }
     __syncthreads();
 
-    // ---- P4: point residual, point scaling limiter, RK combination, store
+    // ---- P4: point residual, point scaling limiter (Sec. 3.4), RK combination, store
     {
         const bool perx = L.bc[0] == BC_PERIODIC, pery = L.bc[2] == BC_PERIODIC;
         const bool lastx = i0 + ntx == L.n1, lasty = j0 + nty == L.n2;
@@ -382,8 +381,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         for (int t = tid; t < tot; t += nth) {
             int la, lb;
             if (t < nreg) {
-                int kind = t / ncell, cc = t % ncell;
-                int il = cc % ntx, jl = cc / ntx;
+                const int kind = t / ncell, cc = t % ncell;
+                const int il = cc % ntx, jl = cc / ntx;
                 la = 2 + 2 * il + (kind == 1 ? 1 : 0);
                 lb = 2 + 2 * jl + (kind == 0 ? 1 : 0);
             } else if (t < nreg + ecol) {
@@ -397,10 +396,28 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 lb = 2 + 2 * nty;
             }
             const int n = lb * LX + la;
+            // global position of the point; the combination inputs (u^n, the
+            // auxiliary state) are loaded first so that their latency hides
+            // behind the residual
+            const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+            const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+            const int site = ea ? (eb ? 3 : 1) : 2;
+            const long long po0 = plane_of(L, site, 0) + cell_off(L, ea ? (a >> 1) : ((a - 1) >> 1),
+                                                                   eb ? (b >> 1) : ((b - 1) >> 1));
+            S g0[4] = {S(0), S(0), S(0), S(0)}, g2[4] = {S(0), S(0), S(0), S(0)};
+            if (tc.ua0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) g0[c] = ((const S *)A.u0)[po0 + c * L.plane];
+            }
+            if (tc.ua2 || A.k.acc) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) g2[c] = ((const S *)A.aux)[po0 + c * L.plane];
+            }
             R r[4];
             point_residual<R, TX, TY>(sm, n, tc, r);
             // the RK combination of point values runs in the storage precision S
-            const R Un[4] = {sU[n], sU[NL + n], sU[2 * NL + n], sU[3 * NL + n]};
+            const Q4 Un4 = sU[n];
+            const R Un[4] = {Un4.x, Un4.y, Un4.z, Un4.w};
             S res[4] = {(S)r[0], (S)r[1], (S)r[2], (S)r[3]};
             S U[4] = {(S)Un[0], (S)Un[1], (S)Un[2], (S)Un[3]};
             if (A.limiter != LIM_NONE) {
@@ -420,7 +437,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                     if (!(UH[0] >= eps) || !(pH >= eps)) {
                         double UL[4] = {Ud[0], Ud[1], Ud[2], Ud[3]};
                         for (int l = 0; l < 2; ++l) {
-                            int st = l == 0 ? 1 : LX;
+                            const int st = l == 0 ? 1 : LX;
                             double Fr[4], Fl[4];
                             lattice_llf<R, TX, TY>(sm, l, n, n + st, L.dx, L.dy, A.gamma, A.mu, A.kappa, Fr);
                             lattice_llf<R, TX, TY>(sm, l, n - st, n, L.dx, L.dy, A.gamma, A.mu, A.kappa, Fl);
@@ -439,31 +456,23 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 }
             }
             // store
-            int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
-            bool ea = (a & 1) == 0, eb = (b & 1) == 0;
-            int site = ea ? (eb ? 3 : 1) : 2;
-            int i = ea ? (a >> 1) : ((a - 1) >> 1);
-            int j = eb ? (b >> 1) : ((b - 1) >> 1);
-            long long off = cell_off(L, i, j);
             S o[4];
             const S ws = tc.w;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                long long po = plane_of(L, site, c) + off;
                 S v = A.k.residual ? S(0) : tc.a1 * U[c];
-                if (tc.ua0) v += tc.a0 * ((const S *)A.u0)[po];
-                if (tc.ua2) v += tc.a2 * ((const S *)A.aux)[po];
+                if (tc.ua0) v += tc.a0 * g0[c];
+                if (tc.ua2) v += tc.a2 * g2[c];
                 o[c] = v + ws * res[c];
-                if (A.k.acc)
-                    ((S *)A.aux)[po] = tc.b2 * ((const S *)A.aux)[po] + tc.b1 * U[c] + tc.bldt * res[c];
+                if (A.k.acc) ((S *)A.aux)[po0 + c * L.plane] = tc.b2 * g2[c] + tc.b1 * U[c] + tc.bldt * res[c];
             }
             if (A.k.wall_fix) {
                 // wall point values: zero (normal) momentum, internal energy kept
                 for (int side = 0; side < 4; ++side) {
-                    int kind = L.bc[side];
+                    const int kind = L.bc[side];
                     if (kind != BC_WALL && kind != BC_SYMMETRY) continue;
-                    int l = side >> 1;
-                    int pos = l == 0 ? a : b, lim = (side & 1) ? 2 * (l == 0 ? L.n1 : L.n2) : 0;
+                    const int l = side >> 1;
+                    const int pos = l == 0 ? a : b, lim = (side & 1) ? 2 * (l == 0 ? L.n1 : L.n2) : 0;
                     if (pos != lim) continue;
                     S ke0 = o[1] * o[1] + o[2] * o[2];
                     if (kind == BC_WALL || l == 0) o[1] = S(0);
@@ -473,58 +482,48 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) ((S *)A.out)[plane_of(L, site, c) + off] = o[c];
+            for (int c = 0; c < 4; ++c) ((S *)A.out)[po0 + c * L.plane] = o[c];
         }
     }
 
-    // ---- P5a: low-order cell quantities on cells [i0-1, i0+TX] x [j0-1, j0+TY]
+    // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
     for (int t = tid; t < T::NCQ; t += nth) {
-        int qi = t % QX, qj = t / QX;
-        int ca = (qj + 1) * CX + (qi + 1);
-        const R *Au = sAW, *Av = sAW + T::NCA, *Ap = sAW + 2 * T::NCA, *AT = sAW + 3 * T::NCA;
-        R rho = sA[ca], mx = sA[T::NCA + ca], my = sA[2 * T::NCA + ca], E = sA[3 * T::NCA + ca];
-        R u = Au[ca], v = Av[ca], p = Ap[ca];
+        const int ca = (t / QX + 1) * CX + (t % QX + 1);
+        const Q4 U = sA[ca], W = sAW[ca];
+        const Q4 We = sAW[ca + 1], Ww = sAW[ca - 1], Wn = sAW[ca + CX], Ws = sAW[ca - CX];
         const R i2x = tc.i2[0], i2y = tc.i2[1];
-        R Sxu = (Au[ca + 1] - Au[ca - 1]) * i2x, Sxv = (Av[ca + 1] - Av[ca - 1]) * i2x,
-          SxT = (AT[ca + 1] - AT[ca - 1]) * i2x;
-        R Syu = (Au[ca + CX] - Au[ca - CX]) * i2y, Syv = (Av[ca + CX] - Av[ca - CX]) * i2y,
-          SyT = (AT[ca + CX] - AT[ca - CX]) * i2y;
+        const R Sxu = (We.x - Ww.x) * i2x, Sxv = (We.y - Ww.y) * i2x, SxT = (We.w - Ww.w) * i2x;
+        const R Syu = (Wn.x - Ws.x) * i2y, Syv = (Wn.y - Ws.y) * i2y, SyT = (Wn.w - Ws.w) * i2y;
+        const R rho = U.x, u = W.x, v = W.y, p = W.z, Tc = W.w;
         R Fx[4], Fy[4];
-        const R Tc = AT[ca];
-        node_flux<R>(0, rho, mx, my, E, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fx);
-        node_flux<R>(1, rho, mx, my, E, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fy);
-        R *q = sCQ + t;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            q[(CQ_FX + c) * T::NCQ] = Fx[c];
-            q[(CQ_FY + c) * T::NCQ] = Fy[c];
-        }
-        R cs = sqrt(gam * Tc);
-        q[CQ_RX * T::NCQ] = fabs(u) + cs;
-        q[CQ_RY * T::NCQ] = fabs(v) + cs;
+        node_flux<R>(0, rho, U.y, U.z, U.w, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fx);
+        node_flux<R>(1, rho, U.y, U.z, U.w, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fy);
+        const R cs = sqrt(gam * Tc);
         // Lemma 3.2 bound b_l with tau_l = (tau_1l, tau_2l), q_l = -kappa dT/dx_l
-        R div = Sxu + Syv;
-        R txx = mu * (R(2) * Sxu - R(2) / R(3) * div), tyy = mu * (R(2) * Syv - R(2) / R(3) * div);
-        R txy = mu * (Syu + Sxv);
-        R re = p / gm1;
-        R qx = -ka * SxT, qy = -ka * SyT;
+        const R div = Sxu + Syv;
+        const R txx = mu * (R(2) * Sxu - R(2) / R(3) * div), tyy = mu * (R(2) * Syv - R(2) / R(3) * div);
+        const R txy = mu * (Syu + Sxv);
+        const R re = p / gm1;
+        const R qx = -ka * SxT, qy = -ka * SyT;
         const R ib = R(1) / (R(2) * rho * re);
-        q[CQ_BX * T::NCQ] = (sqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) * ib;
-        q[CQ_BY * T::NCQ] = (sqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) * ib;
+        const R bx = (sqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) * ib;
+        const R by = (sqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) * ib;
         // Sec. 3.2 sensors
-        R px = fabs(Ap[ca + 1] - R(2) * p + Ap[ca - 1]) / fabs(Ap[ca + 1] + R(2) * p + Ap[ca - 1]);
-        R py = fabs(Ap[ca + CX] - R(2) * p + Ap[ca - CX]) / fabs(Ap[ca + CX] + R(2) * p + Ap[ca - CX]);
-        q[CQ_P1 * T::NCQ] = dmax(px, py);
-        R curl = Sxv - Syu;
-        R ph2 = -div / sqrt(div * div + curl * curl + R(1e-13));
-        q[CQ_P2 * T::NCQ] = dmax(ph2, R(0));
+        const R px = fabs(We.z - R(2) * p + Ww.z) / fabs(We.z + R(2) * p + Ww.z);
+        const R py = fabs(Wn.z - R(2) * p + Ws.z) / fabs(Wn.z + R(2) * p + Ws.z);
+        const R curl = Sxv - Syu;
+        const R ph2 = -div / sqrt(div * div + curl * curl + R(1e-13));
+        Q4 *q = sCQ + 4 * t;
+        q[CQ_FX] = Q4{Fx[0], Fx[1], Fx[2], Fx[3]};
+        q[CQ_FY] = Q4{Fy[0], Fy[1], Fy[2], Fy[3]};
+        q[CQ_RB] = Q4{fabs(u) + cs, fabs(v) + cs, bx, by};
+        q[CQ_PH] = Q4{dmax(px, py), dmax(ph2, R(0)), R(0), R(0)};
     }
     __syncthreads();
 
-    // ---- P5b: face fluxes (high order, low order, limiters)
+    // ---- P5b: face fluxes: high order (Simpson), low order (Eq. (19)), theta_s
+    // (Eq. (22)), theta^rho theta^p (Sec. 3.3)
     {
-        const R *gxu = sGX, *gxv = sGX + NL, *gxT = sGX + 2 * NL;
-        const R *gyu = sGY, *gyv = sGY + NL, *gyT = sGY + 2 * NL;
         const long long nfx = (long long)(L.n1 + 1) * L.n2;
         for (int t = tid; t < T::NFX + T::NFY; t += nth) {
             int l, fl, el;   // direction, face index along l (local), index along the face (local)
@@ -535,7 +534,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                 if (fl > ntx || el >= nty) continue;
             } else {
                 l = 1;
-                int u_ = t - T::NFX;
+                const int u_ = t - T::NFX;
                 el = u_ % TX;
                 fl = u_ / TX;
                 if (el >= ntx || fl > nty) continue;
@@ -544,13 +543,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
             R FH[4] = {0, 0, 0, 0};
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
-                int la = l == 0 ? 2 + 2 * fl : 2 + 2 * el + s;
-                int lb = l == 0 ? 2 + 2 * el + s : 2 + 2 * fl;
-                int n = lb * LX + la;
+                const int la = l == 0 ? 2 + 2 * fl : 2 + 2 * el + s;
+                const int lb = l == 0 ? 2 + 2 * el + s : 2 + 2 * fl;
+                const int n = lb * LX + la;
+                const Q4 U = sU[n], Qn = sQ[n], gx = sGX[n], gy = sGY[n];
                 R Fn[4];
-                node_flux<R>(l, sU[n], sU[NL + n], sU[2 * NL + n], sU[3 * NL + n], sQ[n], sQ[NL + n], sQ[2 * NL + n],
-                             gxu[n], gxv[n], gxT[n], gyu[n], gyv[n], gyT[n], mu, ka, Fn);
-                R ws = s == 1 ? R(4) / R(6) : R(1) / R(6);
+                node_flux<R>(l, U.x, U.y, U.z, U.w, Qn.x, Qn.y, Qn.z, gx.x, gx.y, gx.z, gy.x, gy.y, gy.z, mu, ka, Fn);
+                const R ws = s == 1 ? R(4) / R(6) : R(1) / R(6);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) FH[c] += ws * Fn[c];
             }
@@ -573,21 +572,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                     aR = aL + CX;
                 }
                 const int fo = l == 0 ? CQ_FX : CQ_FY;
-                const int ro = l == 0 ? CQ_RX : CQ_RY, bo = l == 0 ? CQ_BX : CQ_BY;
-                R FLc[4], FRc[4], UbL[4], UbR[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    FLc[c] = sCQ[(fo + c) * T::NCQ + qL];
-                    FRc[c] = sCQ[(fo + c) * T::NCQ + qR];
-                    UbL[c] = sA[c * T::NCA + aL];
-                    UbR[c] = sA[c * T::NCA + aR];
-                }
-                const R lam = dmax(sCQ[ro * T::NCQ + qL], sCQ[ro * T::NCQ + qR]) +
-                              dmax(sCQ[bo * T::NCQ + qL], sCQ[bo * T::NCQ + qR]);
+                const Q4 fL4 = sCQ[4 * qL + fo], fR4 = sCQ[4 * qR + fo];
+                const Q4 rbL = sCQ[4 * qL + CQ_RB], rbR = sCQ[4 * qR + CQ_RB];
+                const Q4 uL4 = sA[aL], uR4 = sA[aR];
+                const R FLc[4] = {fL4.x, fL4.y, fL4.z, fL4.w}, FRc[4] = {fR4.x, fR4.y, fR4.z, fR4.w};
+                const R UbL[4] = {uL4.x, uL4.y, uL4.z, uL4.w}, UbR[4] = {uR4.x, uR4.y, uR4.z, uR4.w};
+                const R lam = l == 0 ? dmax(rbL.x, rbR.x) + dmax(rbL.z, rbR.z) : dmax(rbL.y, rbR.y) + dmax(rbL.w, rbR.w);
                 if (A.limiter == LIM_S_PP) {
-                    R p1 = dmax(sCQ[CQ_P1 * T::NCQ + qL], sCQ[CQ_P1 * T::NCQ + qR]);
-                    R p2 = dmax(sCQ[CQ_P2 * T::NCQ + qL], sCQ[CQ_P2 * T::NCQ + qR]);
-                    tsr = exp(-tc.cs * p1 * p2);
+                    const Q4 phL = sCQ[4 * qL + CQ_PH], phR = sCQ[4 * qR + CQ_PH];
+                    tsr = exp(-tc.cs * dmax(phL.x, phR.x) * dmax(phL.y, phR.y));
                 }
                 bool done = false;
                 if constexpr (sizeof(R) == 4) {
@@ -628,18 +621,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
                     tppr = (R)tppd;
                 }
             }
-            R *Fs = l == 0 ? sFX : sFY;
-            int fidx = l == 0 ? el * (TX + 1) + fl : fl * TX + el;
-            const int nf = l == 0 ? T::NFX : T::NFY;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) Fs[c * nf + fidx] = Fout[c];
+            const Q4 fo4 = {Fout[0], Fout[1], Fout[2], Fout[3]};
+            if (l == 0) sFX[el * (TX + 1) + fl] = fo4;
+            else sFY[fl * TX + el] = fo4;
             if (A.theta) {
-                int gf = l == 0 ? i0 + fl : j0 + fl;   // global face index along l
-                int ge = l == 0 ? j0 + el : i0 + el;
-                bool own = l == 0 ? (fl < ntx || gf == L.n1) : (fl < nty || gf == L.n2);
+                const int gf = l == 0 ? i0 + fl : j0 + fl;   // global face index along l
+                const int ge = l == 0 ? j0 + el : i0 + el;
+                const bool own = l == 0 ? (fl < ntx || gf == L.n1) : (fl < nty || gf == L.n2);
                 if (own) {
-                    long long id = l == 0 ? (long long)ge * (L.n1 + 1) + gf : nfx + (long long)gf * L.n1 + ge;
-                    long long nft = nfx + (long long)L.n1 * (L.n2 + 1);
+                    const long long id = l == 0 ? (long long)ge * (L.n1 + 1) + gf : nfx + (long long)gf * L.n1 + ge;
+                    const long long nft = nfx + (long long)L.n1 * (L.n2 + 1);
                     A.theta[id] = (double)tsr;
                     A.theta[nft + id] = (double)tppr;
                 }
@@ -648,25 +639,33 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
     }
     __syncthreads();
 
-    // ---- P6: cell residual (flux differences), RK combination, store
+    // ---- P6: cell residual (flux differences, Eq. (23)), RK combination, store
     if constexpr (sizeof(S) == 8) {
         const double w = A.k.residual ? 1.0 : A.k.cl * dt;
         const double idx = 1.0 / L.dx, idy = 1.0 / L.dy;
         for (int t = tid; t < ntx * nty; t += nth) {
-            int il = t % ntx, jl = t / ntx;
-            int ca = (jl + 2) * CX + (il + 2);
-            long long off = cell_off(L, i0 + il, j0 + jl);
+            const int il = t % ntx, jl = t / ntx;
+            const Q4 fxr = sFX[jl * (TX + 1) + il + 1], fxl = sFX[jl * (TX + 1) + il];
+            const Q4 fyt = sFY[(jl + 1) * TX + il], fyb = sFY[jl * TX + il];
+            const Q4 ui = sA[(jl + 2) * CX + (il + 2)];
+            const long long po0 = plane_of(L, 0, 0) + cell_off(L, i0 + il, j0 + jl);
+            double g0[4] = {0, 0, 0, 0}, g2[4] = {0, 0, 0, 0};   // global inputs first
+#pragma unroll
             for (int c = 0; c < 4; ++c) {
-                double fxr = sFX[c * T::NFX + jl * (TX + 1) + il + 1], fxl = sFX[c * T::NFX + jl * (TX + 1) + il];
-                double fyt = sFY[c * T::NFY + (jl + 1) * TX + il], fyb = sFY[c * T::NFY + jl * TX + il];
-                double res = -(fxr - fxl) * idx - (fyt - fyb) * idy;
-                long long po = plane_of(L, 0, c) + off;
-                double Uin = sA[c * T::NCA + ca];
+                if (tc.ua0) g0[c] = ld<S>(A.u0, po0 + c * L.plane);
+                if (tc.ua2 || A.k.acc) g2[c] = ld<S>(A.aux, po0 + c * L.plane);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const double res =
+                    -((double)comp(fxr, c) - (double)comp(fxl, c)) * idx - ((double)comp(fyt, c) - (double)comp(fyb, c)) * idy;
+                const long long po = po0 + c * L.plane;
+                const double Uin = comp(ui, c);
                 double v = A.k.residual ? 0.0 : A.k.a1 * Uin;
-                if (A.k.a0 != 0.0) v += A.k.a0 * ld<S>(A.u0, po);
-                if (A.k.a2 != 0.0) v += A.k.a2 * ld<S>(A.aux, po);
+                if (tc.ua0) v += A.k.a0 * g0[c];
+                if (tc.ua2) v += A.k.a2 * g2[c];
                 if (A.k.acc) {
-                    double ac = A.k.b2 * ld<S>(A.aux, po) + A.k.b1 * Uin + A.k.bl * dt * res;
+                    const double ac = A.k.b2 * g2[c] + A.k.b1 * Uin + A.k.bl * dt * res;
                     ((S *)A.aux)[po] = (S)ac;
                 }
                 ((S *)A.out)[po] = (S)(v + w * res);
@@ -680,29 +679,42 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
         const ff a0 = tc.fa0, a1 = tc.fa1, a2 = tc.fa2, wx = tc.fwx, wy = tc.fwy;
         const ff b1 = tc.fb1, b2 = tc.fb2, bx = tc.fbx, by = tc.fby;
         float *out = (float *)A.out;
-        const float *uin = (const float *)A.uin, *u0 = (const float *)A.u0;
+        const float *u0 = (const float *)A.u0;
         float *aux = (float *)A.aux;
         for (int t = tid; t < ntx * nty; t += nth) {
-            int il = t % ntx, jl = t / ntx;
-            int ca = (jl + 2) * CX + (il + 2);
-            long long off = cell_off(L, i0 + il, j0 + jl);
+            const int il = t % ntx, jl = t / ntx;
+            const long long off = cell_off(L, i0 + il, j0 + jl);
+            // every global input of the cell first (one latency for all of them)
+            float ulo[4], g0h[4], g0l[4], g2h[4], g2l[4];
+#pragma unroll
             for (int c = 0; c < 4; ++c) {
-                float fxr = sFX[c * T::NFX + jl * (TX + 1) + il + 1], fxl = sFX[c * T::NFX + jl * (TX + 1) + il];
-                float fyt = sFY[c * T::NFY + (jl + 1) * TX + il], fyb = sFY[c * T::NFY + jl * TX + il];
-                long long po = plane_of(L, 0, c) + off, pl = comp_plane(L, c) + off;
+                const long long po = plane_of(L, 0, c) + off, pl = comp_plane(L, c) + off;
+                ulo[c] = A.k.residual ? 0.f : ((const float *)A.uin)[pl];
+                g0h[c] = tc.ua0 ? u0[po] : 0.f;
+                g0l[c] = tc.ua0 ? u0[pl] : 0.f;
+                g2h[c] = (tc.ua2 || A.k.acc) ? aux[po] : 0.f;
+                g2l[c] = (tc.ua2 || A.k.acc) ? aux[pl] : 0.f;
+            }
+            const Q4 fxr = sFX[jl * (TX + 1) + il + 1], fxl = sFX[jl * (TX + 1) + il];
+            const Q4 fyt = sFY[(jl + 1) * TX + il], fyb = sFY[jl * TX + il];
+            const Q4 ui = sA[(jl + 2) * CX + (il + 2)];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float fr = comp(fxr, c), fl = comp(fxl, c), ft = comp(fyt, c), fb = comp(fyb, c);
+                const long long po = plane_of(L, 0, c) + off, pl = comp_plane(L, c) + off;
                 if (A.k.residual) {
-                    out[po] = -(fxr - fxl) * fidx - (fyt - fyb) * fidy;
+                    out[po] = -(fr - fl) * fidx - (ft - fb) * fidy;
                     out[pl] = 0.f;
                     continue;
                 }
-                const ff dxf = ff_two_sum(fxl, -fxr), dyf = ff_two_sum(fyb, -fyt);   // exact
+                const ff dxf = ff_two_sum(fl, -fr), dyf = ff_two_sum(fb, -ft);   // exact
                 const ff inc = ff_add(ff_mul(wx, dxf), ff_mul(wy, dyf));
-                const ff ui = {(float)sA[c * T::NCA + ca], uin[pl]};
-                ff v = ff_mul(a1, ui);
-                if (tc.ua0) v = ff_add(v, ff_mul(a0, ff{u0[po], u0[pl]}));
-                if (tc.ua2) v = ff_add(v, ff_mul(a2, ff{aux[po], aux[pl]}));
+                const ff uv = {(float)comp(ui, c), ulo[c]};
+                ff v = ff_mul(a1, uv);
+                if (tc.ua0) v = ff_add(v, ff_mul(a0, ff{g0h[c], g0l[c]}));
+                if (tc.ua2) v = ff_add(v, ff_mul(a2, ff{g2h[c], g2l[c]}));
                 if (A.k.acc) {
-                    ff ac = ff_add(ff_mul(b2, ff{aux[po], aux[pl]}), ff_mul(b1, ui));
+                    ff ac = ff_add(ff_mul(b2, ff{g2h[c], g2l[c]}), ff_mul(b1, uv));
                     ac = ff_add(ac, ff_add(ff_mul(bx, dxf), ff_mul(by, dyf)));
                     aux[po] = ac.h;
                     aux[pl] = ac.l;
@@ -716,11 +728,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, R
     if (tid == 0 && s_bad) atomicOr(&A.ctl->notpp, 1);
 }
 
-template <class R, class S, int TX, int TY>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_stage2d(StageArgs A)
+// Resident CTAs per SM that the register budget must allow: as many as the
+// tile's shared memory admits (FP32 16x8: three of 128 threads, two of 256;
+// FP32 32x8 and FP64 16x8: one).
+template <class R, int TX, int NTH>
+constexpr int stage_min_ctas()
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<R, S, TX, TY>(A, blockIdx.x, blockIdx.y, reinterpret_cast<R *>(smem_raw));
+    return (sizeof(R) == 8 || TX == 32) ? 1 : (NTH == 128 ? 3 : 2);
+}
+
+template <class R, class S, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, NTH>()) k_stage2d(StageArgs A)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    stage_tile<R, S, TX, TY, NTH>(A, blockIdx.x, blockIdx.y, reinterpret_cast<V4<R> *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
