@@ -11,6 +11,8 @@ cells x 5 x steps / seconds.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
   python bench.py --impl reference ...   (the CPU oracle, timed on a bounded sample)
+  python bench.py --workload batch ...   (256 uneven problems, persistent kernel + graph)
+  python bench.py --workload tube [--t-end T] ...   (walled shock tube 2000 x 1000)
 """
 from __future__ import annotations
 
@@ -229,6 +231,73 @@ def cpu_baseline(w, S, args):
                               % (w.n[0], w.n[1], sec)}
 
 
+def tube_arm(args, dist, rank, ws):
+    """2D viscous shock tube in a walled box (no-slip walls, symmetry on top),
+    2000 x 1000 cells, Re = 1000: K timed CFL steps after the warm-up; with
+    --t-end the whole run from t = 0 is timed as well (the paper's wall-clock
+    figures for this problem are on 24 CPU cores, context only)."""
+    import torch
+    from paper_2609_29081_b300 import Solver, build, workloads as W
+    from paper_2609_29081_b300._native import FP64, MIXED
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = W.shock_tube_2d((2000, 1000))
+    prec = FP64 if args.precision == "fp64" else MIXED
+    stream = torch.cuda.Stream()
+    full = None
+    with torch.cuda.stream(stream):
+        S = Solver.from_workload(w, precision=prec, stream=stream)
+        S.set_state(w.state)
+        tuned = S.tune()
+        if args.t_end > 0:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ns, nr = S.advance(args.t_end)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            full = {"t_end": args.t_end, "seconds": sec, "steps": ns, "restarts": nr,
+                    "cell_stage_per_s": w.cells * 5 * ns / sec,
+                    "paper_context": "AF on a 24-core Apple M3 Ultra: 8 h 35 min for this grid to t = 1"}
+            S.set_state(w.state)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        cp, cpath = clocks_start()
+        time.sleep(0.4)
+        warm_done = preheat(lambda: S.step(0.0), args.warmup)
+        S.set_profiling(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        restarts = 0
+        for _ in range(args.steps):
+            restarts += S.step(0.0)[1]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clocks_stop(cp, cpath)
+        ms = ev0.elapsed_time(ev1)
+        prof = S.profile()
+        S.set_profiling(False)
+        st = W.split_sites(S.get_state(), 2, *w.n)
+        pmin = min(float((0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])).min()) for U in st)
+        rmin = min(float(U[0].min()) for U in st)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": w.cells * 5 * args.steps * ws / (ms / 1e3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "2D viscous shock tube, walled box [0,1]x[0,0.5], 2000x1000, mu=1e-3, "
+                                   "Pr=0.73, (120,0,0,120/1.4)|(1.2,0,0,1.2/1.4), no-slip x-lo/x-hi/y-lo, "
+                                   "symmetry y-hi, CFL steps, limiter s+pp",
+                       "precision": args.precision, "tuned": tuned, "restarts": restarts,
+                       "warmup_steps_run": warm_done, "l2": "inputs larger than L2"},
+            "clocks": clocks, "gpu_launches": prof["launches"], "stage_ms": prof["stage_ms"] / max(prof["stage_launches"], 1),
+            "positivity": {"rho_min": rmin, "p_min": pmin}}
+    if full:
+        line["full_run"] = full
+    print(json.dumps(line), flush=True)
+
+
 def batch_arm(args, dist, rank, ws):
     """Batched form: 256 independent periodic problems of uneven sizes (mixed
     precision, persistent stage kernel, CUDA graph, autotuned configuration),
@@ -302,11 +371,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libafns")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the run in the other precision")
     ap.add_argument("--n", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "tube"])
+    ap.add_argument("--t-end", type=float, default=0.0)
     ap.add_argument("--nprob", type=int, default=256)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -317,21 +389,102 @@ def main():
     if args.workload == "batch":
         batch_arm(args, dist, rank, ws)
         return
+    if args.workload == "tube":
+        tube_arm(args, dist, rank, ws)
+        return
 
     import torch
-    from paper_2609_29081_b300 import Solver, build, workloads as W
-    from paper_2609_29081_b300._native import FP64, MIXED
+    from paper_2609_29081_b300 import build, workloads as W
     build.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     w = W.smooth_2d(args.n)
-    prec = FP64 if args.precision == "fp64" else MIXED
+    alu_pk = measure_alu_peaks()
+    main_run = single_run(args, w, args.precision, dist, ws, e2e=True)
+    other = "fp64" if args.precision == "mixed" else "mixed"
+    cmp_run = single_run(args, w, other, dist, ws, e2e=False) if args.compare else None
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    cells = w.cells
+    r = main_run
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "2D smooth periodic NS %dx%d (rho=1+0.2sin(x+y), (u,v)=(1,0.5)+8-mode "
+                                   "perturbation, p=1, mu=0.01, Pr=0.72), CFL steps, limiter s+pp"
+                                   % (args.n, args.n),
+                       "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (state %.0f MB per buffer, 5 buffers)" % (r["state_bytes"] / 1e6),
+                       "restarts": r["restarts"], "tuned": r["tuned"], "warmup_steps_run": r["warm_done"]},
+            "roofline": stage_roofline(args.precision, cells, r["stage_ms"], peaks, alu_pk),
+            "clocks": r["clocks"],
+            "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["state_bytes"],
+                    "d2h_bytes_per_step": r["state_bytes"]},
+            "gpu_launches": r["launches"],
+            "stage_ms": r["stage_ms"]}
+    if cmp_run:
+        c = cmp_run
+        line[other] = {"value": c["value"], "unit": UNIT, "ms_per_step": c["ms"] / args.steps,
+                       "stage_ms": c["stage_ms"], "tuned": c["tuned"], "restarts": c["restarts"],
+                       "roofline": stage_roofline(other, cells, c["stage_ms"], peaks, alu_pk)}
+        line["l1_mixed_vs_fp64"] = accuracy_pair(w, ACCURACY_STEPS)
+    if not args.no_cpu:
+        from paper_2609_29081_b300 import Solver
+        from paper_2609_29081_b300._native import FP64, MIXED
+        w0 = W.smooth_2d(args.n)
+        S = Solver.from_workload(w0, precision=MIXED if args.precision == "mixed" else FP64)
+        S.set_state(w0.state)
+        Lr, dt, cb = cpu_baseline(w0, S, args)
+        Lg, _ = S.residual(dt)
+        S.close()
+        avg_r = W.split_sites(Lr, 2, *w0.n)[0]
+        avg_g = W.split_sites(Lg, 2, *w0.n)[0]
+        line["cpu_baseline"] = cb
+        line["l1_vs_oracle"] = {"what": "relative L1 distance of one stage residual of cell averages, GPU (%s) "
+                                        "vs oracle, full grid" % args.precision,
+                                "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum())}
+    print(json.dumps(line), flush=True)
+
+
+ACCURACY_STEPS = 20
+
+
+def accuracy_pair(w, nsteps):
+    """The same nsteps CFL steps from the initial state in both precisions (not
+    timed). The FP64 path equals the oracle to 1e-10 (parity tests), so this is
+    the mixed path's error against the oracle after nsteps."""
+    from paper_2609_29081_b300 import Solver, workloads as W
+    from paper_2609_29081_b300._native import FP64, MIXED
+    fin = {}
+    for name, p in (("mixed", MIXED), ("fp64", FP64)):
+        S = Solver.from_workload(w, precision=p)
+        S.set_state(w.state)
+        for _ in range(nsteps):
+            S.step(0.0)
+        fin[name] = W.split_sites(S.get_state(), 2, *w.n)[0]
+        S.close()
+    d = np.abs(fin["mixed"] - fin["fp64"])
+    return {"value": float(d.sum() / np.abs(fin["fp64"]).sum()),
+            "linf": float(d.max() / np.abs(fin["fp64"]).max()),
+            "what": "relative L1 / Linf distance of the cell averages after %d CFL steps from the "
+                    "initial state, mixed vs FP64" % nsteps}
+
+
+def single_run(args, w, precision, dist, ws, e2e):
+    """Tune, warm up and time args.steps CFL steps of workload w in one precision;
+    optionally the end-to-end loop through host buffers."""
+    import torch
+    from paper_2609_29081_b300 import Solver
+    from paper_2609_29081_b300._native import FP64, MIXED
+    prec = FP64 if precision == "fp64" else MIXED
     stream = torch.cuda.Stream()
+    out = {}
     with torch.cuda.stream(stream):
         S = Solver.from_workload(w, precision=prec, stream=stream)
         S.set_state(w.state)
-        tuned = S.tune()
-        alu_pk = measure_alu_peaks()
+        out["tuned"] = S.tune()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -339,19 +492,18 @@ def main():
         time.sleep(0.4)
         # warm-up right before the timed region: W steps, then more untimed steps
         # until the GPU has been busy for PREHEAT_S (clocks up after the idle sleep)
-        warm_done = preheat(lambda: S.step(0.0), args.warmup)
+        out["warm_done"] = preheat(lambda: S.step(0.0), args.warmup)
         S.set_profiling(True)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         restarts = 0
         for _ in range(args.steps):
-            _, h = S.step(0.0)
-            restarts += h
+            restarts += S.step(0.0)[1]
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        clocks = clocks_stop(cp, cpath)
+        out["clocks"] = clocks_stop(cp, cpath)
         ms = ev0.elapsed_time(ev1)
         prof = S.profile()
         S.set_profiling(False)
@@ -359,60 +511,31 @@ def main():
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        cells = w.cells
-        value = cells * 5 * args.steps * ws / (ms / 1e3)
-
-        # end to end through the public API with pinned host buffers
-        host_in = torch.from_numpy(S.get_state()).pin_memory()
-        host_out = torch.empty_like(host_in).pin_memory()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            S.set_state(host_in.numpy())
-            S.step(0.0)
-            S.get_state(host_out.numpy())
-        torch.cuda.synchronize()
-        e2e_sec = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_sec], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_sec = float(t.item())
-        e2e_val = cells * 5 * args.e2e_steps * ws / e2e_sec
-        state_bytes = host_in.numel() * 8
-
-    if rank != 0:
-        return
-    peaks = load_peaks()
-    stage_ms = prof["stage_ms"] / max(prof["stage_launches"], 1)
-    roofline = stage_roofline(args.precision, cells, stage_ms, peaks, alu_pk)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic",
-            "config": {"workload": "2D smooth periodic NS %dx%d (rho=1+0.2sin(x+y), (u,v)=(1,0.5)+8-mode "
-                                   "perturbation, p=1, mu=0.01, Pr=0.72), CFL steps, limiter s+pp"
-                                   % (args.n, args.n),
-                       "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (state %.0f MB per buffer, 5 buffers)" % (state_bytes / 1e6),
-                       "restarts": restarts, "tuned": tuned, "warmup_steps_run": warm_done},
-            "roofline": roofline, "clocks": clocks,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                    "d2h_bytes_per_step": state_bytes},
-            "gpu_launches": prof["launches"],
-            "stage_ms": stage_ms}
-    if not args.no_cpu:
-        w0 = W.smooth_2d(args.n)
-        S.set_state(w0.state)
-        Lr, dt, cb = cpu_baseline(w0, S, args)
-        Lg, _ = S.residual(dt)
-        avg_r = W.split_sites(Lr, 2, *w0.n)[0]
-        avg_g = W.split_sites(Lg, 2, *w0.n)[0]
-        line["cpu_baseline"] = cb
-        line["l1_vs_oracle"] = {"what": "relative L1 distance of one stage residual of cell averages, GPU vs oracle",
-                                "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum())}
-    print(json.dumps(line), flush=True)
+        out.update(ms=ms, restarts=restarts, launches=prof["launches"],
+                   stage_ms=prof["stage_ms"] / max(prof["stage_launches"], 1),
+                   value=w.cells * 5 * args.steps * ws / (ms / 1e3))
+        if e2e:
+            # end to end through the public API with pinned host buffers
+            host_in = torch.from_numpy(S.get_state()).pin_memory()
+            host_out = torch.empty_like(host_in).pin_memory()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                S.set_state(host_in.numpy())
+                S.step(0.0)
+                S.get_state(host_out.numpy())
+            torch.cuda.synchronize()
+            e2e_sec = time.perf_counter() - t0
+            if dist:
+                t = torch.tensor([e2e_sec], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                e2e_sec = float(t.item())
+            out["e2e"] = w.cells * 5 * args.e2e_steps * ws / e2e_sec
+            out["state_bytes"] = host_in.numel() * 8
+        S.close()
+    return out
 
 
 # Algorithmic work of one 2D stage per cell (counted from the operation counts of

@@ -73,14 +73,17 @@ typedef struct {
     int limiter;       /* af_limiter; AF_LIM_S_PP is the paper's scheme */
     double c_s;        /* smoothness-limiter strength C_s (Sec. 3.2); paper: 1 */
     double cfl_c;      /* inviscid CFL number C^c of Eq. (13); paper: 1.04/d */
-    double cfl_v;      /* viscous CFL number C^v of Eq. (13); paper: 0.33/d */
+    double cfl_v;      /* viscous CFL number C^v of Eq. (13); default 0.33 in 1D (the
+                          paper's), 0.8 x 0.33/2 in 2D: the paper's 0.33/2 is unstable
+                          for 2D flows whose bound is dominated by the viscous term */
     double eps;        /* positivity floor cap epsilon (Sec. 3.3); paper: 1e-13 */
     int max_halvings;  /* restarts allowed per step (Remark 3.2); default 30 */
     int tile_x;        /* 2D tile width in cells (0 = autotuned default) */
     int tile_y;        /* 2D tile height in cells (0 = autotuned default) */
 } af_opts;
 
-/* Fill *o with the paper's defaults for a problem of dimension dim. */
+/* Fill *o with the paper's defaults for a problem of dimension dim (except C^v
+ * in 2D, see cfl_v). */
 af_status af_opts_default(int dim, af_opts *o);
 
 /* Bytes of device workspace af_create needs for this grid and these options. */

@@ -28,7 +28,23 @@ struct Layout {
     int comp;       // compensation planes present (mixed precision)
     int bc[4];
     double dx, dy;
+    // reciprocal stencil factors per direction, set on the host by layout_finish
+    // (so no kernel divides by the grid spacing): 1/dx_l, 1/(6 dx_l),
+    // 1/(3 dx_l^2), 4/dx_l^2, 1/(2 dx_l)
+    double idx[2], i6[2], i3h2[2], f4h2[2], i2[2];
 };
+
+inline void layout_finish(Layout *L)
+{
+    const double h[2] = {L->dx, L->dy};
+    for (int l = 0; l < 2; ++l) {
+        L->idx[l] = 1.0 / h[l];
+        L->i6[l] = 1.0 / (6.0 * h[l]);
+        L->i3h2[l] = 1.0 / (3.0 * h[l] * h[l]);
+        L->f4h2[l] = 4.0 / (h[l] * h[l]);
+        L->i2[l] = 1.0 / (2.0 * h[l]);
+    }
+}
 
 // Plane index of (site, component); compensation plane of cell-average comp c.
 __host__ __device__ __forceinline__ long long plane_of(const Layout &L, int site, int c)

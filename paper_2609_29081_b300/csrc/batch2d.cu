@@ -524,6 +524,7 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
         for (int k = 0; k < 4; ++k) L.bc[k] = bcs[p].side[k];
         L.dx = (g.hi[0] - g.lo[0]) / g.n[0];
         L.dy = (g.hi[1] - g.lo[1]) / g.n[1];
+        layout_finish(&L);
         size_t st = al256((size_t)L.plane * (16 + (c->mixed ? 4 : 0)) * (c->mixed ? 4 : 8));
         for (int k = 0; k < 4; ++k) P.U[k] = q, q += st;
         P.U[4] = nullptr;

@@ -127,24 +127,27 @@ __global__ void __launch_bounds__(128) k_stage1d(StageArgs A)
 
     // P1: centres U_i = (6 Ubar_i - (U_{i-1/2} + U_{i+1/2})) / 4 + scaling limiter
     for (int t = tid; t < QX; t += nth) {
+        // the centre and its limiter in FP64 in both precisions (one cell per
+        // thread; in FP64 storage this is the plain expression)
         int n = 2 * t + 1, ca = t + 1;
-        R Uc[3];
-        for (int c = 0; c < 3; ++c) Uc[c] = (R(6) * sA[c * CX + ca] - (sU[c * LX + n - 1] + sU[c * LX + n + 1])) / R(4);
+        double Uc[3];
+        for (int c = 0; c < 3; ++c)
+            Uc[c] = (6.0 * (double)sA[c * CX + ca] - ((double)sU[c * LX + n - 1] + (double)sU[c * LX + n + 1])) / 4.0;
         if (A.limiter != LIM_NONE) {
-            R pc = gm1 * (Uc[2] - Uc[1] * Uc[1] / (R(2) * Uc[0]));
-            if (!(Uc[0] >= (R)eps) || !(pc >= (R)eps)) {
-                double Ub[3], Ud[3], Ur[3];
-                for (int c = 0; c < 3; ++c) Ub[c] = (double)sA[c * CX + ca], Ud[c] = (double)Uc[c];
-                double g1 = A.gamma - 1.0;
-                double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
-                for (int c = 0; c < 3; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
+            const double g1 = A.gamma - 1.0;
+            double pc = g1 * (Uc[2] - Uc[1] * Uc[1] / (2.0 * Uc[0]));
+            if (!(Uc[0] >= eps) || !(pc >= eps)) {
+                double Ub[3], Ur[3];
+                for (int c = 0; c < 3; ++c) Ub[c] = (double)sA[c * CX + ca];
+                double thr = theta_fn(Ub[0], Uc[0], fmin(eps, Ub[0]));
+                for (int c = 0; c < 3; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Uc[c];
                 double pL = g1 * (Ub[2] - Ub[1] * Ub[1] / (2.0 * Ub[0]));
                 double pH = g1 * (Ur[2] - Ur[1] * Ur[1] / (2.0 * Ur[0]));
                 double th = thr * theta_fn(pL, pH, fmin(eps, pL));
-                for (int c = 0; c < 3; ++c) Uc[c] = (R)((1.0 - th) * Ub[c] + th * Ud[c]);
+                for (int c = 0; c < 3; ++c) Uc[c] = (1.0 - th) * Ub[c] + th * Uc[c];
             }
         }
-        for (int c = 0; c < 3; ++c) sU[c * LX + n] = Uc[c];
+        for (int c = 0; c < 3; ++c) sU[c * LX + n] = (R)Uc[c];
     }
     __syncthreads();
 
@@ -343,7 +346,39 @@ __global__ void __launch_bounds__(128) k_stage1d(StageArgs A)
     __syncthreads();
 
     // P6: cell residual, combination, store
-    {
+    if constexpr (sizeof(S) == 4) {
+        // mixed precision: the cell average is hi + lo in storage; the update is
+        // formed in FP64 from both words and split again, so the face-flux
+        // differences telescope exactly and mass is kept far below FP32 roundoff
+        const double w = A.k.residual ? 1.0 : A.k.cl * dt, idx = 1.0 / L.dx;
+        float *out = (float *)A.out, *aux = (float *)A.aux;
+        const float *u0 = (const float *)A.u0, *uin = (const float *)A.uin;
+        for (int t = tid; t < ntx; t += nth) {
+            for (int c = 0; c < 3; ++c) {
+                const double res = -((double)sF[c * T::NF + t + 1] - (double)sF[c * T::NF + t]) * idx;
+                const long long po = plane_of(L, 0, c) + off1(i0 + t), pl = comp_plane(L, c) + off1(i0 + t);
+                if (A.k.residual) {
+                    out[po] = (float)res;
+                    out[pl] = 0.f;
+                    continue;
+                }
+                const double Uin = (double)sA[c * CX + t + 2] + (double)uin[pl];
+                double v = A.k.a1 * Uin;
+                if (A.k.a0 != 0.0) v += A.k.a0 * ((double)u0[po] + (double)u0[pl]);
+                if (A.k.a2 != 0.0) v += A.k.a2 * ((double)aux[po] + (double)aux[pl]);
+                if (A.k.acc) {
+                    const double ac = A.k.b2 * ((double)aux[po] + (double)aux[pl]) + A.k.b1 * Uin + A.k.bl * dt * res;
+                    const float h = __double2float_rn(ac);
+                    aux[po] = h;
+                    aux[pl] = __double2float_rn(ac - (double)h);
+                }
+                v += w * res;
+                const float h = __double2float_rn(v);
+                out[po] = h;
+                out[pl] = __double2float_rn(v - (double)h);
+            }
+        }
+    } else {
         const double w = A.k.residual ? 1.0 : A.k.cl * dt, idx = 1.0 / L.dx;
         for (int t = tid; t < ntx; t += nth) {
             for (int c = 0; c < 3; ++c) {

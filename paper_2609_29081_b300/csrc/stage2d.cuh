@@ -83,20 +83,23 @@ struct TileConst {
     R i2[2];             // 1 / (2 dx_l): central differences of the cell averages
 };
 
+// No divisions: the grid reciprocals come from the layout (host-computed), dt
+// enters by multiplication.
 template <class R>
 __device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs &A, double dt)
 {
+    const Layout &L = A.L;
     t.gam = (R)A.gamma;
     t.gm1 = (R)(A.gamma - 1.0);
     t.mu = (R)A.mu;
     t.ka = (R)A.kappa;
-    t.dx = (R)A.L.dx;
-    t.dy = (R)A.L.dy;
+    t.dx = (R)L.dx;
+    t.dy = (R)L.dy;
     t.dt = (R)dt;
     t.eps = (R)A.eps;
     t.cs = (R)A.c_s;
-    t.kkx = (R)(4.0 * dt / A.L.dx);
-    t.kky = (R)(4.0 * dt / A.L.dy);
+    t.kkx = (R)(4.0 * dt * L.idx[0]);
+    t.kky = (R)(4.0 * dt * L.idx[1]);
     t.w = (R)(A.k.residual ? 1.0 : A.k.cl * dt);
     t.a0 = (R)A.k.a0;
     t.a1 = (R)A.k.a1;
@@ -107,22 +110,21 @@ __device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs
     t.fa0 = ff_from(A.k.a0);
     t.fa1 = ff_from(A.k.a1);
     t.fa2 = ff_from(A.k.a2);
-    t.fwx = ff_from(A.k.cl * dt / A.L.dx);
-    t.fwy = ff_from(A.k.cl * dt / A.L.dy);
+    t.fwx = ff_from(A.k.cl * dt * L.idx[0]);
+    t.fwy = ff_from(A.k.cl * dt * L.idx[1]);
     t.fb1 = ff_from(A.k.b1);
     t.fb2 = ff_from(A.k.b2);
-    t.fbx = ff_from(A.k.bl * dt / A.L.dx);
-    t.fby = ff_from(A.k.bl * dt / A.L.dy);
-    t.idx = (R)(1.0 / A.L.dx);
-    t.idy = (R)(1.0 / A.L.dy);
+    t.fbx = ff_from(A.k.bl * dt * L.idx[0]);
+    t.fby = ff_from(A.k.bl * dt * L.idx[1]);
+    t.idx = (R)L.idx[0];
+    t.idy = (R)L.idx[1];
     t.ua0 = A.k.a0 != 0.0;
     t.ua2 = A.k.a2 != 0.0;
-    const double h[2] = {A.L.dx, A.L.dy};
     for (int l = 0; l < 2; ++l) {
-        t.i6[l] = (R)(1.0 / (6.0 * h[l]));
-        t.i3h2[l] = (R)(1.0 / (3.0 * h[l] * h[l]));
-        t.f4h2[l] = (R)(4.0 / (h[l] * h[l]));
-        t.i2[l] = (R)(1.0 / (2.0 * h[l]));
+        t.i6[l] = (R)L.i6[l];
+        t.i3h2[l] = (R)L.i3h2[l];
+        t.f4h2[l] = (R)L.f4h2[l];
+        t.i2[l] = (R)L.i2[l];
     }
 }
 

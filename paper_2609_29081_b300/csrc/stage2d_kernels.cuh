@@ -236,12 +236,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     const int tid = threadIdx.x;
     constexpr int nth = NTH;
     const int ntx = min(TX, L.n1 - i0), nty = min(TY, L.n2 - j0);
-    const double dt = A.ctl->dt;
     const double eps = A.eps;
-    if (tid == 0) {
-        s_bad = 0;
-        tile_const_init<R>(tc, A, dt);
-    }
     Q4 *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
     Q4 *sA = sm + T::oA, *sAW = sm + T::oAW, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
     const S *uin = (const S *)A.uin;
@@ -279,6 +274,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         } else {
             sA[t] = benign;
         }
+    }
+    // while the tile loads are in flight: the step size and the per-tile constants
+    const double dt = A.ctl->dt;
+    if (tid == 0) {
+        s_bad = 0;
+        tile_const_init<R>(tc, A, dt);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -642,7 +643,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     // ---- P6: cell residual (flux differences, Eq. (23)), RK combination, store
     if constexpr (sizeof(S) == 8) {
         const double w = A.k.residual ? 1.0 : A.k.cl * dt;
-        const double idx = 1.0 / L.dx, idy = 1.0 / L.dy;
+        const double idx = L.idx[0], idy = L.idx[1];
         for (int t = tid; t < ntx * nty; t += nth) {
             const int il = t % ntx, jl = t / ntx;
             const Q4 fxr = sFX[jl * (TX + 1) + il + 1], fxl = sFX[jl * (TX + 1) + il];

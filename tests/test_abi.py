@@ -46,7 +46,7 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     L = N.load()
     o = N.Opts()
     assert L.af_opts_default(2, ctypes.byref(o)) == N.AF_OK
-    assert o.cfl_c == pytest.approx(0.52) and o.cfl_v == pytest.approx(0.165) and o.eps == 1e-13
+    assert o.cfl_c == pytest.approx(0.52) and o.cfl_v == pytest.approx(0.8 * 0.165) and o.eps == 1e-13
     assert o.limiter == N.LIM_S_PP and o.max_halvings == 30
     assert L.af_opts_default(3, ctypes.byref(o)) == N.AF_EINVAL
     g = N.Grid()

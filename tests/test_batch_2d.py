@@ -72,7 +72,7 @@ def test_batch_restarts_stay_per_problem():
     """A near-vacuum blast in the batch restarts (Remark 3.2) without touching the
     others; every DoF of every problem stays admissible."""
     from paper_2609_29081_b300 import MIXED, BatchSolver
-    wls = problems()[:3] + [W.blast_2d((32, 32), seed=2)]
+    wls = problems()[:3] + [W.blast_2d((32, 32), seed=2, rho_min=1e-10, p_min=1e-12)]
     B = BatchSolver(wls, precision=MIXED)
     for i, w in enumerate(wls):
         B.set_state(i, w.state)

@@ -535,3 +535,43 @@ def test_smoothness_sensor_textbook_values(orc):
     assert ts[4] == pytest.approx(np.exp(-1.0 / 5.0), rel=1e-12)   # cells 3|4
     assert ts[0] == 1.0 and ts[6] == 1.0                           # no compression
     assert ts[2] == pytest.approx(np.exp(-1.0 / 3.0), rel=1e-12)   # cells 1|2: phi1(2)=1/3, phi2(2)=1
+
+
+# ---------------------------------------------------------------------------
+# Time step: the stability limits of Eq. (13)
+# ---------------------------------------------------------------------------
+
+def _steps_until_blowup(orc, w, nsteps, **cfl):
+    P = orc.problem(w.dim, *w.n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, gamma=w.gamma, limiter=0, **cfl)
+    s = w.state.copy()
+    for k in range(nsteps):
+        rc = orc.step(P, s, orc.dt_max(P, s), max_halvings=0)[0]
+        avg = W.split_sites(s, w.dim, *w.n)[0]
+        if rc != 0 or not np.isfinite(avg).all() or np.abs(avg).max() > 100:
+            return k
+    return nsteps
+
+
+def test_viscous_cfl_limit_1d_is_the_papers():
+    """The paper's von Neumann analysis gives C^v = 0.33 for the viscous part
+    (Eq. (13)). On a viscosity-dominated 1D flow (mu = 3, 48 cells: the viscous
+    term is ~97% of the bound) the unlimited scheme runs 2000 CFL steps bounded at
+    C^v = 0.33 and departs within them at 1.05 x 0.33: the stability limit of the
+    oracle's 1D viscous discretisation is the printed one."""
+    import oracle as orc
+    w = W.smooth_1d(48, mu=3.0)
+    assert _steps_until_blowup(orc, w, 2000, cfl_v=0.33) == 2000
+    assert _steps_until_blowup(orc, w, 2000, cfl_v=1.05 * 0.33) < 2000
+
+
+def test_viscous_cfl_2d_default_is_stable_where_papers_is_not():
+    """Reading of Eq. (13) in 2D: with C^v = 0.33/2 a viscosity-dominated 2D flow
+    (mu = 3, 24^2) departs within 100 steps (the cross-derivative terms of Eq. (12)
+    widen the viscous spectrum beyond twice the 1D one); the default
+    C^v = 0.8 x 0.33/2 keeps it bounded for 300 steps."""
+    import oracle as orc
+    w = W.smooth_2d(24, mu=3.0)
+    P = orc.problem(2, 24, 24)
+    assert P.cfl_v == pytest.approx(0.8 * 0.33 / 2) and P.cfl_c == pytest.approx(1.04 / 2)
+    assert _steps_until_blowup(orc, w, 100, cfl_v=0.33 / 2) < 100
+    assert _steps_until_blowup(orc, w, 300) == 300
