@@ -176,15 +176,40 @@ def clocks_stop(p, path):
 
 
 def dist_setup(args):
+    """One process per GPU (torchrun): NCCL for the GPU arms, gloo for the CPU
+    reference arm; no collective touches the data path (replicas / independent
+    problems), only the timing reduction."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        if args.impl != "reference":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
         return dist, rank, ws
     return None, 0, 1
+
+
+def reduce_over_ranks(dist, values, ops):
+    """Reduce floats across ranks ("max" for times, "sum" for work) on the
+    backend's device; returns them unchanged without a process group."""
+    if not dist:
+        return list(values)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    out = []
+    for v, op in zip(values, ops):
+        t = torch.tensor([float(v)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        out.append(float(t.item()))
+    return out
+
+
+def batch_seed(rank):
+    """Problem-set seed of a rank in the batched arm: rank 0 runs the seed-5 set,
+    every other rank an independent set of the same statistics (weak scaling)."""
+    return 5 + rank
 
 
 def reference_arm(args, rank, ws):
@@ -274,7 +299,7 @@ def tube_arm(args, dist, rank, ws):
         ev1.record(stream)
         torch.cuda.synchronize()
         clocks = clocks_stop(cp, cpath)
-        ms = ev0.elapsed_time(ev1)
+        ms = reduce_over_ranks(dist, [ev0.elapsed_time(ev1)], ["max"])[0]
         prof = S.profile()
         S.set_profiling(False)
         st = W.split_sites(S.get_state(), 2, *w.n)
@@ -307,7 +332,7 @@ def batch_arm(args, dist, rank, ws):
     from paper_2609_29081_b300._native import FP64, MIXED
     build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    wls = W.batch_problems(nprob=args.nprob)
+    wls = W.batch_problems(nprob=args.nprob, seed=batch_seed(rank))
     B = BatchSolver(wls, precision=MIXED)
     for i, w in enumerate(wls):
         B.set_state(i, w.state)
@@ -330,11 +355,7 @@ def batch_arm(args, dist, rank, ws):
     st = [B.stats(i) for i in range(len(wls))]
     updates = sum(w.cells * 5 * (s["accepted"] - a0) for w, s, a0 in zip(wls, st, acc0))
     restarts = sum(s["restarts"] for s in st)
-    if dist:
-        t = torch.tensor([ms, updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, updates = float(t[0]), float(t[1])
+    ms, updates = reduce_over_ranks(dist, [ms, updates], ["max", "sum"])
     value = updates / (ms / 1e3)
     # FP64 one by one on a bounded sample (first 16 problems, 2 steps each)
     one_cells, one_ms = 0, 0.0
@@ -356,7 +377,7 @@ def batch_arm(args, dist, rank, ws):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "batched: %d periodic 2D problems, sides from {64..512}, mu log-uniform "
-                                   "[1e-4,1e-2], Mach 0.1-3, 25%% near-vacuum blasts (seed 5)" % len(wls),
+                                   "[1e-4,1e-2], Mach 0.1-3, 25%% near-vacuum blasts (seed 5 + rank)" % len(wls),
                        "cells": int(sum(w.cells for w in wls)), "tuned": cfg, "restarts": restarts,
                        "graph": True, "warmup_steps_run": warm_done},
             "clocks": clocks, "gpu_launches": nlaunch * args.steps,
@@ -507,10 +528,7 @@ def single_run(args, w, precision, dist, ws, e2e):
         ms = ev0.elapsed_time(ev1)
         prof = S.profile()
         S.set_profiling(False)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_over_ranks(dist, [ms], ["max"])[0]
         out.update(ms=ms, restarts=restarts, launches=prof["launches"],
                    stage_ms=prof["stage_ms"] / max(prof["stage_launches"], 1),
                    value=w.cells * 5 * args.steps * ws / (ms / 1e3))
@@ -528,10 +546,7 @@ def single_run(args, w, precision, dist, ws, e2e):
                 S.get_state(host_out.numpy())
             torch.cuda.synchronize()
             e2e_sec = time.perf_counter() - t0
-            if dist:
-                t = torch.tensor([e2e_sec], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                e2e_sec = float(t.item())
+            e2e_sec = reduce_over_ranks(dist, [e2e_sec], ["max"])[0]
             out["e2e"] = w.cells * 5 * args.e2e_steps * ws / e2e_sec
             out["state_bytes"] = host_in.numel() * 8
         S.close()

@@ -170,7 +170,7 @@ __global__ void k_batch_ghost(BatchProb *probs, int in_idx, int pass)
 
 // --- the persistent stage kernel over the work list
 template <class R, class S, int TX, int TY, int NTH>
-__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, NTH>()) k_batch_stage(BatchArgs B)
+__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch_stage(BatchArgs B)
 {
     extern __shared__ __align__(32) unsigned char smem_batch[];
     V4<R> *sm = reinterpret_cast<V4<R> *>(smem_batch);

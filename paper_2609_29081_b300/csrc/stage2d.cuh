@@ -2,17 +2,21 @@
 //
 // One CTA owns a TX x TY tile of cells. It stages the tile's half lattice
 // (point values + reconstructed cell centres, two lattice nodes of halo) and the
-// cell averages (two cells of halo) in shared memory, then computes in phases:
-//   P0 load         point values and cell averages of the stage input
-//   P1 centres      Simpson inversion (Sec. 2.2) + scaling limiter (Remark 3.1)
-//   P2 primitives   u, v, T, c at every lattice node and every cell
-//   P3 gradients    D_c^(x) Z and D_c^(y) Z (Eq. (8)) at lattice nodes
-//   P4 points       point residual (Eq. (12)), point scaling limiter (Sec. 3.4),
-//                   RK combination, store
-//   P5 faces        low-order cell quantities (Sec. 3.1, 3.2), high-order Simpson
-//                   face flux, LLF flux (Eq. (19)), theta_s (Eq. (22)),
-//                   theta^rho theta^p (Sec. 3.3)
-//   P6 cells        cell residual (Eq. (23)), RK combination, store
+// cell averages (two cells of halo) in shared memory, then computes in phases
+// separated by barriers:
+//   P0  load        point values and cell averages of the stage input
+//   P1  centres +   Simpson inversion (Sec. 2.2) + scaling limiter (Remark 3.1),
+//       primitives  and u, v, T, c at every lattice node
+//   P3  gradients   D_c^(x) Z and D_c^(y) Z (Eq. (8)) at lattice nodes
+//   P4  points +    point residual (Eq. (12)), point scaling limiter (Sec. 3.4),
+//       faces (HO)  RK combination, store; high-order Simpson face fluxes
+//   P5a cells (LO)  low-order cell quantities (Sec. 3.1, 3.2)
+//   P5b faces       LLF flux (Eq. (19)), theta_s (Eq. (22)), theta^rho theta^p
+//                   (Sec. 3.3), limited flux
+//   P6  cells       cell residual (Eq. (23)), RK combination, store
+// The lattice state, primitives and gradients are dead after P4, so the
+// low-order cell records of P5a reuse their space; the shared memory of a 16x8
+// FP32 tile (54 KB) then admits four CTAs per SM.
 // Faces on tile borders are evaluated by both neighbouring tiles from identical
 // inputs with identical code, so the two copies agree bit for bit and the update
 // stays conservative to roundoff.
@@ -43,19 +47,25 @@ struct Tile2 {
     static constexpr int CX = TX + 4, CY = TY + 4, NCA = CX * CY;   // cells with 2 halo
     static constexpr int QX = TX + 2, QY = TY + 2, NCQ = QX * QY;   // cells with 1 halo
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+    // x gradients exist on lattice columns [2, LX-3], y gradients on rows [2, LY-3]
+    static constexpr int GXW = LX - 4, NGX = GXW * LY, NGY = LX * (LY - 4);
     // shared-memory offsets in units of V4 (one node / cell / face record)
     static constexpr int oU = 0;                 // NL  x (rho, rho u, rho v, E)
     static constexpr int oQ = oU + NL;           // NL  x (u, v, T, c)
-    static constexpr int oGX = oQ + NL;          // NL  x d/dx (u, v, T, -)
-    static constexpr int oGY = oGX + NL;         // NL  x d/dy (u, v, T, -)
-    static constexpr int oA = oGY + NL;          // NCA x cell averages
-    static constexpr int oAW = oA + NCA;         // NCA x (u, v, p, T) of the averages
-    static constexpr int oCQ = oAW + NCA;        // NCQ x 4 records of low-order cell quantities
-    static constexpr int oFX = oCQ + 4 * NCQ;    // NFX x limited x-face flux
-    static constexpr int oFY = oFX + NFX;        // NFY x limited y-face flux
+    static constexpr int oGX = oQ + NL;          // NGX x d/dx (u, v, T, -)
+    static constexpr int oGY = oGX + NGX;        // NGY x d/dy (u, v, T, -)
+    static constexpr int oA = oGY + NGY;         // NCA x cell averages
+    static constexpr int oFX = oA + NCA;         // NFX x x-face flux: high order, then limited
+    static constexpr int oFY = oFX + NFX;        // NFY x y-face flux
     static constexpr int total = oFY + NFY;      // in V4 records
+    // after P4: 4 records of low-order cell quantities per cell over the lattice state
+    static constexpr int oCQ = oU;
+    static_assert(4 * NCQ <= NL, "low-order cell records fit in the lattice state");
     template <class R>
     static constexpr size_t bytes() { return (size_t)total * 4 * sizeof(R); }
+    // index of the x / y gradient of lattice node (la, lb)
+    __host__ __device__ static constexpr int gx(int la, int lb) { return lb * GXW + (la - 2); }
+    __host__ __device__ static constexpr int gy(int la, int lb) { return (lb - 2) * LX + la; }
 };
 
 // Four values of one lattice node, cell or face, stored together so that one

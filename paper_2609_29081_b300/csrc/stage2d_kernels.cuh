@@ -61,10 +61,11 @@ __device__ __forceinline__ R comp(const V4<R> &v, int c)
 // sU: conservative, sQ: (u, v, T, c), sGX / sGY: D_c gradients of (u, v, T).
 // ---------------------------------------------------------------------------
 template <class R, int TX, int TY>
-__device__ __forceinline__ void point_residual(const V4<R> *sm, int n, const TileConst<R> &tc, R res[4])
+__device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, const TileConst<R> &tc, R res[4])
 {
     using T = Tile2<TX, TY>;
     constexpr int LX = T::LX;
+    const int n = lb * LX + la;
     const V4<R> *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
     const R mu = tc.mu, ka = tc.ka;
     res[0] = res[1] = res[2] = res[3] = R(0);
@@ -130,13 +131,13 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int n, const Til
         for (int k = 0; k < 5; ++k) {
             if (k == 2) continue;
             const R wc = (R)kDC[k];
-            if (l == 0) {   // K_12 d_y Z
-                const V4<R> gy = sGY[n + (k - 2)];
+            if (l == 0) {   // K_12 d_y Z at the x-neighbours
+                const V4<R> gy = sGY[T::gy(la + k - 2, lb)];
                 g1 += wc * (-mu23 * gy.y);
                 g2 += wc * (mu * gy.x);
                 g3 += wc * (mu * q[k].y * gy.x - mu23 * q[k].x * gy.y);
-            } else {        // K_21 d_x Z
-                const V4<R> gx = sGX[n + (k - 2) * LX];
+            } else {        // K_21 d_x Z at the y-neighbours
+                const V4<R> gx = sGX[T::gx(la, lb + k - 2)];
                 g1 += wc * (mu * gx.y);
                 g2 += wc * (-mu23 * gx.x);
                 g3 += wc * (-mu23 * q[k].y * gx.x + mu * q[k].x * gx.y);
@@ -223,12 +224,82 @@ __device__ void lattice_llf(const V4<R> *sm, int l, int A, int B, double dx, dou
 // ---------------------------------------------------------------------------
 // One tile (bx, by) of one problem; the single-problem kernel runs one tile per
 // CTA, the batched persistent kernel loops over (problem, tile) work items.
+// (u, v, p, T) of a cell average, one reciprocal of rho.
+template <class R>
+__device__ __forceinline__ V4<R> cell_prims(const V4<R> &U, R gm1)
+{
+    const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
+    const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
+    return V4<R>{u, v, p, p * r};
+}
+
+// High-order total flux of face item f (x-faces first, then y-faces) of the
+// tile: Simpson's rule over the vertex, edge and vertex point fluxes of the face
+// (Eq. (12)), each with its node gradients; written to the face's flux slot.
+template <class R, int TX, int TY>
+__device__ __forceinline__ void face_high_order(V4<R> *sm, int f, int ntx, int nty, R mu, R ka)
+{
+    using T = Tile2<TX, TY>;
+    constexpr int LX = T::LX;
+    int l, fl, el;   // direction, face index along l (local), index along the face (local)
+    if (f < T::NFX) {
+        l = 0;
+        fl = f % (TX + 1);
+        el = f / (TX + 1);
+        if (fl > ntx || el >= nty) return;
+    } else {
+        l = 1;
+        const int u_ = f - T::NFX;
+        el = u_ % TX;
+        fl = u_ / TX;
+        if (el >= ntx || fl > nty) return;
+    }
+    const V4<R> *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
+    R FH[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int la = l == 0 ? 2 + 2 * fl : 2 + 2 * el + s;
+        const int lb = l == 0 ? 2 + 2 * el + s : 2 + 2 * fl;
+        const int n = lb * LX + la;
+        const V4<R> U = sU[n], Qn = sQ[n], gx = sGX[T::gx(la, lb)], gy = sGY[T::gy(la, lb)];
+        R Fn[4];
+        node_flux<R>(l, U.x, U.y, U.z, U.w, Qn.x, Qn.y, Qn.z, gx.x, gx.y, gx.z, gy.x, gy.y, gy.z, mu, ka, Fn);
+        const R ws = s == 1 ? R(4) / R(6) : R(1) / R(6);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) FH[c] += ws * Fn[c];
+    }
+    V4<R> *slot = l == 0 ? sm + T::oFX + el * (TX + 1) + fl : sm + T::oFY + fl * TX + el;
+    *slot = V4<R>{FH[0], FH[1], FH[2], FH[3]};
+}
+
+// Point nodes of the tile lattice (all nodes but the cell centres), numbered
+// compactly row pair by row pair: an even lattice row holds LX points (vertices
+// and y-edges), the odd row after it (LX + 1) / 2 (x-edges).
+template <int LX, int LY>
+__host__ __device__ constexpr int point_count()
+{
+    return ((LY + 1) / 2) * LX + (LY / 2) * ((LX + 1) / 2);
+}
+template <int LX>
+__device__ __forceinline__ void point_node(int t, int &la, int &lb)
+{
+    constexpr int PAIR = LX + (LX + 1) / 2;
+    const int pr = t / PAIR, r = t - pr * PAIR;
+    if (r < LX) {
+        lb = 2 * pr;
+        la = r;
+    } else {
+        lb = 2 * pr + 1;
+        la = 2 * (r - LX);
+    }
+}
+
 template <class R, class S, int TX, int TY, int NTH>
 __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm)
 {
     using T = Tile2<TX, TY>;
     using Q4 = V4<R>;
-    constexpr int NL = T::NL, LX = T::LX, CX = T::CX, QX = T::QX;
+    constexpr int LX = T::LX, CX = T::CX, QX = T::QX;
     __shared__ int s_bad;
     __shared__ TileConst<R> tc;
     const Layout &L = A.L;
@@ -237,30 +308,32 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     constexpr int nth = NTH;
     const int ntx = min(TX, L.n1 - i0), nty = min(TY, L.n2 - j0);
     const double eps = A.eps;
+    constexpr int NP = point_count<LX, T::LY>();
     Q4 *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
-    Q4 *sA = sm + T::oA, *sAW = sm + T::oAW, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
+    Q4 *sA = sm + T::oA, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
     const S *uin = (const S *)A.uin;
     const Q4 benign = {R(1), R(0), R(0), R(2.5)};
 
     // ---- P0: load point values and cell averages (two-node / two-cell halo),
     // asynchronously: every load of the thread is in flight before the one wait
     static_assert(sizeof(R) == sizeof(S), "tile and storage precision are the same");
-    for (int t = tid; t < NL; t += nth) {
-        const int la = t % LX, lb = t / LX;
+    for (int t = tid; t < NP; t += nth) {
+        int la, lb;
+        point_node<LX>(t, la, lb);
+        const int t_ = lb * LX + la;
         const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
         const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
-        if (!ea && !eb) continue;
         const int site = ea ? (eb ? 3 : 1) : 2;
         const int i = ea ? (a >> 1) : ((a - 1) >> 1);
         const int j = eb ? (b >> 1) : ((b - 1) >> 1);
         if (i <= L.n1 + 2 && j <= L.n2 + 2) {
             const S *g = uin + plane_of(L, site, 0) + cell_off(L, i, j);
-            cp_async_elem(&sU[t].x, g);
-            cp_async_elem(&sU[t].y, g + L.plane);
-            cp_async_elem(&sU[t].z, g + 2 * L.plane);
-            cp_async_elem(&sU[t].w, g + 3 * L.plane);
+            cp_async_elem(&sU[t_].x, g);
+            cp_async_elem(&sU[t_].y, g + L.plane);
+            cp_async_elem(&sU[t_].z, g + 2 * L.plane);
+            cp_async_elem(&sU[t_].w, g + 3 * L.plane);
         } else {
-            sU[t] = benign;
+            sU[t_] = benign;
         }
     }
     for (int t = tid; t < T::NCA; t += nth) {
@@ -285,86 +358,85 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     __syncthreads();
     const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka;
 
-    // ---- P1: cell centres (Simpson inversion, Sec. 2.2) + centre scaling limiter (Remark 3.1)
-    for (int t = tid; t < T::NCQ; t += nth) {
-        const int qi = t % QX, qj = t / QX;
-        const int n = (2 * qj + 1) * LX + (2 * qi + 1);
-        const Q4 ab = sA[(qj + 1) * CX + (qi + 1)];
-        const Q4 e0 = sU[n - 1], e1 = sU[n + 1], e2 = sU[n - LX], e3 = sU[n + LX];
-        const Q4 v0 = sU[n - LX - 1], v1 = sU[n - LX + 1], v2 = sU[n + LX - 1], v3 = sU[n + LX + 1];
-        R Uc[4];
+    // ---- P1: cell centres (Simpson inversion, Sec. 2.2) + centre scaling limiter
+    // (Remark 3.1), and the primitive quantities (u, v, T, c) of every lattice node
+    // with one reciprocal of rho each: u = m_x/rho, v = m_y/rho,
+    // p = (gamma-1)(E - m.u/2), T = p/rho. Centre items write their own node.
+    for (int t = tid; t < T::NCQ + NP; t += nth) {
+        int n;
+        Q4 U;
+        if (t < T::NCQ) {
+            const int qi = t % QX, qj = t / QX;
+            n = (2 * qj + 1) * LX + (2 * qi + 1);
+            const Q4 ab = sA[(qj + 1) * CX + (qi + 1)];
+            const Q4 e0 = sU[n - 1], e1 = sU[n + 1], e2 = sU[n - LX], e3 = sU[n + LX];
+            const Q4 v0 = sU[n - LX - 1], v1 = sU[n - LX + 1], v2 = sU[n + LX - 1], v3 = sU[n + LX + 1];
+            R Uc[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const R edges = comp(e0, c) + comp(e1, c) + comp(e2, c) + comp(e3, c);
-            const R verts = comp(v0, c) + comp(v1, c) + comp(v2, c) + comp(v3, c);
-            Uc[c] = (R(36) * comp(ab, c) - R(4) * edges - verts) / R(16);
-        }
-        if (A.limiter != LIM_NONE) {
-            R mag[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                mag[c] = R(4) * (fabs(comp(ab, c)) + fabs(comp(e0, c)) + fabs(comp(e1, c)) + fabs(comp(e2, c)) +
-                                 fabs(comp(e3, c)));
-            if (!surely_above(Uc, mag, gm1, tc.eps)) {
-                // FP64 island: the centre in FP64 (same expression), then the scaling
-                // toward the cell average of Remark 3.1 if it is below epsilon
-                double Ub[4], Ud[4];
-                for (int c = 0; c < 4; ++c) {
-                    double edges = (double)comp(e0, c) + (double)comp(e1, c) + (double)comp(e2, c) + (double)comp(e3, c);
-                    double verts = (double)comp(v0, c) + (double)comp(v1, c) + (double)comp(v2, c) + (double)comp(v3, c);
-                    Ub[c] = (double)comp(ab, c);
-                    Ud[c] = (36.0 * Ub[c] - 4.0 * edges - verts) / 16.0;
-                }
-                double g1 = A.gamma - 1.0;
-                double pc = g1 * (Ud[3] - (Ud[1] * Ud[1] + Ud[2] * Ud[2]) / (2.0 * Ud[0]));
-                if (!(Ud[0] >= eps) || !(pc >= eps)) {
-                    double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
-                    double Ur[4];
-                    for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
-                    double pL = g1 * (Ub[3] - (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / (2.0 * Ub[0]));
-                    double pH = g1 * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
-                    double th = thr * theta_fn(pL, pH, fmin(eps, pL));
-                    for (int c = 0; c < 4; ++c) Ud[c] = (1.0 - th) * Ub[c] + th * Ud[c];
-                }
-                for (int c = 0; c < 4; ++c) Uc[c] = (R)Ud[c];
+            for (int c = 0; c < 4; ++c) {
+                const R edges = comp(e0, c) + comp(e1, c) + comp(e2, c) + comp(e3, c);
+                const R verts = comp(v0, c) + comp(v1, c) + comp(v2, c) + comp(v3, c);
+                Uc[c] = (R(36) * comp(ab, c) - R(4) * edges - verts) / R(16);
             }
+            if (A.limiter != LIM_NONE) {
+                R mag[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    mag[c] = R(4) * (fabs(comp(ab, c)) + fabs(comp(e0, c)) + fabs(comp(e1, c)) + fabs(comp(e2, c)) +
+                                     fabs(comp(e3, c)));
+                if (!surely_above(Uc, mag, gm1, tc.eps)) {
+                    // FP64 island: the centre in FP64 (same expression), then the scaling
+                    // toward the cell average of Remark 3.1 if it is below epsilon
+                    double Ub[4], Ud[4];
+                    for (int c = 0; c < 4; ++c) {
+                        double edges = (double)comp(e0, c) + (double)comp(e1, c) + (double)comp(e2, c) + (double)comp(e3, c);
+                        double verts = (double)comp(v0, c) + (double)comp(v1, c) + (double)comp(v2, c) + (double)comp(v3, c);
+                        Ub[c] = (double)comp(ab, c);
+                        Ud[c] = (36.0 * Ub[c] - 4.0 * edges - verts) / 16.0;
+                    }
+                    double g1 = A.gamma - 1.0;
+                    double pc = g1 * (Ud[3] - (Ud[1] * Ud[1] + Ud[2] * Ud[2]) / (2.0 * Ud[0]));
+                    if (!(Ud[0] >= eps) || !(pc >= eps)) {
+                        double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
+                        double Ur[4];
+                        for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
+                        double pL = g1 * (Ub[3] - (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / (2.0 * Ub[0]));
+                        double pH = g1 * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
+                        double th = thr * theta_fn(pL, pH, fmin(eps, pL));
+                        for (int c = 0; c < 4; ++c) Ud[c] = (1.0 - th) * Ub[c] + th * Ud[c];
+                    }
+                    for (int c = 0; c < 4; ++c) Uc[c] = (R)Ud[c];
+                }
+            }
+            U = Q4{Uc[0], Uc[1], Uc[2], Uc[3]};
+            sU[n] = U;
+        } else {
+            int la, lb;
+            point_node<LX>(t - T::NCQ, la, lb);
+            n = lb * LX + la;
+            U = sU[n];
         }
-        sU[n] = Q4{Uc[0], Uc[1], Uc[2], Uc[3]};
-    }
-    __syncthreads();
-
-    // ---- P2: primitive quantities at every lattice node and every cell; one
-    // reciprocal of rho each: u = m_x/rho, v = m_y/rho, p = (gamma-1)(E - m.u/2), T = p/rho
-    for (int t = tid; t < NL; t += nth) {
-        const Q4 U = sU[t];
         const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
         const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
         const R Tn = p * r;
-        sQ[t] = Q4{u, v, Tn, sqrt(gam * Tn)};
-    }
-    for (int t = tid; t < T::NCA; t += nth) {
-        const Q4 U = sA[t];
-        const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
-        const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
-        sAW[t] = Q4{u, v, p, p * r};
+        sQ[n] = Q4{u, v, Tn, sqrt(gam * Tn)};
     }
     __syncthreads();
 
-    // ---- P3: D_c gradients (Eq. (8)) of Z = (u, v, T) along x and along y
+    // ---- P3: D_c gradients (Eq. (8)) of Z = (u, v, T) along x (lattice columns
+    // [2, LX-3]) and along y (rows [2, LY-3]), stored compactly
     {
         const R i6x = tc.i6[0], i6y = tc.i6[1];
-        const int nx = (LX - 4) * T::LY;
-        for (int t = tid; t < nx; t += nth) {
-            const int n = (t / (LX - 4)) * LX + 2 + t % (LX - 4);
+        for (int t = tid; t < T::NGX; t += nth) {
+            const int n = (t / T::GXW) * LX + 2 + t % T::GXW;
             const Q4 a = sQ[n - 2], b = sQ[n - 1], c = sQ[n + 1], d = sQ[n + 2];
-            sGX[n] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6x, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6x,
+            sGX[t] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6x, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6x,
                         (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6x, R(0)};
         }
-        const int ny = LX * (T::LY - 4);
-        for (int t = tid; t < ny; t += nth) {
-            const int n = (2 + t / LX) * LX + t % LX;
+        for (int t = tid; t < T::NGY; t += nth) {
+            const int n = 2 * LX + t;
             const Q4 a = sQ[n - 2 * LX], b = sQ[n - LX], c = sQ[n + LX], d = sQ[n + 2 * LX];
-            sGY[n] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6y, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6y,
+            sGY[t] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6y, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6y,
                         (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6y, R(0)};
         }
     }
@@ -379,7 +451,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         const int erow = (lasty && !pery) ? 2 * ntx : 0;
         const int ecor = (lastx && !perx && lasty && !pery) ? 1 : 0;
         const int tot = nreg + ecol + erow + ecor;
-        for (int t = tid; t < tot; t += nth) {
+        for (int t = tid; t < tot + T::NFX + T::NFY; t += nth) {
+            if (t >= tot) {
+                // high-order total face flux: Simpson over vertex, edge, vertex
+                face_high_order<R, TX, TY>(sm, t - tot, ntx, nty, mu, ka);
+                continue;
+            }
             int la, lb;
             if (t < nreg) {
                 const int kind = t / ncell, cc = t % ncell;
@@ -415,7 +492,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 for (int c = 0; c < 4; ++c) g2[c] = ((const S *)A.aux)[po0 + c * L.plane];
             }
             R r[4];
-            point_residual<R, TX, TY>(sm, n, tc, r);
+            point_residual<R, TX, TY>(sm, la, lb, tc, r);
             // the RK combination of point values runs in the storage precision S
             const Q4 Un4 = sU[n];
             const R Un[4] = {Un4.x, Un4.y, Un4.z, Un4.w};
@@ -487,11 +564,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         }
     }
 
+    // the lattice state, primitives and gradients are dead from here on: the
+    // low-order cell records overwrite them
+    __syncthreads();
+
     // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
     for (int t = tid; t < T::NCQ; t += nth) {
         const int ca = (t / QX + 1) * CX + (t % QX + 1);
-        const Q4 U = sA[ca], W = sAW[ca];
-        const Q4 We = sAW[ca + 1], Ww = sAW[ca - 1], Wn = sAW[ca + CX], Ws = sAW[ca - CX];
+        const Q4 U = sA[ca];
+        const Q4 W = cell_prims(U, gm1), We = cell_prims(sA[ca + 1], gm1), Ww = cell_prims(sA[ca - 1], gm1);
+        const Q4 Wn = cell_prims(sA[ca + CX], gm1), Ws = cell_prims(sA[ca - CX], gm1);
         const R i2x = tc.i2[0], i2y = tc.i2[1];
         const R Sxu = (We.x - Ww.x) * i2x, Sxv = (We.y - Ww.y) * i2x, SxT = (We.w - Ww.w) * i2x;
         const R Syu = (Wn.x - Ws.x) * i2y, Syv = (Wn.y - Ws.y) * i2y, SyT = (Wn.w - Ws.w) * i2y;
@@ -540,20 +622,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 fl = u_ / TX;
                 if (el >= ntx || fl > nty) continue;
             }
-            // high-order total flux: Simpson over vertex, edge, vertex
-            R FH[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                const int la = l == 0 ? 2 + 2 * fl : 2 + 2 * el + s;
-                const int lb = l == 0 ? 2 + 2 * el + s : 2 + 2 * fl;
-                const int n = lb * LX + la;
-                const Q4 U = sU[n], Qn = sQ[n], gx = sGX[n], gy = sGY[n];
-                R Fn[4];
-                node_flux<R>(l, U.x, U.y, U.z, U.w, Qn.x, Qn.y, Qn.z, gx.x, gx.y, gx.z, gy.x, gy.y, gy.z, mu, ka, Fn);
-                const R ws = s == 1 ? R(4) / R(6) : R(1) / R(6);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) FH[c] += ws * Fn[c];
-            }
+            // high-order total flux of P4; the limited flux replaces it in place
+            Q4 *fslot = l == 0 ? sFX + el * (TX + 1) + fl : sFY + fl * TX + el;
+            const Q4 fh4 = *fslot;
+            const R FH[4] = {fh4.x, fh4.y, fh4.z, fh4.w};
             R Fout[4];
             R tsr = R(1), tppr = R(1);
             if (A.limiter == LIM_NONE) {
@@ -622,9 +694,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                     tppr = (R)tppd;
                 }
             }
-            const Q4 fo4 = {Fout[0], Fout[1], Fout[2], Fout[3]};
-            if (l == 0) sFX[el * (TX + 1) + fl] = fo4;
-            else sFY[fl * TX + el] = fo4;
+            *fslot = Q4{Fout[0], Fout[1], Fout[2], Fout[3]};
             if (A.theta) {
                 const int gf = l == 0 ? i0 + fl : j0 + fl;   // global face index along l
                 const int ge = l == 0 ? j0 + el : i0 + el;
@@ -730,16 +800,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
 }
 
 // Resident CTAs per SM that the register budget must allow: as many as the
-// tile's shared memory admits (FP32 16x8: three of 128 threads, two of 256;
-// FP32 32x8 and FP64 16x8: one).
-template <class R, int TX, int NTH>
+// tile's shared memory admits (228 KB per SM, 1 KB reserved per CTA, static
+// shared variables), but never fewer registers per thread than the kernel needs
+// without heavy spilling (128 in FP32, 200 in FP64). FP32 16x8: four CTAs of
+// 128 threads or two of 256; FP32 32x8: two; FP64 16x8: two of 128, one of 256.
+template <class R, int TX, int TY, int NTH>
 constexpr int stage_min_ctas()
 {
-    return (sizeof(R) == 8 || TX == 32) ? 1 : (NTH == 128 ? 3 : 2);
+    constexpr int by_smem = 233472 / (int)(Tile2<TX, TY>::template bytes<R>() + 1024 + 512);
+    constexpr int by_regs = 65536 / (NTH * (sizeof(R) == 8 ? 200 : 128));
+    constexpr int m = by_smem < by_regs ? by_smem : by_regs;
+    return m < 1 ? 1 : m;
 }
 
 template <class R, class S, int TX, int TY, int NTH>
-__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, NTH>()) k_stage2d(StageArgs A)
+__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_stage2d(StageArgs A)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     stage_tile<R, S, TX, TY, NTH>(A, blockIdx.x, blockIdx.y, reinterpret_cast<V4<R> *>(smem_raw));
