@@ -40,7 +40,8 @@ class Problem(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int),
                 ("c_s", ctypes.c_double), ("cfl_c", ctypes.c_double),
-                ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
+                ("source", ctypes.c_int), ("src_p0", ctypes.c_double), ("time", ctypes.c_double)]
 
 
 _lib = None

@@ -813,6 +813,50 @@ static void point_low_order(const grid_t *g, int a0, int a1, double dt, double *
 /* The residual L(u) of one stage                                            */
 /* ------------------------------------------------------------------------- */
 
+/* ------------------------------------------------------------------------- */
+/* Manufactured source (Sec. 4, 2D manufactured Taylor-Green vortex): with     */
+/* a = exp(-2 mu t), b = cos 2x + cos 2y, u = a sin x cos y, v = -a cos x sin y, */
+/* rho = 1 and p = p0/(gamma-1) + a^2 b/4, only the energy equation needs      */
+/* S_E = (p_t + u p_x + v p_y)/(gamma-1) - 4 mu a^2 cos^2 x cos^2 y - kappa Lap p */
+/* with p_t = -mu a^2 b, p_x = -a^2 sin(2x)/2, p_y = -a^2 sin(2y)/2,           */
+/* Lap p = -a^2 b. Point values get S at the node, cell averages the 5 x 5     */
+/* Gauss-Legendre average of S over the cell.                                  */
+/* ------------------------------------------------------------------------- */
+
+static double tg_energy_source(const orc_problem *P, double x, double y, double t)
+{
+    double a = exp(-2.0 * P->mu * t), a2 = a * a;
+    double b = cos(2.0 * x) + cos(2.0 * y);
+    double u = a * sin(x) * cos(y), v = -a * cos(x) * sin(y);
+    double pt = -P->mu * a2 * b, px = -a2 * sin(2.0 * x) / 2.0, py = -a2 * sin(2.0 * y) / 2.0;
+    double lap = -a2 * b;
+    double cx = cos(x), cy = cos(y);
+    return (pt + u * px + v * py) / (P->gamma - 1.0) - 4.0 * P->mu * a2 * cx * cx * cy * cy - kappa_of(P) * lap;
+}
+
+static void source_point(const orc_problem *P, double x, double y, double t, double *S)
+{
+    for (int c = 0; c < MAXC; ++c) S[c] = 0.0;
+    if (P->source == ORC_SRC_TAYLOR_GREEN && P->dim == 2) S[3] = tg_energy_source(P, x, y, t);
+}
+
+static void source_cell(const orc_problem *P, double x0, double y0, double hx, double hy, double t, double *S)
+{
+    /* 5-point Gauss-Legendre nodes and weights on [-1, 1] */
+    static const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
+                                 0.9061798459386640};
+    static const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                                 0.2369268850561891};
+    for (int c = 0; c < MAXC; ++c) S[c] = 0.0;
+    if (P->source == ORC_SRC_NONE || P->dim != 2) return;
+    for (int q1 = 0; q1 < 5; ++q1)
+        for (int q0 = 0; q0 < 5; ++q0) {
+            double Sq[MAXC];
+            source_point(P, x0 + 0.5 * hx * (1.0 + gx[q0]), y0 + 0.5 * hy * (1.0 + gx[q1]), t, Sq);
+            for (int c = 0; c < MAXC; ++c) S[c] += 0.25 * gw[q0] * gw[q1] * Sq[c];
+        }
+}
+
 int orc_residual(const orc_problem *P, const double *state, double dt, double *L, double *theta_s,
                  double *theta_pp, int *notpp)
 {
@@ -933,6 +977,13 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
                          g->h[1];
                 L[packed_cell(P, c, i0, i1)] = r;
             }
+    if (P->source != ORC_SRC_NONE)
+        for (int i1 = 0; i1 < imax(g, 1); ++i1)
+            for (int i0 = 0; i0 < g->n[0]; ++i0) {
+                double S[MAXC];
+                source_cell(P, P->lo1 + i0 * g->h[0], P->lo2 + i1 * g->h[1], g->h[0], g->h[1], P->time, S);
+                for (int c = 0; c < nc; ++c) L[packed_cell(P, c, i0, i1)] += S[c];
+            }
 
     /* point-value residual with the scaling limiter of Sec. 3.4 */
     for (int a1 = 0; a1 <= amax(g, 1); ++a1)
@@ -940,6 +991,11 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
             if (is_centre(g, a0, a1)) continue;
             double R[MAXC], U[MAXC], UH[MAXC];
             point_residual(g, a0, a1, R);
+            if (P->source != ORC_SRC_NONE) {
+                double S[MAXC];
+                source_point(P, P->lo1 + 0.5 * a0 * g->h[0], P->lo2 + 0.5 * a1 * g->h[1], P->time, S);
+                for (int c = 0; c < nc; ++c) R[c] += S[c];
+            }
             if (P->limiter != ORC_LIM_NONE) {
                 lat_get(g, g->U, a0, a1, U);
                 for (int c = 0; c < nc; ++c) UH[c] = U[c] + dt * R[c];
@@ -974,6 +1030,9 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
 void orc_defaults(orc_problem *P)
 {
     P->limiter = ORC_LIM_S_PP;
+    P->source = ORC_SRC_NONE;
+    P->src_p0 = 100.0;
+    P->time = 0.0;
     P->c_s = 1.0;
     P->cfl_c = 1.04 / P->dim;
     P->cfl_v = P->dim == 1 ? 0.33 : 0.8 * 0.33 / 2.0;   /* reading R14 */
@@ -1039,13 +1098,19 @@ int orc_step(const orc_problem *P, double *state, double dt, int max_halvings, d
     double *u[6], *Lk[5];
     for (int k = 0; k < 6; ++k) u[k] = (double *)malloc(n * sizeof(double));
     for (int k = 0; k < 5; ++k) Lk[k] = (double *)malloc(n * sizeof(double));
+    /* time of stage state u(s) as a fraction of dt: c(u(s+1)) = sum_k a_sk c(u(k)) + b_sk */
+    double cst[6] = {0.0};
+    for (int s = 0; s < 5; ++s)
+        for (int k = 0; k <= s; ++k) cst[s + 1] += a[s][k] * cst[k] + b[s][k];
+    orc_problem Q = *P;
     int h = 0, rc = ORC_ENOTPP;
     for (;;) {
         int bad = 0;
         memcpy(u[0], state, n * sizeof(double));
         for (int s = 0; s < 5 && !bad; ++s) {
             int nb = 0;
-            orc_residual(P, u[s], dt, Lk[s], NULL, NULL, &nb);
+            Q.time = P->time + cst[s] * dt;
+            orc_residual(&Q, u[s], dt, Lk[s], NULL, NULL, &nb);
             if (nb) bad = 1;
             for (size_t x = 0; x < n; ++x) {
                 double v = 0.0;
@@ -1074,12 +1139,14 @@ int orc_advance(const orc_problem *P, double *state, double t, double t_end, int
                 int *steps, int *restarts)
 {
     int ns = 0, nr = 0, rc = ORC_OK;
+    orc_problem Q = *P;
     while (t < t_end && (max_steps <= 0 || ns < max_steps)) {
         double dt = orc_dt_max(P, state);
         if (t + dt > t_end) dt = t_end - t;
         double taken;
         int h;
-        rc = orc_step(P, state, dt, max_halvings, &taken, &h);
+        Q.time = t;
+        rc = orc_step(&Q, state, dt, max_halvings, &taken, &h);
         nr += h;
         if (rc != ORC_OK) break;
         t += taken;

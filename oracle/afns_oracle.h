@@ -54,7 +54,13 @@ typedef struct {
     double cfl_c;       /* inviscid CFL number C^c */
     double cfl_v;       /* viscous CFL number C^v */
     double eps;         /* cap of the positivity floors epsilon (1e-13 in Sec. 3.3) */
+    int source;         /* ORC_SRC_*: manufactured source term added to L */
+    double src_p0;      /* p0 of the Taylor-Green source (Sec. 4: 100) */
+    double time;        /* time of the state given to orc_residual / orc_step */
 } orc_problem;
+
+#define ORC_SRC_NONE 0
+#define ORC_SRC_TAYLOR_GREEN 1  /* energy source of the 2D manufactured Taylor-Green vortex (Sec. 4) */
 
 /* Fill the paper's defaults for everything but the grid, gas and BCs. */
 void orc_defaults(orc_problem *P);

@@ -33,6 +33,8 @@ class Workload:
     t_end: float
     state: np.ndarray = field(repr=False)
     steps: int = 0          # nominal step count of the configuration (0: run to t_end)
+    source: int = 0         # manufactured source (0: none, 1: Taylor-Green energy source)
+    src_p0: float = 100.0   # p0 of the Taylor-Green source
 
     def __post_init__(self):
         periodize(self.state, self.dim, self.n, self.bc)
@@ -186,6 +188,29 @@ def smooth_2d(n=1024, mu=0.01, Pr=0.72, gamma=1.4, seed=3, steps=200, mean=(1.0,
     s = project(2, nn, lo, hi, gamma, f)
     return Workload("smooth_2d_periodic_%dx%d" % nn, 2, nn, lo, hi, gamma, mu, Pr,
                     (BC_PERIODIC,) * 4, t_end, s, steps)
+
+
+SRC_TAYLOR_GREEN = 1
+
+
+def taylor_green_2d(n=80, t=0.0, mu=1e-5, Pr=1.0, p0=100.0, gamma=1.4, t_end=0.2):
+    """2D manufactured Taylor-Green vortex on [0, 2 pi]^2 (Sec. 4), the exact
+    solution at time t: rho = 1, (u, v) = a (sin x cos y, -cos x sin y),
+    p = p0/(gamma-1) + a^2 (cos 2x + cos 2y)/4 with a = exp(-2 mu t). The energy
+    equation carries the manufactured source (Workload.source = 1)."""
+    lo, hi = (0.0, 0.0), (2 * np.pi, 2 * np.pi)
+    a = np.exp(-2.0 * mu * t)
+
+    def f(x, y):
+        u = a * np.sin(x) * np.cos(y)
+        v = -a * np.cos(x) * np.sin(y)
+        p = p0 / (gamma - 1.0) + a * a * (np.cos(2 * x) + np.cos(2 * y)) / 4.0
+        return np.ones_like(x), [u, v], p
+
+    nn = (n, n) if np.isscalar(n) else tuple(n)
+    st = project(2, nn, lo, hi, gamma, f)
+    return Workload("taylor_green_2d_%dx%d_t%g" % (nn[0], nn[1], t), 2, nn, lo, hi, gamma, mu, Pr,
+                    (BC_PERIODIC,) * 4, t_end, st, 0, SRC_TAYLOR_GREEN, p0)
 
 
 def shock_tube_2d(n=(2000, 1000), mu=1e-3, Pr=0.73, gamma=1.4, t_end=1.0):

@@ -575,3 +575,62 @@ def test_viscous_cfl_2d_default_is_stable_where_papers_is_not():
     assert P.cfl_v == pytest.approx(0.8 * 0.33 / 2) and P.cfl_c == pytest.approx(1.04 / 2)
     assert _steps_until_blowup(orc, w, 100, cfl_v=0.33 / 2) < 100
     assert _steps_until_blowup(orc, w, 300) == 300
+
+
+# ---------------------------------------------------------------------------
+# Manufactured Taylor-Green vortex (Sec. 4): the one 2D exact solution
+# ---------------------------------------------------------------------------
+
+def test_taylor_green_source_is_the_navier_stokes_residual():
+    """The energy source printed with the manufactured Taylor-Green vortex equals
+    the residual of the energy equation of Eqs. (1)-(3) for the prescribed fields,
+    and the mass and momentum equations hold without a source (sympy, from the
+    PDE; independent of the oracle)."""
+    import sympy as sp
+    x, y, t, mu, g, Pr, p0 = sp.symbols("x y t mu gamma Pr p0", positive=True)
+    a = sp.exp(-2 * mu * t)
+    b = sp.cos(2 * x) + sp.cos(2 * y)
+    rho, u, v = sp.Integer(1), a * sp.sin(x) * sp.cos(y), -a * sp.cos(x) * sp.sin(y)
+    p = p0 / (g - 1) + a ** 2 * b / 4
+    kappa = g * mu / ((g - 1) * Pr)
+    E = p / (g - 1) + rho * (u ** 2 + v ** 2) / 2
+    ux, uy, vx, vy = sp.diff(u, x), sp.diff(u, y), sp.diff(v, x), sp.diff(v, y)
+    div = ux + vy
+    txx, tyy, txy = mu * (2 * ux - sp.Rational(2, 3) * div), mu * (2 * vy - sp.Rational(2, 3) * div), mu * (uy + vx)
+    qx, qy = -kappa * sp.diff(p / rho, x), -kappa * sp.diff(p / rho, y)
+    res = [sp.diff(rho, t) + sp.diff(rho * u, x) + sp.diff(rho * v, y),
+           sp.diff(rho * u, t) + sp.diff(rho * u * u + p - txx, x) + sp.diff(rho * u * v - txy, y),
+           sp.diff(rho * v, t) + sp.diff(rho * u * v - txy, x) + sp.diff(rho * v * v + p - tyy, y),
+           sp.diff(E, t) + sp.diff((E + p) * u - (u * txx + v * txy) + qx, x)
+           + sp.diff((E + p) * v - (u * txy + v * tyy) + qy, y)]
+    pt, px, py, lap = -mu * a ** 2 * b, -a ** 2 * sp.sin(2 * x) / 2, -a ** 2 * sp.sin(2 * y) / 2, -a ** 2 * b
+    SE = (pt + u * px + v * py) / (g - 1) - 4 * mu * a ** 2 * sp.cos(x) ** 2 * sp.cos(y) ** 2 - kappa * lap
+    for r, s in zip(res, [0, 0, 0, SE]):
+        assert sp.simplify(sp.expand_trig(r - s)) == 0
+
+
+def test_taylor_green_converges_to_the_exact_solution(orc):
+    """With the manufactured energy source the scheme converges to the exact
+    Taylor-Green solution (mu = 1e-5, Pr = 1, p0 = 100, t = 0.2, limiter s+pp):
+    observed L1 orders of all four cell-average components above 3.4 between 24^2
+    and 48^2 (measured 3.70, 4.88, 4.88, 3.57); without the source the energy
+    error is more than 20 times larger (a dropped or mis-timed source fails)."""
+    T = 0.2
+    errs = []
+    for n in (24, 48):
+        w = W.taylor_green_2d(n)
+        P = orc.problem(2, n, n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, gamma=w.gamma, source=1, src_p0=100.0)
+        s = w.state.copy()
+        rc, ns, nr = orc.advance(P, s, 0.0, T)
+        assert rc == 0
+        ex = W.taylor_green_2d(n, t=T).state
+        errs.append(np.abs(W.split_sites(s, 2, n, n)[0] - W.split_sites(ex, 2, n, n)[0]).sum(axis=(1, 2)) / n ** 2)
+    orders = np.log2(errs[0] / errs[1])
+    assert orders.min() > 3.4, (errs, orders)
+    w = W.taylor_green_2d(24)
+    P = orc.problem(2, 24, 24, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, gamma=w.gamma)
+    s = w.state.copy()
+    orc.advance(P, s, 0.0, T)
+    ex = W.taylor_green_2d(24, t=T).state
+    e_nosrc = np.abs(W.split_sites(s, 2, 24, 24)[0][3] - W.split_sites(ex, 2, 24, 24)[0][3]).sum() / 24 ** 2
+    assert e_nosrc > 20 * errs[0][3], (e_nosrc, errs[0][3])
