@@ -437,7 +437,8 @@ def main():
                                    "perturbation, p=1, mu=0.01, Pr=0.72), CFL steps, limiter s+pp"
                                    % (args.n, args.n),
                        "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (state %.0f MB per buffer, 5 buffers)" % (r["state_bytes"] / 1e6),
+                       "l2": "working set larger than L2: a stage reads 1-3 state buffers of %.0f MB and writes 1-2"
+                             % (w.cells * (20 * 4 if args.precision == "mixed" else 16 * 8) / 1e6),
                        "restarts": r["restarts"], "tuned": r["tuned"], "warmup_steps_run": r["warm_done"]},
             "roofline": stage_roofline(args.precision, cells, r["stage_ms"], peaks, alu_pk),
             "clocks": r["clocks"],
@@ -533,22 +534,25 @@ def single_run(args, w, precision, dist, ws, e2e):
                    stage_ms=prof["stage_ms"] / max(prof["stage_launches"], 1),
                    value=w.cells * 5 * args.steps * ws / (ms / 1e3))
         if e2e:
-            # end to end through the public API with pinned host buffers
-            host_in = torch.from_numpy(S.get_state()).pin_memory()
+            # end to end through the public API with pinned host buffers (FP32
+            # site arrays for the mixed path, FP64 for the FP64 path)
+            f32 = precision == "mixed"
+            host_in = torch.from_numpy(S.get_state_f32() if f32 else S.get_state()).pin_memory()
             host_out = torch.empty_like(host_in).pin_memory()
+            put, get = (S.set_state_f32, S.get_state_f32) if f32 else (S.set_state, S.get_state)
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
-                S.set_state(host_in.numpy())
+                put(host_in.numpy())
                 S.step(0.0)
-                S.get_state(host_out.numpy())
+                get(host_out.numpy())
             torch.cuda.synchronize()
             e2e_sec = time.perf_counter() - t0
             e2e_sec = reduce_over_ranks(dist, [e2e_sec], ["max"])[0]
             out["e2e"] = w.cells * 5 * args.e2e_steps * ws / e2e_sec
-            out["state_bytes"] = host_in.numel() * 8
+            out["state_bytes"] = host_in.numel() * host_in.element_size()
         S.close()
     return out
 

@@ -56,6 +56,13 @@ typedef enum {
 
 typedef enum { AF_FP64 = 0, AF_MIXED = 1 } af_precision;
 typedef enum { AF_LIM_NONE = 0, AF_LIM_PP = 1, AF_LIM_S_PP = 2 } af_limiter;
+/* Manufactured source of the 2D Taylor-Green vortex (Sec. 4): with
+ * a = exp(-2 mu t), b = cos 2x + cos 2y, rho = 1, (u, v) = a (sin x cos y,
+ * -cos x sin y) and p = p0/(gamma-1) + a^2 b/4 solve Eqs. (1)-(3) plus the energy
+ * source S_E = (p_t + u p_x + v p_y)/(gamma-1) - 4 mu a^2 cos^2 x cos^2 y
+ * - kappa Lap p. Point values get S_E at the node and the stage time, cell
+ * averages its 5 x 5 Gauss-Legendre cell average. 2D only. */
+typedef enum { AF_SRC_NONE = 0, AF_SRC_TAYLOR_GREEN = 1 } af_source;
 
 typedef struct {
     int dim;        /* 1 or 2 */
@@ -80,6 +87,8 @@ typedef struct {
     int max_halvings;  /* restarts allowed per step (Remark 3.2); default 30 */
     int tile_x;        /* 2D tile width in cells (0 = autotuned default) */
     int tile_y;        /* 2D tile height in cells (0 = autotuned default) */
+    int source;        /* af_source: manufactured source term added to every stage */
+    double src_p0;     /* p0 of the Taylor-Green source (paper: 100) */
 } af_opts;
 
 /* Fill *o with the paper's defaults for a problem of dimension dim (except C^v
@@ -111,6 +120,17 @@ af_status af_destroy(afns_ctx *ctx);
  */
 af_status af_set_state(afns_ctx *ctx, const double *const site[4], int on_device, double t);
 af_status af_get_state(afns_ctx *ctx, double *const site[4], int on_device, double *t);
+
+/*
+ * FP32 variants for AF_MIXED contexts (AF_EINVAL on an FP64 context): the same
+ * site layout with float elements, copied straight into / out of the FP32 state,
+ * half the bytes of the FP64 calls. af_set_state_f32 starts the compensation
+ * words of the cell averages at zero and validates like af_set_state;
+ * af_get_state_f32 returns every value rounded to FP32 (for a cell average, the
+ * rounding of its compensated value hi + lo).
+ */
+af_status af_set_state_f32(afns_ctx *ctx, const float *const site[4], int on_device, double t);
+af_status af_get_state_f32(afns_ctx *ctx, float *const site[4], int on_device, double *t);
 
 /* Largest stable step of Eq. (13) on the current cell averages. */
 af_status af_dt_max(afns_ctx *ctx, double *dt);
@@ -218,7 +238,7 @@ af_status af_dt_max_noalloc(const af_grid *grid, double gamma, double mu, double
 /* is recomputed with dt/2 in the next batch step while the other problems     */
 /* move on. A batch step never waits for the host, so it is captured once in a */
 /* CUDA graph and replayed. Problems are 2D; precision and limiter come from    */
-/* opts (NULL = paper defaults with AF_MIXED).                                  */
+/* opts (NULL = paper defaults with AF_MIXED); no manufactured source.          */
 /* ------------------------------------------------------------------------- */
 typedef struct afb_ctx afb_ctx;
 

@@ -24,7 +24,7 @@ LIM_NONE, LIM_PP, LIM_S_PP = 0, 1, 2
 EXPORTED = ["af_opts_default", "af_workspace_bytes", "af_create", "af_destroy", "af_set_state",
             "af_get_state", "af_dt_max", "af_step", "af_advance", "af_residual", "af_get_limiter",
             "af_sizes", "af_set_profiling", "af_get_profile", "af_tune", "af_dt_max_noalloc",
-            "af_alu_peak", "af_last_error"]
+            "af_alu_peak", "af_set_state_f32", "af_get_state_f32", "af_last_error"]
 
 
 class AfnsError(RuntimeError):
@@ -45,7 +45,8 @@ class BC(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("limiter", ctypes.c_int), ("c_s", ctypes.c_double),
                 ("cfl_c", ctypes.c_double), ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
-                ("max_halvings", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+                ("max_halvings", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("source", ctypes.c_int), ("src_p0", ctypes.c_double)]
 
 
 _lib = None
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
     L.af_destroy.argtypes = [vp]
     L.af_set_state.argtypes = [vp, P4, ctypes.c_int, ctypes.c_double]
     L.af_get_state.argtypes = [vp, P4, ctypes.c_int, dp]
+    L.af_set_state_f32.argtypes = [vp, P4, ctypes.c_int, ctypes.c_double]
+    L.af_get_state_f32.argtypes = [vp, P4, ctypes.c_int, dp]
     L.af_dt_max.argtypes = [vp, dp]
     L.af_step.argtypes = [vp, ctypes.c_double, dp, ip]
     L.af_advance.argtypes = [vp, ctypes.c_double, ip, ip]
@@ -150,6 +153,8 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, **kw):
+        if getattr(w, "source", 0) and "source" not in kw:
+            kw.update(source=w.source, src_p0=w.src_p0)
         return cls(w.dim, w.n, w.lo, w.hi, w.gamma, w.mu, w.Pr, w.bc, **kw)
 
     def _check(self, st):
@@ -170,20 +175,37 @@ class Solver:
             pass
 
     # -- site pointer arrays of a packed buffer (numpy host array or torch tensor)
-    def _ptrs(self, buf):
+    def _ptrs(self, buf, f32=False):
         P4 = ctypes.c_void_p * 4
         p = P4()
         if isinstance(buf, np.ndarray):
-            assert buf.dtype == np.float64 and buf.flags.c_contiguous and buf.size == self.size
+            assert buf.dtype == (np.float32 if f32 else np.float64) and buf.flags.c_contiguous and buf.size == self.size
             base, on_dev = buf.ctypes.data, 0
         else:
-            assert buf.dtype == self.torch.float64 and buf.is_contiguous() and buf.numel() == self.size
+            assert buf.dtype == (self.torch.float32 if f32 else self.torch.float64)
+            assert buf.is_contiguous() and buf.numel() == self.size
             base, on_dev = buf.data_ptr(), int(buf.is_cuda)
-        o = 0
+        o, esz = 0, 4 if f32 else 8
         for k, shp in enumerate(self.shapes):
-            p[k] = base + 8 * o
+            p[k] = base + esz * o
             o += int(np.prod(shp))
         return p, on_dev
+
+    def set_state_f32(self, state, t=0.0):
+        """FP32 site arrays (mixed-precision contexts only)."""
+        if isinstance(state, np.ndarray):
+            state = np.ascontiguousarray(state, dtype=np.float32)
+        p, dev = self._ptrs(state, f32=True)
+        self._check(self.lib.af_set_state_f32(self.ctx, p, dev, t))
+
+    def get_state_f32(self, out=None):
+        if out is None:
+            out = np.empty(self.size, dtype=np.float32)
+        p, dev = self._ptrs(out, f32=True)
+        t = ctypes.c_double(0)
+        self._check(self.lib.af_get_state_f32(self.ctx, p, dev, ctypes.byref(t)))
+        self.t = t.value
+        return out
 
     def set_state(self, state, t=0.0):
         if isinstance(state, np.ndarray):

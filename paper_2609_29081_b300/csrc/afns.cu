@@ -28,6 +28,8 @@ cudaError_t launch_dt1d_fp64(const Layout &L, const double *buf, double gamma, d
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_validate1d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st);
 cudaError_t launch_ghost1d_f32(const Layout &L, float *buf, cudaStream_t st);
+cudaError_t launch_validate1d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st);
+cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st);
 cudaError_t launch_stage1d_mixed(const StageArgs &A, cudaStream_t st);
 cudaError_t launch_dt1d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
@@ -134,6 +136,8 @@ static void make_layout(const af_grid *g, const int *bc, Layout *L)
     for (int k = 0; k < 4; ++k) L->bc[k] = bc[k];
     L->dx = (g->hi[0] - g->lo[0]) / g->n[0];
     L->dy = g->dim == 2 ? (g->hi[1] - g->lo[1]) / g->n[1] : 1.0;
+    L->lo[0] = g->lo[0];
+    L->lo[1] = g->dim == 2 ? g->lo[1] : 0.0;
     layout_finish(L);
 }
 
@@ -178,6 +182,9 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
     }
     if (o->precision != AF_FP64 && o->precision != AF_MIXED) return *why = "unknown precision", AF_EINVAL;
     if (o->limiter < 0 || o->limiter > 2) return *why = "unknown limiter", AF_EINVAL;
+    if (o->source != AF_SRC_NONE && o->source != AF_SRC_TAYLOR_GREEN) return *why = "unknown source", AF_EINVAL;
+    if (o->source == AF_SRC_TAYLOR_GREEN && g->dim != 2)
+        return *why = "the Taylor-Green source is two-dimensional", AF_EINVAL;
     if (!(o->cfl_c > 0) || !(o->cfl_v > 0) || !(o->eps > 0) || o->max_halvings < 0)
         return *why = "bad CFL numbers, eps or max_halvings", AF_EINVAL;
     return AF_OK;
@@ -199,6 +206,8 @@ af_status af_opts_default(int dim, af_opts *o)
     o->cfl_v = dim == 1 ? 0.33 : 0.8 * 0.33 / 2.0;
     o->eps = 1e-13;
     o->max_halvings = 30;
+    o->source = AF_SRC_NONE;
+    o->src_p0 = 100.0;
     return AF_OK;
 }
 
@@ -381,24 +390,30 @@ static cudaError_t do_validate(afns_ctx *c, const void *buf)
 }
 
 // Copy between the public site arrays and a padded state buffer (dir 0: in, 1: out).
-static af_status copy_sites(afns_ctx *c, void *buf, double *const site[4], int on_device, int dir)
+template <class T>
+static af_status copy_sites_t(afns_ctx *c, void *buf, T *const site[4], int on_device, int dir)
 {
     for (int s = 0; s < c->L.nsite; ++s) {
         if (!site[s]) return fail(c, AF_EINVAL, "null site pointer");
         int w, h;
         site_dims(c, s, &w, &h);
         for (int comp = 0; comp < c->L.nc; ++comp) {
-            double *dev = (double *)buf + plane_of(c->L, s, comp) + (c->dim == 2 ? cell_off(c->L, 0, 0) : 2);
-            double *host = site[s] + (size_t)comp * w * h;
+            T *dev = (T *)buf + plane_of(c->L, s, comp) + (c->dim == 2 ? cell_off(c->L, 0, 0) : 2);
+            T *host = site[s] + (size_t)comp * w * h;
             cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
-            cudaError_t e = dir == 0 ? cudaMemcpy2DAsync(dev, c->L.pitch * sizeof(double), host, w * sizeof(double),
-                                                        w * sizeof(double), h, k, c->st)
-                                     : cudaMemcpy2DAsync(host, w * sizeof(double), dev, c->L.pitch * sizeof(double),
-                                                         w * sizeof(double), h, k, c->st);
+            cudaError_t e = dir == 0 ? cudaMemcpy2DAsync(dev, c->L.pitch * sizeof(T), host, w * sizeof(T),
+                                                        w * sizeof(T), h, k, c->st)
+                                     : cudaMemcpy2DAsync(host, w * sizeof(T), dev, c->L.pitch * sizeof(T),
+                                                         w * sizeof(T), h, k, c->st);
             if (e != cudaSuccess) return cuda_check(c, e, "state copy");
         }
     }
     return AF_OK;
+}
+
+static af_status copy_sites(afns_ctx *c, void *buf, double *const site[4], int on_device, int dir)
+{
+    return copy_sites_t<double>(c, buf, site, on_device, dir);
 }
 
 static af_status sites_in(afns_ctx *c, void *buf, double *const site[4], int on_device)
@@ -449,6 +464,46 @@ extern "C" af_status af_get_state(afns_ctx *c, double *const site[4], int on_dev
     return AF_OK;
 }
 
+// FP32 site arrays of a mixed-precision context: straight into / out of the
+// FP32 state (the compensation words of the averages start at zero; on the way
+// out the averages are their FP32 roundings hi = fl(hi + lo)).
+extern "C" af_status af_set_state_f32(afns_ctx *c, const float *const site[4], int on_device, double t)
+{
+    if (!c || !site) return fail(c, AF_EINVAL, "null argument");
+    if (!c->mixed) return fail(c, AF_EINVAL, "FP32 state arrays need an AF_MIXED context");
+    af_status s = copy_sites_t<float>(c, c->U[0], const_cast<float *const *>(site), on_device, 0);
+    if (s != AF_OK) return s;
+    float *lo = (float *)c->U[0] + comp_plane(c->L, 0);
+    cudaError_t e = cudaMemsetAsync(lo, 0, sizeof(float) * (size_t)c->L.nc * c->L.plane, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
+    if (e == cudaSuccess)
+        e = c->dim == 1 ? launch_validate1d_f32(c->L, (const float *)c->U[0], c->gamma, c->flag, c->st)
+                        : launch_validate2d_f32(c->L, (const float *)c->U[0], c->gamma, c->flag, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "af_set_state_f32");
+    if (*c->h_flag & 1) return fail(c, AF_EINVAL, "state has a DoF outside G (rho <= 0, p <= 0 or not finite)");
+    if (*c->h_flag & 2) return fail(c, AF_EINVAL, "periodic duplicate point values differ from their partners");
+    c->t = t;
+    c->has_state = true;
+    return AF_OK;
+}
+
+extern "C" af_status af_get_state_f32(afns_ctx *c, float *const site[4], int on_device, double *t)
+{
+    if (!c || !site) return fail(c, AF_EINVAL, "null argument");
+    if (!c->mixed) return fail(c, AF_EINVAL, "FP32 state arrays need an AF_MIXED context");
+    if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
+    cudaError_t e = do_ghost(c, c->U[0]);
+    if (e != cudaSuccess) return cuda_check(c, e, "ghost fill");
+    af_status s = copy_sites_t<float>(c, c->U[0], site, on_device, 1);
+    if (s != AF_OK) return s;
+    e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_check(c, e, "af_get_state_f32");
+    if (t) *t = c->t;
+    return AF_OK;
+}
+
 static StageArgs base_args(afns_ctx *c)
 {
     StageArgs A{};
@@ -460,6 +515,8 @@ static StageArgs base_args(afns_ctx *c)
     A.eps = c->opts.eps;
     A.c_s = c->opts.c_s;
     A.limiter = c->opts.limiter;
+    A.source = c->opts.source;
+    A.src_p0 = c->opts.src_p0;
     return A;
 }
 
@@ -501,22 +558,26 @@ static cudaError_t run_rk(afns_ctx *c)
     for (int k = 0; k < 4; ++k) walls |= c->bc[k] == AF_BC_WALL || c->bc[k] == AF_BC_SYMMETRY;
     StageCoef k{};
     k.wall_fix = walls;
+    // time of each stage input as a fraction of dt: c(u(s+1)) = a_ss c(u(s)) + b_s
+    // (u(0) = u^n enters every combination at time 0)
+    double ct[5] = {0.0};
+    for (int s = 1; s < 5; ++s) ct[s] = kRK_a[s - 1][s - 1] * ct[s - 1] + kRK_b[s - 1];
     cudaError_t e;
     // u1 = u0 + b0 dt L(u0)
-    k.a0 = 0; k.a1 = 1; k.a2 = 0; k.cl = kRK_b[0];
+    k.a0 = 0; k.a1 = 1; k.a2 = 0; k.cl = kRK_b[0]; k.ct = ct[0];
     if ((e = run_stage(c, c->U[0], c->U[1], k, nullptr)) != cudaSuccess) return e;
     // u2 = a10 u0 + a11 u1 + b1 dt L(u1)
-    k.a0 = kRK_a[1][0]; k.a1 = kRK_a[1][1]; k.cl = kRK_b[1];
+    k.a0 = kRK_a[1][0]; k.a1 = kRK_a[1][1]; k.cl = kRK_b[1]; k.ct = ct[1];
     if ((e = run_stage(c, c->U[1], c->U[2], k, nullptr)) != cudaSuccess) return e;
     // u3 = a20 u0 + a22 u2 + b2 dt L(u2)
-    k.a0 = kRK_a[2][0]; k.a1 = kRK_a[2][2]; k.cl = kRK_b[2];
+    k.a0 = kRK_a[2][0]; k.a1 = kRK_a[2][2]; k.cl = kRK_b[2]; k.ct = ct[2];
     if ((e = run_stage(c, c->U[2], c->U[1], k, nullptr)) != cudaSuccess) return e;
     // u4 = a30 u0 + a33 u3 + b3 dt L(u3); acc = a42 u2 + a43 u3 + b43 dt L(u3)
-    k.a0 = kRK_a[3][0]; k.a1 = kRK_a[3][3]; k.cl = kRK_b[3];
+    k.a0 = kRK_a[3][0]; k.a1 = kRK_a[3][3]; k.cl = kRK_b[3]; k.ct = ct[3];
     k.acc = 1; k.b2 = kRK_a[4][2]; k.b1 = kRK_a[4][3]; k.bl = kRK_b43;
     if ((e = run_stage(c, c->U[1], c->U[3], k, nullptr)) != cudaSuccess) return e;
     // u5 = acc + a44 u4 + b4 dt L(u4)
-    k.acc = 0; k.a0 = 0; k.a2 = 1; k.a1 = kRK_a[4][4]; k.cl = kRK_b[4];
+    k.acc = 0; k.a0 = 0; k.a2 = 1; k.a1 = kRK_a[4][4]; k.cl = kRK_b[4]; k.ct = ct[4];
     return run_stage(c, c->U[3], c->U[1], k, nullptr);
 }
 

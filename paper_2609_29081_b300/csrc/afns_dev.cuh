@@ -27,6 +27,7 @@ struct Layout {
     int nsite;      // 4 in 2D, 2 in 1D
     int comp;       // compensation planes present (mixed precision)
     int bc[4];
+    double lo[2];   // domain origin (x, y)
     double dx, dy;
     // reciprocal stencil factors per direction, set on the host by layout_finish
     // (so no kernel divides by the grid spacing): 1/dx_l, 1/(6 dx_l),
@@ -81,6 +82,7 @@ struct Ctl {
 struct StageCoef {
     double a0, a1, a2, cl;
     double b1, b2, bl;
+    double ct;        // time of the stage input: t + ct dt (manufactured sources)
     int acc;
     int residual;
     int wall_fix;

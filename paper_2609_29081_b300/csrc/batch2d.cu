@@ -194,6 +194,8 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch
         A.eps = B.eps;
         A.c_s = B.c_s;
         A.limiter = B.limiter;
+        A.source = 0;
+        A.src_p0 = 0.0;
         stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm);
         __syncthreads();
     }
@@ -476,6 +478,7 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
     *out = nullptr;
     af_opts d;
     if (!opts) af_opts_default(2, &d), d.precision = AF_MIXED, opts = &d;
+    if (opts->source != AF_SRC_NONE) return AF_EINVAL;   // manufactured sources: single-problem contexts only
     size_t need = 0;
     if (afb_workspace_bytes(nprob, grids, opts, &need) != AF_OK) return AF_EINVAL;
     for (int p = 0; p < nprob; ++p) {
@@ -524,6 +527,8 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
         for (int k = 0; k < 4; ++k) L.bc[k] = bcs[p].side[k];
         L.dx = (g.hi[0] - g.lo[0]) / g.n[0];
         L.dy = (g.hi[1] - g.lo[1]) / g.n[1];
+        L.lo[0] = g.lo[0];
+        L.lo[1] = g.lo[1];
         layout_finish(&L);
         size_t st = al256((size_t)L.plane * (16 + (c->mixed ? 4 : 0)) * (c->mixed ? 4 : 8));
         for (int k = 0; k < 4; ++k) P.U[k] = q, q += st;

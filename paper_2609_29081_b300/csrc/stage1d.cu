@@ -61,4 +61,11 @@ cudaError_t launch_validate1d_fp64(const Layout &L, const double *buf, double ga
     return cudaGetLastError();
 }
 
+cudaError_t launch_validate1d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st)
+{
+    int blocks = std::min((2 * L.n1 + 1 + 255) / 256, 148 * 8);
+    k_validate1d<float><<<blocks, 256, 0, st>>>(L, buf, gamma, flag);
+    return cudaGetLastError();
+}
+
 }  // namespace afns

@@ -74,12 +74,23 @@ cudaError_t launch_dt_final(const double *partial, int nparts, Ctl *ctl, int cli
 
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st) { return launch_ghost2d<double>(L, buf, st); }
 
-cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st)
+template <class S>
+static cudaError_t launch_validate2d(const Layout &L, const S *buf, double gamma, int *flag, cudaStream_t st)
 {
     long long total = (long long)(L.n1 + 1) * (L.n2 + 1) * 4;
     int blocks = (int)std::min<long long>((total + 255) / 256, 148 * 16);
-    k_validate2d<double><<<blocks, 256, 0, st>>>(L, buf, gamma, flag);
+    k_validate2d<S><<<blocks, 256, 0, st>>>(L, buf, gamma, flag);
     return cudaGetLastError();
+}
+
+cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st)
+{
+    return launch_validate2d<double>(L, buf, gamma, flag, st);
+}
+
+cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st)
+{
+    return launch_validate2d<float>(L, buf, gamma, flag, st);
 }
 
 }  // namespace afns

@@ -37,6 +37,8 @@ struct StageArgs {
     StageCoef k;
     double gamma, mu, kappa, eps, c_s;
     int limiter;
+    int source;        // 0: none, 1: Taylor-Green energy source (Sec. 4 example)
+    double src_p0;
 };
 
 template <int TX, int TY>
@@ -58,7 +60,7 @@ struct Tile2 {
     static constexpr int oFX = oA + NCA;         // NFX x x-face flux: high order, then limited
     static constexpr int oFY = oFX + NFX;        // NFY x y-face flux
     static constexpr int total = oFY + NFY;      // in V4 records
-    // after P4: 4 records of low-order cell quantities per cell over the lattice state
+    // after P4: the 4 x NCQ records of low-order cell quantities over the lattice state
     static constexpr int oCQ = oU;
     static_assert(4 * NCQ <= NL, "low-order cell records fit in the lattice state");
     template <class R>
@@ -138,7 +140,37 @@ __device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs
     }
 }
 
-// Records of the low-order cell quantities (4 consecutive V4 per cell):
+// Manufactured energy source of the 2D Taylor-Green vortex (Sec. 4 example),
+// FP64: a = exp(-2 mu t), b = cos 2x + cos 2y, u = a sin x cos y,
+// v = -a cos x sin y, p = p0/(gamma-1) + a^2 b/4 (rho = 1);
+// S_E = (p_t + u p_x + v p_y)/(gamma-1) - 4 mu a^2 cos^2 x cos^2 y - kappa Lap p,
+// p_t = -mu a^2 b, p_x = -a^2 sin(2x)/2, p_y = -a^2 sin(2y)/2, Lap p = -a^2 b.
+__device__ inline double tg_energy_source(const StageArgs &A, double x, double y, double t)
+{
+    const double a = exp(-2.0 * A.mu * t), a2 = a * a;
+    const double b = cos(2.0 * x) + cos(2.0 * y);
+    const double sx = sin(x), cx = cos(x), sy = sin(y), cy = cos(y);
+    const double u = a * sx * cy, v = -a * cx * sy;
+    const double pt = -A.mu * a2 * b, px = -a2 * sin(2.0 * x) / 2.0, py = -a2 * sin(2.0 * y) / 2.0;
+    return (pt + u * px + v * py) / (A.gamma - 1.0) - 4.0 * A.mu * a2 * cx * cx * cy * cy + A.kappa * a2 * b;
+}
+
+// Its average over the cell [x0, x0 + hx] x [y0, y0 + hy]: 5 x 5 Gauss-Legendre.
+__device__ inline double tg_energy_source_cell(const StageArgs &A, double x0, double y0, double hx, double hy,
+                                               double t)
+{
+    const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
+    const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                          0.2369268850561891};
+    double s = 0.0;
+    for (int q1 = 0; q1 < 5; ++q1)
+        for (int q0 = 0; q0 < 5; ++q0)
+            s += 0.25 * gw[q0] * gw[q1] *
+                 tg_energy_source(A, x0 + 0.5 * hx * (1.0 + gx[q0]), y0 + 0.5 * hy * (1.0 + gx[q1]), t);
+    return s;
+}
+
+// Records of the low-order cell quantities (4 arrays of NCQ records, one per field):
 // [0] total flux F_x, [1] total flux F_y, [2] (rho_x, rho_y, b_x, b_y), [3] (phi1, phi2, -, -)
 enum { CQ_FX = 0, CQ_FY = 1, CQ_RB = 2, CQ_PH = 3 };
 

@@ -457,12 +457,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 face_high_order<R, TX, TY>(sm, t - tot, ntx, nty, mu, ka);
                 continue;
             }
+            // own points, ordered so that neighbouring threads read neighbouring
+            // lattice nodes: the even lattice rows (vertex, y-edge, vertex, ...)
+            // as runs of 2 ntx consecutive nodes, then the x-edges of the odd rows
             int la, lb;
             if (t < nreg) {
-                const int kind = t / ncell, cc = t % ncell;
-                const int il = cc % ntx, jl = cc / ntx;
-                la = 2 + 2 * il + (kind == 1 ? 1 : 0);
-                lb = 2 + 2 * jl + (kind == 0 ? 1 : 0);
+                if (t < 2 * ncell) {
+                    const int rw = t / (2 * ntx), k = t - rw * (2 * ntx);
+                    la = 2 + k;
+                    lb = 2 + 2 * rw;
+                } else {
+                    const int cc = t - 2 * ncell, jl = cc / ntx;
+                    la = 2 + 2 * (cc - jl * ntx);
+                    lb = 3 + 2 * jl;
+                }
             } else if (t < nreg + ecol) {
                 la = 2 + 2 * ntx;
                 lb = 2 + (t - nreg);
@@ -493,6 +501,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
             }
             R r[4];
             point_residual<R, TX, TY>(sm, la, lb, tc, r);
+            if (A.source)
+                r[3] += (R)tg_energy_source(A, L.lo[0] + 0.5 * a * L.dx, L.lo[1] + 0.5 * b * L.dy,
+                                            A.ctl->t + A.k.ct * dt);
             // the RK combination of point values runs in the storage precision S
             const Q4 Un4 = sU[n];
             const R Un[4] = {Un4.x, Un4.y, Un4.z, Un4.w};
@@ -596,11 +607,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         const R py = fabs(Wn.z - R(2) * p + Ws.z) / fabs(Wn.z + R(2) * p + Ws.z);
         const R curl = Sxv - Syu;
         const R ph2 = -div / sqrt(div * div + curl * curl + R(1e-13));
-        Q4 *q = sCQ + 4 * t;
-        q[CQ_FX] = Q4{Fx[0], Fx[1], Fx[2], Fx[3]};
-        q[CQ_FY] = Q4{Fy[0], Fy[1], Fy[2], Fy[3]};
-        q[CQ_RB] = Q4{fabs(u) + cs, fabs(v) + cs, bx, by};
-        q[CQ_PH] = Q4{dmax(px, py), dmax(ph2, R(0)), R(0), R(0)};
+        sCQ[CQ_FX * T::NCQ + t] = Q4{Fx[0], Fx[1], Fx[2], Fx[3]};
+        sCQ[CQ_FY * T::NCQ + t] = Q4{Fy[0], Fy[1], Fy[2], Fy[3]};
+        sCQ[CQ_RB * T::NCQ + t] = Q4{fabs(u) + cs, fabs(v) + cs, bx, by};
+        sCQ[CQ_PH * T::NCQ + t] = Q4{dmax(px, py), dmax(ph2, R(0)), R(0), R(0)};
     }
     __syncthreads();
 
@@ -645,14 +655,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                     aR = aL + CX;
                 }
                 const int fo = l == 0 ? CQ_FX : CQ_FY;
-                const Q4 fL4 = sCQ[4 * qL + fo], fR4 = sCQ[4 * qR + fo];
-                const Q4 rbL = sCQ[4 * qL + CQ_RB], rbR = sCQ[4 * qR + CQ_RB];
+                const Q4 fL4 = sCQ[fo * T::NCQ + qL], fR4 = sCQ[fo * T::NCQ + qR];
+                const Q4 rbL = sCQ[CQ_RB * T::NCQ + qL], rbR = sCQ[CQ_RB * T::NCQ + qR];
                 const Q4 uL4 = sA[aL], uR4 = sA[aR];
                 const R FLc[4] = {fL4.x, fL4.y, fL4.z, fL4.w}, FRc[4] = {fR4.x, fR4.y, fR4.z, fR4.w};
                 const R UbL[4] = {uL4.x, uL4.y, uL4.z, uL4.w}, UbR[4] = {uR4.x, uR4.y, uR4.z, uR4.w};
                 const R lam = l == 0 ? dmax(rbL.x, rbR.x) + dmax(rbL.z, rbR.z) : dmax(rbL.y, rbR.y) + dmax(rbL.w, rbR.w);
                 if (A.limiter == LIM_S_PP) {
-                    const Q4 phL = sCQ[4 * qL + CQ_PH], phR = sCQ[4 * qR + CQ_PH];
+                    const Q4 phL = sCQ[CQ_PH * T::NCQ + qL], phR = sCQ[CQ_PH * T::NCQ + qR];
                     tsr = exp(-tc.cs * dmax(phL.x, phR.x) * dmax(phL.y, phR.y));
                 }
                 bool done = false;
@@ -726,10 +736,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 if (tc.ua0) g0[c] = ld<S>(A.u0, po0 + c * L.plane);
                 if (tc.ua2 || A.k.acc) g2[c] = ld<S>(A.aux, po0 + c * L.plane);
             }
+            const double src = A.source ? tg_energy_source_cell(A, L.lo[0] + (i0 + il) * L.dx,
+                                                                L.lo[1] + (j0 + jl) * L.dy, L.dx, L.dy,
+                                                                A.ctl->t + A.k.ct * dt)
+                                        : 0.0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const double res =
+                double res =
                     -((double)comp(fxr, c) - (double)comp(fxl, c)) * idx - ((double)comp(fyt, c) - (double)comp(fyb, c)) * idy;
+                if (c == 3 && A.source) res += src;
                 const long long po = po0 + c * L.plane;
                 const double Uin = comp(ui, c);
                 double v = A.k.residual ? 0.0 : A.k.a1 * Uin;
@@ -769,17 +784,25 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
             const Q4 fxr = sFX[jl * (TX + 1) + il + 1], fxl = sFX[jl * (TX + 1) + il];
             const Q4 fyt = sFY[(jl + 1) * TX + il], fyb = sFY[jl * TX + il];
             const Q4 ui = sA[(jl + 2) * CX + (il + 2)];
+            // manufactured energy source (FP64, only when enabled): its weighted
+            // contributions enter the compensated sums as float-float values
+            const double src = A.source ? tg_energy_source_cell(A, L.lo[0] + (i0 + il) * L.dx,
+                                                                L.lo[1] + (j0 + jl) * L.dy, L.dx, L.dy,
+                                                                A.ctl->t + A.k.ct * dt)
+                                        : 0.0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float fr = comp(fxr, c), fl = comp(fxl, c), ft = comp(fyt, c), fb = comp(fyb, c);
                 const long long po = plane_of(L, 0, c) + off, pl = comp_plane(L, c) + off;
+                const bool has_src = c == 3 && A.source;
                 if (A.k.residual) {
-                    out[po] = -(fr - fl) * fidx - (ft - fb) * fidy;
+                    out[po] = -(fr - fl) * fidx - (ft - fb) * fidy + (has_src ? (float)src : 0.f);
                     out[pl] = 0.f;
                     continue;
                 }
                 const ff dxf = ff_two_sum(fl, -fr), dyf = ff_two_sum(fb, -ft);   // exact
-                const ff inc = ff_add(ff_mul(wx, dxf), ff_mul(wy, dyf));
+                ff inc = ff_add(ff_mul(wx, dxf), ff_mul(wy, dyf));
+                if (has_src) inc = ff_add(inc, ff_from(A.k.cl * dt * src));
                 const ff uv = {(float)comp(ui, c), ulo[c]};
                 ff v = ff_mul(a1, uv);
                 if (tc.ua0) v = ff_add(v, ff_mul(a0, ff{g0h[c], g0l[c]}));
@@ -787,6 +810,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 if (A.k.acc) {
                     ff ac = ff_add(ff_mul(b2, ff{g2h[c], g2l[c]}), ff_mul(b1, uv));
                     ac = ff_add(ac, ff_add(ff_mul(bx, dxf), ff_mul(by, dyf)));
+                    if (has_src) ac = ff_add(ac, ff_from(A.k.bl * dt * src));
                     aux[po] = ac.h;
                     aux[pl] = ac.l;
                 }

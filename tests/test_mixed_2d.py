@@ -130,3 +130,24 @@ def test_mixed_error_below_discretisation_error():
     disc = np.abs(sol["f64"] - restr).sum() / np.abs(restr).sum()
     fp32 = np.abs(sol["mix"] - sol["f64"]).sum() / np.abs(sol["f64"]).sum()
     assert fp32 < disc, (fp32, disc)
+
+
+def test_f32_state_io():
+    """FP32 site arrays in and out of a mixed context: the round trip is exact,
+    stepping from FP32 input equals stepping from the same values given in FP64,
+    and an FP64 context refuses FP32 arrays."""
+    from paper_2609_29081_b300 import FP64, MIXED, AfnsError, Solver
+    w = W.random_smooth_2d((33, 17), seed=3)
+    s32 = w.state.astype(np.float32)
+    S = Solver.from_workload(w, precision=MIXED)
+    S.set_state_f32(s32)
+    assert np.array_equal(S.get_state_f32(), s32)
+    R = Solver.from_workload(w, precision=MIXED)
+    R.set_state(s32.astype(np.float64))
+    for _ in range(3):
+        S.step(0.0)
+        R.step(0.0)
+    assert np.array_equal(S.get_state(), R.get_state())
+    F = Solver.from_workload(w, precision=FP64)
+    with pytest.raises(AfnsError):
+        F.set_state_f32(s32)
