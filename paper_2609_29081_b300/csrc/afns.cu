@@ -13,11 +13,13 @@
 #include <new>
 #include <string>
 
+#include <cuda.h>
+
 #include "afns.h"
 #include "stage2d.cuh"
 
 namespace afns {
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, cudaStream_t st);
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st);
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st);
@@ -33,11 +35,12 @@ cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamm
 cudaError_t launch_stage1d_mixed(const StageArgs &A, cudaStream_t st);
 cudaError_t launch_dt1d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, cudaStream_t st);
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st);
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st);
+cudaError_t launch_tile_consts(const StageArgs &A, void *out, int fp32, cudaStream_t st);
 cudaError_t launch_to_f64(const Layout &L, const float *src, double *dst, int use_lo, cudaStream_t st);
 
 __global__ void k_set_ctl(Ctl *ctl, double dt, double t, double t_end)
@@ -46,6 +49,7 @@ __global__ void k_set_ctl(Ctl *ctl, double dt, double t, double t_end)
     ctl->t = t;
     ctl->t_end = t_end;
     ctl->notpp = 0;
+    ctl->err = 0;
 }
 __global__ void k_halve_ctl(Ctl *ctl)
 {
@@ -86,6 +90,11 @@ struct afns_ctx {
     bool mixed = false;
     int tile_x = 16;             // 2D tile width (16, or 32 in the mixed path)
     int threads = 256;           // threads per CTA of the stage kernel
+    // TMA tensor maps of the five state buffers for the 2D stage kernel, per tile
+    // width (16, 32): 3D (element of a row, row, plane), box (TX+4, TY+4, 4)
+    CUtensorMap maps[2][5];
+    void *map_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // buffer of maps[.][k] (U[] rotates)
+    void *tconst = nullptr;      // per-stage tile constants (2D stage kernel)
     Ctl *ctl = nullptr;
     Ctl *h_ctl = nullptr;   // pinned mirror
     double *partial = nullptr;
@@ -142,7 +151,7 @@ static void make_layout(const af_grid *g, const int *bc, Layout *L)
 }
 
 struct WsPlan {
-    size_t state, stage64, ctl, partial, theta, flag, total;
+    size_t state, stage64, ctl, partial, theta, flag, tconst, total;
     int nparts;
     size_t nfaces;
 };
@@ -161,8 +170,48 @@ static WsPlan plan_ws(const Layout &L, const af_opts *o)
     p.flag = align256(sizeof(int) * 4);
     // the mixed path converts to / from the FP64 public layout through a staging state
     p.stage64 = o->precision == AF_MIXED ? align256((size_t)L.nsite * L.nc * (size_t)L.plane * sizeof(double)) : 0;
-    p.total = 5 * p.state + p.stage64 + p.ctl + p.partial + p.theta + p.flag;
+    p.tconst = align256(sizeof(TileConst<double>));
+    p.total = 5 * p.state + p.stage64 + p.ctl + p.partial + p.theta + p.flag + p.tconst;
     return p;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map of one 2D state buffer for tiles of TX x TY cells: the box covers
+// the tile's cells with two of halo in each direction (TX+4 elements from the
+// 16-byte aligned row start i0, TY+4 rows) and the 4 component planes of a site.
+static bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty)
+{
+    EncodeTiledFn f = encode_tiled();
+    if (!f) return false;
+    const cuuint64_t gdim[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)L.nsite * L.nc};
+    const cuuint64_t gstride[2] = {(cuuint64_t)L.pitch * esz, (cuuint64_t)L.plane * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)(tx + 4), (cuuint32_t)(ty + 4), 4};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return f(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, buf, gdim, gstride, box,
+             estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static af_status check_args(const af_grid *g, double gamma, double mu, double Pr, const af_bc *bc, const af_opts *o,
@@ -287,6 +336,8 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->theta = (double *)q;
     q += p.theta;
     c->flag = (int *)q;
+    q += p.flag;
+    c->tconst = q;
     c->nfaces = p.nfaces;
     if (cudaMallocHost((void **)&c->h_ctl, sizeof(Ctl) + 16) != cudaSuccess) {
         cudaGetLastError();
@@ -302,6 +353,17 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
         std::fprintf(stderr, "af_create: %s\n", cudaGetErrorString(e));
         af_destroy(c);
         return AF_ECUDA;
+    }
+    if (c->dim == 2) {
+        const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
+        for (int k = 0; k < 5; ++k) c->map_buf[k] = c->U[k];
+        for (int w = 0; w < 2; ++w)
+            for (int k = 0; k < 5; ++k)
+                if (!make_stage_map(&c->maps[w][k], c->map_buf[k], c->L, esz, w == 0 ? 16 : 32, 8)) {
+                    std::fprintf(stderr, "af_create: tensor map encoding failed\n");
+                    af_destroy(c);
+                    return AF_ECUDA;
+                }
     }
     *out = c;
     return AF_OK;
@@ -374,8 +436,12 @@ static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
 {
     c->launches += 1;
     if (c->dim == 1) return c->mixed ? launch_stage1d_mixed(A, c->st) : launch_stage1d_fp64(A, c->st);
-    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->threads, c->st);
-    return launch_stage2d_fp64(A, c->tile_x, c->threads, c->st);
+    int k = 0;
+    while (k < 5 && c->map_buf[k] != A.uin) ++k;
+    if (k == 5) return cudaErrorInvalidValue;
+    const CUtensorMap *map = &c->maps[c->tile_x == 32 ? 1 : 0][k];
+    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->threads, map, c->st);
+    return launch_stage2d_fp64(A, c->tile_x, c->threads, map, c->st);
 }
 
 // Public FP64 site arrays <-> state buffer. The FP64 path copies directly; the
@@ -532,6 +598,11 @@ static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &
     A.out = out;
     A.theta = theta;
     A.k = k;
+    if (c->dim == 2) {
+        A.tconst = c->tconst;
+        if ((e = launch_tile_consts(A, c->tconst, c->mixed ? 1 : 0, c->st)) != cudaSuccess) return e;
+        c->launches += 1;
+    }
     bool prof = c->profiling && c->ev_used < 5;
     if (prof) cudaEventRecord(c->ev[c->ev_used][0], c->st);
     e = do_stage(c, A);
@@ -586,6 +657,7 @@ static af_status read_ctl(afns_ctx *c)
     cudaError_t e = cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e == cudaSuccess && c->profiling) harvest_events(c);
+    if (e == cudaSuccess && c->h_ctl->err) return fail(c, AF_ECUDA, "a stage kernel's tile load timed out");
     return cuda_check(c, e, "control read");
 }
 

@@ -74,7 +74,7 @@ struct Ctl {
     double t_end;     // clip target of the CFL step (<= t: no clip)
     double dt_cfl;    // last CFL bound
     int notpp;        // a low-order state the limiters evaluate left G
-    int pad;
+    int err;          // a tile load of a stage kernel timed out (result invalid)
 };
 
 // SSP-RK54 stage combination: out = a0 u0 + a1 uin + a2 aux + cl dt L(uin);
@@ -204,6 +204,60 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
 #ifdef __CUDA_ARCH__
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+#endif
+}
+
+// --- TMA tile loads: one mbarrier per CTA; thread 0 arms it with the byte count
+// and issues 3D tensor copies (x = element in row, y = row, z = plane) into
+// shared memory; every thread then waits on the barrier's phase with a bounded
+// number of polls. The host-compiler pass of this header is never executed on
+// the GPU and compiles to nothing.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(b), "r"(count) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+#endif
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+#endif
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst_shared, const void *tmap, int x, int y, int z, uint64_t *bar)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(d),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(b)
+        : "memory");
+#endif
+}
+
+// Poll the barrier's phase `parity` at most max_polls times; true once complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long max_polls)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    for (long long k = 0; k < max_polls; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+#else
+    return true;
 #endif
 }
 

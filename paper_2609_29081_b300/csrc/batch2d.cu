@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch
         A.limiter = B.limiter;
         A.source = 0;
         A.src_p0 = 0.0;
-        stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm);
+        A.tconst = nullptr;   // per-problem step sizes: each tile forms its constants
+        stage_tile<R, S, TX, TY, NTH, false>(A, tile % P.tiles_x, tile / P.tiles_x, sm, nullptr);
         __syncthreads();
     }
 }

@@ -21,7 +21,7 @@ cudaError_t launch_ghost2d(const Layout &L, S *buf, cudaStream_t st)
 }
 
 template <class R, class S, int TX, int TY, int NTH>
-cudaError_t launch_stage2d_n(const StageArgs &A, cudaStream_t st)
+cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *map, cudaStream_t st)
 {
     using T = Tile2<TX, TY>;
     size_t smem = T::template bytes<R>();
@@ -38,24 +38,24 @@ cudaError_t launch_stage2d_n(const StageArgs &A, cudaStream_t st)
         attr_set = true;
     }
     dim3 grid((A.L.n1 + TX - 1) / TX, (A.L.n2 + TY - 1) / TY);
-    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A);
+    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A, *map);
     return cudaGetLastError();
 }
 
 // threads: 128 or 256 per CTA (a compile-time constant of the kernel)
 template <class R, class S, int TX, int TY>
-cudaError_t launch_stage2d_t(const StageArgs &A, cudaStream_t st, int threads = 256)
+cudaError_t launch_stage2d_t(const StageArgs &A, const CUtensorMap *map, cudaStream_t st, int threads = 256)
 {
-    if (threads == 128) return launch_stage2d_n<R, S, TX, TY, 128>(A, st);
-    return launch_stage2d_n<R, S, TX, TY, 256>(A, st);
+    if (threads == 128) return launch_stage2d_n<R, S, TX, TY, 128>(A, map, st);
+    return launch_stage2d_n<R, S, TX, TY, 256>(A, map, st);
 }
 
 // Tile shapes: FP64 16x8 only (the 32x8 FP64 tile exceeds shared memory); FP32
 // 16x8 or 32x8. threads: 256 or 128 per CTA (every phase loops over its items).
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, cudaStream_t st)
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st)
 {
     (void)tx;
-    return launch_stage2d_t<double, double, 16, 8>(A, st, threads > 0 ? threads : 256);
+    return launch_stage2d_t<double, double, 16, 8>(A, map, st, threads > 0 ? threads : 256);
 }
 
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
@@ -63,6 +63,13 @@ cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, d
 {
     k_dt_partial2d<double><<<nparts, 256, 0, st>>>(L, buf, gamma, mu, Pr, cfl_c, cfl_v, partial);
     k_dt_final<<<1, 256, 0, st>>>(partial, nparts, ctl, clip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_consts(const StageArgs &A, void *out, int fp32, cudaStream_t st)
+{
+    if (fp32) k_tile_consts<float><<<1, 32, 0, st>>>(A, (TileConst<float> *)out);
+    else k_tile_consts<double><<<1, 32, 0, st>>>(A, (TileConst<double> *)out);
     return cudaGetLastError();
 }
 
@@ -100,10 +107,10 @@ cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamm
 // ---------------------------------------------------------------------------
 namespace afns {
 
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, cudaStream_t st)
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st)
 {
-    if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, st, threads > 0 ? threads : 256);
-    return launch_stage2d_t<float, float, 16, 8>(A, st, threads > 0 ? threads : 256);
+    if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, map, st, threads > 0 ? threads : 256);
+    return launch_stage2d_t<float, float, 16, 8>(A, map, st, threads > 0 ? threads : 256);
 }
 
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st) { return launch_ghost2d<float>(L, buf, st); }

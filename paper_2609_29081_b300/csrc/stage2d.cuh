@@ -22,6 +22,8 @@
 // stays conservative to roundoff.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only; no driver call is made from here)
+
 #include "afns_dev.cuh"
 
 namespace afns {
@@ -39,6 +41,7 @@ struct StageArgs {
     int limiter;
     int source;        // 0: none, 1: Taylor-Green energy source (Sec. 4 example)
     double src_p0;
+    const void *tconst;  // per-stage tile constants computed by k_tile_consts (or null)
 };
 
 template <int TX, int TY>

@@ -224,6 +224,28 @@ __device__ void lattice_llf(const V4<R> *sm, int l, int A, int B, double dx, dou
 // ---------------------------------------------------------------------------
 // One tile (bx, by) of one problem; the single-problem kernel runs one tile per
 // CTA, the batched persistent kernel loops over (problem, tile) work items.
+// Per-tile constants: copied (cp.async, one 4-byte word per thread) from the
+// record k_tile_consts wrote for this stage, or, without one, formed by thread 0.
+template <class R>
+__device__ __forceinline__ void load_tile_consts(TileConst<R> &tc, const StageArgs &A, int tid)
+{
+    static_assert(sizeof(TileConst<R>) % 4 == 0, "word copy");
+    constexpr int NW = sizeof(TileConst<R>) / 4;
+    if (A.tconst) {
+        if (tid < NW) cp_async_elem(reinterpret_cast<unsigned *>(&tc) + tid, reinterpret_cast<const unsigned *>(A.tconst) + tid);
+    } else if (tid == 0) {
+        tile_const_init<R>(tc, A, A.ctl->dt);
+    }
+}
+
+// The per-tile constants of one stage, once per launch (one thread): the FP64
+// products and conversions stay out of every tile's critical path.
+template <class R>
+__global__ void k_tile_consts(StageArgs A, TileConst<R> *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) tile_const_init<R>(*out, A, A.ctl->dt);
+}
+
 // (u, v, p, T) of a cell average, one reciprocal of rho.
 template <class R>
 __device__ __forceinline__ V4<R> cell_prims(const V4<R> &U, R gm1)
@@ -294,14 +316,15 @@ __device__ __forceinline__ void point_node(int t, int &la, int &lb)
     }
 }
 
-template <class R, class S, int TX, int TY, int NTH>
-__device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm)
+template <class R, class S, int TX, int TY, int NTH, bool TMA>
+__device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm, const void *tmap)
 {
     using T = Tile2<TX, TY>;
     using Q4 = V4<R>;
     constexpr int LX = T::LX, CX = T::CX, QX = T::QX;
     __shared__ int s_bad;
     __shared__ TileConst<R> tc;
+    __shared__ __align__(8) uint64_t s_bar;
     const Layout &L = A.L;
     const int i0 = bx * TX, j0 = by * TY;
     const int tid = threadIdx.x;
@@ -314,48 +337,86 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     const S *uin = (const S *)A.uin;
     const Q4 benign = {R(1), R(0), R(0), R(2.5)};
 
-    // ---- P0: load point values and cell averages (two-node / two-cell halo),
-    // asynchronously: every load of the thread is in flight before the one wait
+    // ---- P0: load point values and cell averages (two-node / two-cell halo)
     static_assert(sizeof(R) == sizeof(S), "tile and storage precision are the same");
-    for (int t = tid; t < NP; t += nth) {
-        int la, lb;
-        point_node<LX>(t, la, lb);
-        const int t_ = lb * LX + la;
-        const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
-        const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
-        const int site = ea ? (eb ? 3 : 1) : 2;
-        const int i = ea ? (a >> 1) : ((a - 1) >> 1);
-        const int j = eb ? (b >> 1) : ((b - 1) >> 1);
-        if (i <= L.n1 + 2 && j <= L.n2 + 2) {
-            const S *g = uin + plane_of(L, site, 0) + cell_off(L, i, j);
-            cp_async_elem(&sU[t_].x, g);
-            cp_async_elem(&sU[t_].y, g + L.plane);
-            cp_async_elem(&sU[t_].z, g + 2 * L.plane);
-            cp_async_elem(&sU[t_].w, g + 3 * L.plane);
-        } else {
-            sU[t_] = benign;
+    if constexpr (TMA) {
+        // four 3D tensor copies, one per DoF site: columns [i0-2, i0+TX+1],
+        // rows [j0-2, j0+TY+1], the site's 4 component planes, into a staging
+        // area in the gradient space (unused until P3); then one pass turns the
+        // planes into the 4-component node and cell records
+        constexpr int BX = TX + 4, BY = TY + 4, BOX = 4 * BX * BY;
+        static_assert(BX == CX && BY == T::CY, "the box is the cell frame");
+        static_assert(4 * BOX * sizeof(R) + 128 <= (size_t)(T::NGX + T::NGY) * sizeof(Q4), "staging fits");
+        R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
+        if (tid == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(&s_bar, (unsigned)(4 * BOX * sizeof(R)));
+            for (int site = 0; site < 4; ++site) tma_load_3d(stg + site * BOX, tmap, i0, j0, 4 * site, &s_bar);
         }
-    }
-    for (int t = tid; t < T::NCA; t += nth) {
-        const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
-        if (i <= L.n1 + 2 && j <= L.n2 + 2) {
-            const S *g = uin + plane_of(L, 0, 0) + cell_off(L, i, j);
-            cp_async_elem(&sA[t].x, g);
-            cp_async_elem(&sA[t].y, g + L.plane);
-            cp_async_elem(&sA[t].z, g + 2 * L.plane);
-            cp_async_elem(&sA[t].w, g + 3 * L.plane);
-        } else {
-            sA[t] = benign;
+        // while the copies are in flight: the per-tile constants
+        load_tile_consts<R>(tc, A, tid);
+        if (tid == 0) s_bad = 0;
+        if (!mbar_wait(&s_bar, 0, 1LL << 26)) atomicOr(&A.ctl->err, 1);
+        cp_async_wait_all();
+        for (int t = tid; t < NP; t += nth) {
+            int la, lb;
+            point_node<LX>(t, la, lb);
+            const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+            const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+            const int site = ea ? (eb ? 3 : 1) : 2;
+            const int i = ea ? (a >> 1) : ((a - 1) >> 1);
+            const int j = eb ? (b >> 1) : ((b - 1) >> 1);
+            const R *g = stg + site * BOX + (j - j0 + 2) * BX + (i - i0 + 2);
+            sU[lb * LX + la] = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]}
+                                                                : benign;
         }
+        for (int t = tid; t < T::NCA; t += nth) {
+            const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
+            const R *g = stg + t;
+            sA[t] = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]} : benign;
+        }
+    } else {
+        // element copies (cp.async): every load of the thread is in flight
+        // before the one wait
+        for (int t = tid; t < NP; t += nth) {
+            int la, lb;
+            point_node<LX>(t, la, lb);
+            const int t_ = lb * LX + la;
+            const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+            const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+            const int site = ea ? (eb ? 3 : 1) : 2;
+            const int i = ea ? (a >> 1) : ((a - 1) >> 1);
+            const int j = eb ? (b >> 1) : ((b - 1) >> 1);
+            if (i <= L.n1 + 2 && j <= L.n2 + 2) {
+                const S *g = uin + plane_of(L, site, 0) + cell_off(L, i, j);
+                cp_async_elem(&sU[t_].x, g);
+                cp_async_elem(&sU[t_].y, g + L.plane);
+                cp_async_elem(&sU[t_].z, g + 2 * L.plane);
+                cp_async_elem(&sU[t_].w, g + 3 * L.plane);
+            } else {
+                sU[t_] = benign;
+            }
+        }
+        for (int t = tid; t < T::NCA; t += nth) {
+            const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
+            if (i <= L.n1 + 2 && j <= L.n2 + 2) {
+                const S *g = uin + plane_of(L, 0, 0) + cell_off(L, i, j);
+                cp_async_elem(&sA[t].x, g);
+                cp_async_elem(&sA[t].y, g + L.plane);
+                cp_async_elem(&sA[t].z, g + 2 * L.plane);
+                cp_async_elem(&sA[t].w, g + 3 * L.plane);
+            } else {
+                sA[t] = benign;
+            }
+        }
+        // while the tile loads are in flight: the per-tile constants
+        load_tile_consts<R>(tc, A, tid);
+        if (tid == 0) s_bad = 0;
+        cp_async_wait_all();
     }
-    // while the tile loads are in flight: the step size and the per-tile constants
-    const double dt = A.ctl->dt;
-    if (tid == 0) {
-        s_bad = 0;
-        tile_const_init<R>(tc, A, dt);
-    }
-    cp_async_wait_all();
     __syncthreads();
+    const double dt = A.ctl->dt;
     const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka;
 
     // ---- P1: cell centres (Simpson inversion, Sec. 2.2) + centre scaling limiter
@@ -837,11 +898,14 @@ constexpr int stage_min_ctas()
     return m < 1 ? 1 : m;
 }
 
+// One tile per CTA; the tile is loaded by TMA through the tensor map of the
+// stage input (a 3D map: x = element of a row, y = row, z = plane).
 template <class R, class S, int TX, int TY, int NTH>
-__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_stage2d(StageArgs A)
+__global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
+    k_stage2d(StageArgs A, const __grid_constant__ CUtensorMap tmap)
 {
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    stage_tile<R, S, TX, TY, NTH>(A, blockIdx.x, blockIdx.y, reinterpret_cast<V4<R> *>(smem_raw));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    stage_tile<R, S, TX, TY, NTH, true>(A, blockIdx.x, blockIdx.y, reinterpret_cast<V4<R> *>(smem_raw), &tmap);
 }
 
 // ---------------------------------------------------------------------------
