@@ -51,6 +51,7 @@ struct BatchArgs {
     int in_idx, out_idx;
     double eps, c_s;
     int limiter;
+    void *tconst;               // per-problem tile constants of the stage (TileConst<R>[nprob])
 };
 
 // --- CFL: chunks of 4096 cells
@@ -168,6 +169,43 @@ __global__ void k_batch_ghost(BatchProb *probs, int in_idx, int pass)
     }
 }
 
+// Stage arguments of problem p.
+template <class R>
+__device__ __forceinline__ StageArgs batch_stage_args(const BatchArgs &B, int p)
+{
+    const BatchProb &P = B.probs[p];
+    StageArgs A;
+    A.L = P.L;
+    A.uin = P.U[B.in_idx];
+    A.u0 = P.U[0];
+    A.aux = P.U[2];
+    A.out = P.U[B.out_idx];
+    A.ctl = P.ctl;
+    A.theta = nullptr;
+    A.k = B.k;
+    A.gamma = P.gamma;
+    A.mu = P.mu;
+    A.kappa = P.kappa;
+    A.eps = B.eps;
+    A.c_s = B.c_s;
+    A.limiter = B.limiter;
+    A.source = 0;
+    A.src_p0 = 0.0;
+    A.tconst = reinterpret_cast<const TileConst<R> *>(B.tconst) + p;
+    return A;
+}
+
+// The tile constants of every problem for one stage (its own step size), one
+// thread per problem, before the stage kernel.
+template <class R>
+__global__ void k_batch_tile_consts(BatchArgs B, int nprob)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob || B.probs[p].failed) return;
+    const StageArgs A = batch_stage_args<R>(B, p);
+    tile_const_init<R>(reinterpret_cast<TileConst<R> *>(B.tconst)[p], A, A.ctl->dt);
+}
+
 // --- the persistent stage kernel over the work list
 template <class R, class S, int TX, int TY, int NTH>
 __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch_stage(BatchArgs B)
@@ -179,24 +217,7 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch
         const BatchProb &P = B.probs[p];
         if (P.failed) continue;   // uniform per block
         const int tile = B.item_t[item];
-        StageArgs A;
-        A.L = P.L;
-        A.uin = P.U[B.in_idx];
-        A.u0 = P.U[0];
-        A.aux = P.U[2];
-        A.out = P.U[B.out_idx];
-        A.ctl = P.ctl;
-        A.theta = nullptr;
-        A.k = B.k;
-        A.gamma = P.gamma;
-        A.mu = P.mu;
-        A.kappa = P.kappa;
-        A.eps = B.eps;
-        A.c_s = B.c_s;
-        A.limiter = B.limiter;
-        A.source = 0;
-        A.src_p0 = 0.0;
-        A.tconst = nullptr;   // per-problem step sizes: each tile forms its constants
+        const StageArgs A = batch_stage_args<R>(B, p);
         stage_tile<R, S, TX, TY, NTH, false>(A, tile % P.tiles_x, tile / P.tiles_x, sm, nullptr);
         __syncthreads();
     }
@@ -294,6 +315,7 @@ struct afb_ctx {
     Ctl *d_ctl = nullptr;
     unsigned long long *d_mx = nullptr;
     int *d_chunk_p = nullptr, *d_chunk_c = nullptr;
+    void *d_tconst = nullptr;           // per-problem tile constants of the current stage
     int nchunks = 0;
     int *d_items[3][2] = {};            // per tile config: item_p, item_t (configs share the schedule arrays)
     int nitems[3] = {0, 0, 0};
@@ -435,10 +457,13 @@ static cudaError_t issue_step(afb_ctx *c)
             k.b1 = 0.096059710526147;
             k.bl = 0.063692468666290;
         }
+        B.tconst = c->d_tconst;
+        if (c->mixed) k_batch_tile_consts<float><<<(c->nprob + 127) / 128, 128, 0, c->st>>>(B, c->nprob);
+        else k_batch_tile_consts<double><<<(c->nprob + 127) / 128, 128, 0, c->st>>>(B, c->nprob);
         if ((e = launch_batch_stage(c, B)) != cudaSuccess) return e;
     }
     k_batch_commit<<<(c->nprob + 127) / 128, 128, 0, c->st>>>(c->d_probs, c->nprob, c->opts.max_halvings);
-    c->launches_per_step = 2 + 5 * 3 + 1;
+    c->launches_per_step = 2 + 5 * 4 + 1;
     return cudaGetLastError();
 }
 
@@ -556,6 +581,7 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
     c->nchunks = (int)chunk_p.size();
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_probs, sizeof(BatchProb) * nprob);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_chunk_p, sizeof(int) * c->nchunks * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tconst, sizeof(TileConst<double>) * nprob);
     if (e == cudaSuccess) {
         c->d_chunk_c = c->d_chunk_p + c->nchunks;
         e = cudaMemcpy(c->d_chunk_p, chunk_p.data(), sizeof(int) * c->nchunks, cudaMemcpyHostToDevice);
@@ -616,6 +642,7 @@ af_status afb_destroy(afb_ctx *c)
             if (c->d_items[tb][k]) cudaFree(c->d_items[tb][k]);
     if (c->d_probs) cudaFree(c->d_probs);
     if (c->d_chunk_p) cudaFree(c->d_chunk_p);
+    if (c->d_tconst) cudaFree(c->d_tconst);
     if (c->h_flag) cudaFreeHost(c->h_flag);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;

@@ -246,6 +246,17 @@ __global__ void k_tile_consts(StageArgs A, TileConst<R> *out)
     if (threadIdx.x == 0 && blockIdx.x == 0) tile_const_init<R>(*out, A, A.ctl->dt);
 }
 
+// (u, v, T, c) of a lattice node, one reciprocal of rho: u = m_x/rho,
+// v = m_y/rho, p = (gamma-1)(E - m.u/2), T = p/rho, c = sqrt(gamma T).
+template <class R>
+__device__ __forceinline__ V4<R> node_prims(const V4<R> &U, R gm1, R gam)
+{
+    const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
+    const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
+    const R Tn = p * r;
+    return V4<R>{u, v, Tn, sqrt(gam * Tn)};
+}
+
 // (u, v, p, T) of a cell average, one reciprocal of rho.
 template <class R>
 __device__ __forceinline__ V4<R> cell_prims(const V4<R> &U, R gm1)
@@ -368,8 +379,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
             const int i = ea ? (a >> 1) : ((a - 1) >> 1);
             const int j = eb ? (b >> 1) : ((b - 1) >> 1);
             const R *g = stg + site * BOX + (j - j0 + 2) * BX + (i - i0 + 2);
-            sU[lb * LX + la] = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]}
-                                                                : benign;
+            const Q4 U = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]}
+                                                          : benign;
+            sU[lb * LX + la] = U;
+            // the point's primitives right away (the centres get theirs in P1)
+            sQ[lb * LX + la] = node_prims(U, (R)(A.gamma - 1.0), (R)A.gamma);
         }
         for (int t = tid; t < T::NCA; t += nth) {
             const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
@@ -415,15 +429,35 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         if (tid == 0) s_bad = 0;
         cp_async_wait_all();
     }
+    // the cell update (last phase) reads u^n, the accumulator and the
+    // compensation words of its cells from global memory: start them towards L2
+    // now, so that the last phase does not wait on DRAM
+    {
+        const bool pu0 = A.k.a0 != 0.0, paux = A.k.a2 != 0.0 || A.k.acc;
+        for (int t = tid; t < ntx * nty && !A.k.residual; t += nth) {
+            const long long off = cell_off(L, i0 + t % ntx, j0 + t / ntx);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const long long po = plane_of(L, 0, c) + off;
+                if (pu0) prefetch_l2((const S *)A.u0 + po);
+                if (paux) prefetch_l2((const S *)A.aux + po);
+                if constexpr (sizeof(S) == 4) {
+                    const long long pl = comp_plane(L, c) + off;
+                    prefetch_l2((const S *)A.uin + pl);
+                    if (pu0) prefetch_l2((const S *)A.u0 + pl);
+                    if (paux) prefetch_l2((const S *)A.aux + pl);
+                }
+            }
+        }
+    }
     __syncthreads();
     const double dt = A.ctl->dt;
     const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka;
 
     // ---- P1: cell centres (Simpson inversion, Sec. 2.2) + centre scaling limiter
-    // (Remark 3.1), and the primitive quantities (u, v, T, c) of every lattice node
-    // with one reciprocal of rho each: u = m_x/rho, v = m_y/rho,
-    // p = (gamma-1)(E - m.u/2), T = p/rho. Centre items write their own node.
-    for (int t = tid; t < T::NCQ + NP; t += nth) {
+    // (Remark 3.1), and the primitive quantities (u, v, T, c) of the centres; of
+    // the point nodes too unless the TMA path formed them in P0.
+    for (int t = tid; t < T::NCQ + (TMA ? 0 : NP); t += nth) {
         int n;
         Q4 U;
         if (t < T::NCQ) {
@@ -477,10 +511,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
             n = lb * LX + la;
             U = sU[n];
         }
-        const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
-        const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
-        const R Tn = p * r;
-        sQ[n] = Q4{u, v, Tn, sqrt(gam * Tn)};
+        sQ[n] = node_prims(U, gm1, gam);
     }
     __syncthreads();
 
