@@ -41,7 +41,12 @@ FP64_DERIVED_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 FP32_DERIVED_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read + write) per stage launch from ncu, with the digest of the
 # kernel sources they were taken on; reported only while the sources match.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/stage2d_mixed_smooth1024.md: first RK stage of a step, 32x8 tiles
+    "mixed:1db0a64577a2b414": 129.65e6,
+    # profiles/stage2d_fp64_smooth1024.md: first RK stage of a step, 16x8 tiles
+    "fp64:1db0a64577a2b414": 233.42e6,
+}
 
 
 def kernel_digest(precision):
