@@ -328,6 +328,49 @@ def tube_arm(args, dist, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def ladder_arm(args, rank):
+    """Grid-refinement ladder of the smooth periodic flow (256^2 .. 2048^2 by
+    default) to --t-end (default 0.05): relative L1 distance of the cell averages
+    of N cells from the 2N solution restricted by 2x2 averaging, and the observed
+    orders, for the FP64 and the mixed path (limiter s+pp)."""
+    import torch
+    from paper_2609_29081_b300 import Solver, build, workloads as W
+    from paper_2609_29081_b300._native import FP64, MIXED
+    build.build()
+    t_end = args.t_end if args.t_end > 0 else 0.05
+    ns = [256, 512, 1024, 2048]
+    out = {}
+    for name, prec in (("mixed", MIXED), ("fp64", FP64)):
+        sol, secs = {}, {}
+        for n in ns:
+            w = W.smooth_2d(n)
+            S = Solver.from_workload(w, precision=prec)
+            S.set_state(w.state)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, _ = S.advance(t_end)
+            torch.cuda.synchronize()
+            secs[n] = (time.perf_counter() - t0, steps)
+            sol[n] = W.split_sites(S.get_state(), 2, n, n)[0]
+            S.close()
+        err = []
+        for n in ns[:-1]:
+            f = sol[2 * n]
+            r = 0.25 * (f[:, 0::2, 0::2] + f[:, 1::2, 0::2] + f[:, 0::2, 1::2] + f[:, 1::2, 1::2])
+            err.append(float(np.abs(sol[n] - r).sum() / np.abs(r).sum()))
+        out[name] = {"n": ns[:-1], "l1": err,
+                     "orders": [float(np.log2(err[k] / err[k + 1])) for k in range(len(err) - 1)],
+                     "seconds_steps": {str(n): secs[n] for n in ns}}
+        if name == "mixed":
+            mixed_sol = sol
+        else:
+            out["mixed_vs_fp64_l1"] = {str(n): float(np.abs(mixed_sol[n] - sol[n]).sum() / np.abs(sol[n]).sum())
+                                       for n in ns}
+    if rank == 0:
+        print(json.dumps({"workload": "2D smooth periodic NS refinement ladder, t_end=%g, limiter s+pp" % t_end,
+                          "ladder": out}), flush=True)
+
+
 def batch_arm(args, dist, rank, ws):
     """Batched form: 256 independent periodic problems of uneven sizes (mixed
     precision, persistent stage kernel, CUDA graph, autotuned configuration),
@@ -403,7 +446,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "tube"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "tube", "ladder"])
     ap.add_argument("--t-end", type=float, default=0.0)
     ap.add_argument("--nprob", type=int, default=256)
     args = ap.parse_args()
@@ -417,6 +460,9 @@ def main():
         return
     if args.workload == "tube":
         tube_arm(args, dist, rank, ws)
+        return
+    if args.workload == "ladder":
+        ladder_arm(args, rank)
         return
 
     import torch
@@ -466,12 +512,16 @@ def main():
         Lr, dt, cb = cpu_baseline(w0, S, args)
         Lg, _ = S.residual(dt)
         S.close()
-        avg_r = W.split_sites(Lr, 2, *w0.n)[0]
-        avg_g = W.split_sites(Lg, 2, *w0.n)[0]
+        # the first SSP-RK54 stage update u + b0 dt L of the cell averages, both sides
+        b0 = 0.391752226571890
+        u0 = W.split_sites(w0.state, 2, *w0.n)[0]
+        avg_r = u0 + b0 * dt * W.split_sites(Lr, 2, *w0.n)[0]
+        avg_g = u0 + b0 * dt * W.split_sites(Lg, 2, *w0.n)[0]
         line["cpu_baseline"] = cb
-        line["l1_vs_oracle"] = {"what": "relative L1 distance of one stage residual of cell averages, GPU (%s) "
-                                        "vs oracle, full grid" % args.precision,
-                                "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum())}
+        line["l1_vs_oracle"] = {"what": "relative L1 / Linf distance of the first stage update u + b0 dt L(u) of "
+                                        "the cell averages, GPU (%s) vs oracle, full grid" % args.precision,
+                                "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum()),
+                                "linf": float(np.abs(avg_g - avg_r).max() / np.abs(avg_r).max())}
     print(json.dumps(line), flush=True)
 
 

@@ -85,8 +85,8 @@ typedef struct {
                           for 2D flows whose bound is dominated by the viscous term */
     double eps;        /* positivity floor cap epsilon (Sec. 3.3); paper: 1e-13 */
     int max_halvings;  /* restarts allowed per step (Remark 3.2); default 30 */
-    int tile_x;        /* 2D tile width in cells (0 = autotuned default) */
-    int tile_y;        /* 2D tile height in cells (0 = autotuned default) */
+    int tile_x;        /* 2D tile width in cells: 16 (default) or 32 (AF_MIXED, tile_y 8) */
+    int tile_y;        /* 2D tile height in cells: 8 (default) or 16 (tile_x 16) */
     int source;        /* af_source: manufactured source term added to every stage */
     double src_p0;     /* p0 of the Taylor-Green source (paper: 100) */
 } af_opts;
@@ -164,13 +164,26 @@ af_status af_residual(afns_ctx *ctx, double dt, double *const L[4], int on_devic
 af_status af_get_limiter(afns_ctx *ctx, double *theta_s, double *theta_pp);
 
 /*
- * Autotuner of the 2D stage kernel launch (tile width 16 or 32 cells, 256 or 128
- * threads per CTA; 32-wide tiles only in AF_MIXED): times each candidate on
- * residual evaluations of the current state (the state is not changed) and keeps
- * the fastest for the following steps. Results do not depend on the choice.
- * Needs a state (AF_ESTATE otherwise). Outputs may be NULL.
+ * Autotuner of the 2D stage kernel launch (tiles of 16x8, 16x16 or 32x8 cells,
+ * 256 or 128 threads per CTA; 32x8 tiles only in AF_MIXED): times each candidate
+ * on residual evaluations of the current state (the state is not changed) and
+ * keeps the fastest for the following steps. Results do not depend on the
+ * choice. Needs a state (AF_ESTATE otherwise). Outputs may be NULL.
  */
-af_status af_tune(afns_ctx *ctx, int *tile_x, int *threads);
+af_status af_tune(afns_ctx *ctx, int *tile_x, int *tile_y, int *threads);
+
+/*
+ * Test hook of the bounded tile-load wait (the paper has no counterpart). The 2D
+ * stage kernel loads each tile with TMA copies that complete an mbarrier armed
+ * with the copies' byte count; every thread waits on it for at most 2 s of the
+ * GPU's global timer, after which the kernel flags the step and the call that
+ * reads it (af_step, af_advance, af_residual, af_dt_max) returns AF_ECUDA with a
+ * message, leaving the context usable. extra_bytes > 0 arms the barrier with that
+ * many bytes more than the copies deliver, so every wait runs out; 0 restores
+ * normal operation. extra_bytes must be a multiple of 16. Meant for tests on
+ * small grids: each CTA then spends 2 s.
+ */
+af_status af_debug_tile_wait(afns_ctx *ctx, int extra_bytes);
 
 /* Number of cells n1*n2 and of faces (sizes of the arrays above). */
 af_status af_sizes(const afns_ctx *ctx, size_t *cells, size_t *faces, size_t *site_elems4);

@@ -24,7 +24,7 @@ LIM_NONE, LIM_PP, LIM_S_PP = 0, 1, 2
 EXPORTED = ["af_opts_default", "af_workspace_bytes", "af_create", "af_destroy", "af_set_state",
             "af_get_state", "af_dt_max", "af_step", "af_advance", "af_residual", "af_get_limiter",
             "af_sizes", "af_set_profiling", "af_get_profile", "af_tune", "af_dt_max_noalloc",
-            "af_alu_peak", "af_set_state_f32", "af_get_state_f32", "af_last_error"]
+            "af_alu_peak", "af_set_state_f32", "af_get_state_f32", "af_debug_tile_wait", "af_last_error"]
 
 
 class AfnsError(RuntimeError):
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.af_set_state.argtypes = [vp, P4, ctypes.c_int, ctypes.c_double]
     L.af_get_state.argtypes = [vp, P4, ctypes.c_int, dp]
     L.af_set_state_f32.argtypes = [vp, P4, ctypes.c_int, ctypes.c_double]
+    L.af_debug_tile_wait.argtypes = [vp, ctypes.c_int]
     L.af_get_state_f32.argtypes = [vp, P4, ctypes.c_int, dp]
     L.af_dt_max.argtypes = [vp, dp]
     L.af_step.argtypes = [vp, ctypes.c_double, dp, ip]
@@ -79,7 +80,7 @@ def load(path: str = LIB_PATH):
     L.af_residual.argtypes = [vp, ctypes.c_double, P4, ctypes.c_int, ip]
     L.af_get_limiter.argtypes = [vp, vp, vp]
     L.af_sizes.argtypes = [vp, sp, sp, sp]
-    L.af_tune.argtypes = [vp, ip, ip]
+    L.af_tune.argtypes = [vp, ip, ip, ip]
     L.af_dt_max_noalloc.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     L.af_alu_peak.argtypes = [ctypes.c_int, dp]
     L.af_set_profiling.argtypes = [vp, ctypes.c_int]
@@ -253,9 +254,9 @@ class Solver:
         return ts, tp
 
     def tune(self):
-        tx, th = ctypes.c_int(0), ctypes.c_int(0)
-        self._check(self.lib.af_tune(self.ctx, ctypes.byref(tx), ctypes.byref(th)))
-        return {"tile_x": tx.value, "threads": th.value}
+        tx, ty, th = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.lib.af_tune(self.ctx, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(th)))
+        return {"tile_x": tx.value, "tile_y": ty.value, "threads": th.value}
 
     def set_profiling(self, on=True):
         self._check(self.lib.af_set_profiling(self.ctx, int(on)))

@@ -19,7 +19,7 @@
 #include "stage2d.cuh"
 
 namespace afns {
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st);
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map, cudaStream_t st);
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st);
@@ -35,7 +35,7 @@ cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamm
 cudaError_t launch_stage1d_mixed(const StageArgs &A, cudaStream_t st);
 cudaError_t launch_dt1d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st);
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map, cudaStream_t st);
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
@@ -88,13 +88,14 @@ struct afns_ctx {
     void *U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // u^n, u1/u3/u5, u2/acc, u4, residual
     double *stage64 = nullptr;   // FP64 staging state of the mixed path
     bool mixed = false;
-    int tile_x = 16;             // 2D tile width (16, or 32 in the mixed path)
+    int tile_x = 16, tile_y = 8; // 2D tile: 16x8, 16x16, or 32x8 (mixed path)
     int threads = 256;           // threads per CTA of the stage kernel
     // TMA tensor maps of the five state buffers for the 2D stage kernel, per tile
-    // width (16, 32): 3D (element of a row, row, plane), box (TX+4, TY+4, 4)
-    CUtensorMap maps[2][5];
+    // shape (16x8, 32x8, 16x16): 3D (element of a row, row, plane), box (TX+4, TY+4, 4)
+    CUtensorMap maps[3][5];
     void *map_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // buffer of maps[.][k] (U[] rotates)
     void *tconst = nullptr;      // per-stage tile constants (2D stage kernel)
+    int debug_extra_tx = 0;      // test hook of af_debug_tile_wait
     Ctl *ctl = nullptr;
     Ctl *h_ctl = nullptr;   // pinned mirror
     double *partial = nullptr;
@@ -327,6 +328,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->L.comp = c->mixed ? 1 : 0;
     c->stage64 = c->mixed ? (double *)q : nullptr;
     c->tile_x = (c->mixed && opts->tile_x == 32) ? 32 : 16;
+    c->tile_y = (c->tile_x == 16 && opts->tile_y == 16) ? 16 : 8;
     q += p.stage64;
     c->ctl = (Ctl *)q;
     q += p.ctl;
@@ -357,9 +359,10 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     if (c->dim == 2) {
         const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
         for (int k = 0; k < 5; ++k) c->map_buf[k] = c->U[k];
-        for (int w = 0; w < 2; ++w)
+        static const int shape[3][2] = {{16, 8}, {32, 8}, {16, 16}};
+        for (int w = 0; w < 3; ++w)
             for (int k = 0; k < 5; ++k)
-                if (!make_stage_map(&c->maps[w][k], c->map_buf[k], c->L, esz, w == 0 ? 16 : 32, 8)) {
+                if (!make_stage_map(&c->maps[w][k], c->map_buf[k], c->L, esz, shape[w][0], shape[w][1])) {
                     std::fprintf(stderr, "af_create: tensor map encoding failed\n");
                     af_destroy(c);
                     return AF_ECUDA;
@@ -439,9 +442,9 @@ static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
     int k = 0;
     while (k < 5 && c->map_buf[k] != A.uin) ++k;
     if (k == 5) return cudaErrorInvalidValue;
-    const CUtensorMap *map = &c->maps[c->tile_x == 32 ? 1 : 0][k];
-    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->threads, map, c->st);
-    return launch_stage2d_fp64(A, c->tile_x, c->threads, map, c->st);
+    const CUtensorMap *map = &c->maps[c->tile_x == 32 ? 1 : (c->tile_y == 16 ? 2 : 0)][k];
+    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->tile_y, c->threads, map, c->st);
+    return launch_stage2d_fp64(A, c->tile_x, c->tile_y, c->threads, map, c->st);
 }
 
 // Public FP64 site arrays <-> state buffer. The FP64 path copies directly; the
@@ -598,6 +601,7 @@ static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &
     A.out = out;
     A.theta = theta;
     A.k = k;
+    A.extra_tx = c->debug_extra_tx;
     if (c->dim == 2) {
         A.tconst = c->tconst;
         if ((e = launch_tile_consts(A, c->tconst, c->mixed ? 1 : 0, c->st)) != cudaSuccess) return e;
@@ -773,6 +777,13 @@ extern "C" af_status af_residual(afns_ctx *c, double dt, double *const Lout[4], 
     return AF_OK;
 }
 
+extern "C" af_status af_debug_tile_wait(afns_ctx *c, int extra_bytes)
+{
+    if (!c || extra_bytes < 0 || extra_bytes % 16) return fail(c, AF_EINVAL, "extra_bytes: a multiple of 16, >= 0");
+    c->debug_extra_tx = extra_bytes;
+    return AF_OK;
+}
+
 extern "C" af_status af_get_limiter(afns_ctx *c, double *theta_s, double *theta_pp)
 {
     if (!c) return AF_EINVAL;
@@ -813,20 +824,20 @@ extern "C" af_status af_get_profile(afns_ctx *c, double *stage_ms, long long *st
 // (tile width, threads per CTA) on residual evaluations of the current state,
 // which leave the state untouched, and keeps the fastest. Results do not depend
 // on the configuration (every face and node is computed by the same arithmetic).
-extern "C" af_status af_tune(afns_ctx *c, int *tile_x, int *threads)
+extern "C" af_status af_tune(afns_ctx *c, int *tile_x, int *tile_y, int *threads)
 {
     if (!c) return AF_EINVAL;
     if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
     if (c->dim == 2) {
         struct Cand {
-            int tx, th;
+            int tx, ty, th;
         };
-        const Cand cands[] = {{16, 256}, {16, 128}, {32, 256}, {32, 128}};
+        const Cand cands[] = {{16, 8, 256}, {16, 8, 128}, {32, 8, 256}, {32, 8, 128}, {16, 16, 256}, {16, 16, 128}};
         cudaEvent_t a, b;
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
             return cuda_check(c, cudaGetLastError(), "tune events");
         float best = 1e30f;
-        Cand pick{c->tile_x, c->threads};
+        Cand pick{c->tile_x, c->tile_y, c->threads};
         int prof = c->profiling;
         c->profiling = 0;
         cudaError_t e = cudaSuccess;
@@ -838,6 +849,7 @@ extern "C" af_status af_tune(afns_ctx *c, int *tile_x, int *threads)
             if (e != cudaSuccess) break;
             if (cd.tx == 32 && !c->mixed) continue;
             c->tile_x = cd.tx;
+            c->tile_y = cd.ty;
             c->threads = cd.th;
             e = run_stage(c, c->U[0], c->U[4], k, nullptr);   // warm-up (sets the shared-memory limit)
             if (e == cudaSuccess) e = cudaEventRecord(a, c->st);
@@ -852,10 +864,12 @@ extern "C" af_status af_tune(afns_ctx *c, int *tile_x, int *threads)
         cudaEventDestroy(b);
         c->profiling = prof;
         c->tile_x = pick.tx;
+        c->tile_y = pick.ty;
         c->threads = pick.th;
         if (e != cudaSuccess) return cuda_check(c, e, "tune");
     }
     if (tile_x) *tile_x = c->tile_x;
+    if (tile_y) *tile_y = c->tile_y;
     if (threads) *threads = c->threads;
     return AF_OK;
 }

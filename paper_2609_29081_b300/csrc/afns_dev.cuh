@@ -249,12 +249,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst_shared, const void *tmap, 
 #endif
 }
 
-// Poll the barrier's phase `parity` at most max_polls times; true once complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long max_polls)
+// Poll the barrier's phase `parity` until it completes (true) or max_ns of the
+// global timer have passed (false): a wait that can end, whatever happens to the
+// copies it waits for.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long max_ns)
 {
 #ifdef __CUDA_ARCH__
     const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-    for (long long k = 0; k < max_polls; ++k) {
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t0));
+    for (;;) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -262,8 +266,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
             : "r"(b), "r"(parity)
             : "memory");
         if (done) return true;
+        asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+        if (t - t0 > max_ns) return false;
     }
-    return false;
 #else
     return true;
 #endif

@@ -50,11 +50,14 @@ cudaError_t launch_stage2d_t(const StageArgs &A, const CUtensorMap *map, cudaStr
     return launch_stage2d_n<R, S, TX, TY, 256>(A, map, st);
 }
 
-// Tile shapes: FP64 16x8 only (the 32x8 FP64 tile exceeds shared memory); FP32
-// 16x8 or 32x8. threads: 256 or 128 per CTA (every phase loops over its items).
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st)
+// Tile shapes: FP64 16x8 or 16x16 (the 32x8 FP64 tile exceeds shared memory);
+// FP32 16x8, 32x8 or 16x16. threads: 256 or 128 per CTA (every phase loops over
+// its items).
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map,
+                                cudaStream_t st)
 {
     (void)tx;
+    if (ty == 16) return launch_stage2d_t<double, double, 16, 16>(A, map, st, threads > 0 ? threads : 256);
     return launch_stage2d_t<double, double, 16, 8>(A, map, st, threads > 0 ? threads : 256);
 }
 
@@ -107,9 +110,11 @@ cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamm
 // ---------------------------------------------------------------------------
 namespace afns {
 
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int threads, const CUtensorMap *map, cudaStream_t st)
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map,
+                                 cudaStream_t st)
 {
     if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, map, st, threads > 0 ? threads : 256);
+    if (ty == 16) return launch_stage2d_t<float, float, 16, 16>(A, map, st, threads > 0 ? threads : 256);
     return launch_stage2d_t<float, float, 16, 8>(A, map, st, threads > 0 ? threads : 256);
 }
 

@@ -42,6 +42,7 @@ struct StageArgs {
     int source;        // 0: none, 1: Taylor-Green energy source (Sec. 4 example)
     double src_p0;
     const void *tconst;  // per-stage tile constants computed by k_tile_consts (or null)
+    int extra_tx;        // test hook: bytes the tile-load barrier expects beyond the copies (0)
 };
 
 template <int TX, int TY>

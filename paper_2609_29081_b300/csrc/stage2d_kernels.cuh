@@ -362,13 +362,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         if (tid == 0) mbar_init(&s_bar, 1);
         __syncthreads();
         if (tid == 0) {
-            mbar_expect_tx(&s_bar, (unsigned)(4 * BOX * sizeof(R)));
+            mbar_expect_tx(&s_bar, (unsigned)(4 * BOX * sizeof(R)) + (unsigned)A.extra_tx);
             for (int site = 0; site < 4; ++site) tma_load_3d(stg + site * BOX, tmap, i0, j0, 4 * site, &s_bar);
         }
         // while the copies are in flight: the per-tile constants
         load_tile_consts<R>(tc, A, tid);
         if (tid == 0) s_bad = 0;
-        if (!mbar_wait(&s_bar, 0, 1LL << 26)) atomicOr(&A.ctl->err, 1);
+        // a load that has not landed after 2 s is reported, not waited for forever
+        if (!mbar_wait(&s_bar, 0, 2000000000ull)) atomicOr(&A.ctl->err, 1);
         cp_async_wait_all();
         for (int t = tid; t < NP; t += nth) {
             int la, lb;

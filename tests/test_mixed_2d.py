@@ -70,13 +70,13 @@ def test_mixed_ten_steps_against_fp64_oracle(orc, case):
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_launch_configuration_does_not_change_results(prec):
-    """Tile width and CTA size (autotuned) change no bit of the result."""
+    """Tile shape and CTA size (autotuned) change no bit of the result."""
     from paper_2609_29081_b300 import MIXED, FP64, Solver
     w = W.random_smooth_2d((70, 37), seed=13, bc=(1, 1, 2, 3))
     p = MIXED if prec == "mixed" else FP64
     outs = []
-    for tx in ((16, 32) if prec == "mixed" else (16,)):
-        S = Solver.from_workload(w, precision=p, tile_x=tx)
+    for tx, ty in (((16, 8), (32, 8), (16, 16)) if prec == "mixed" else ((16, 8), (16, 16))):
+        S = Solver.from_workload(w, precision=p, tile_x=tx, tile_y=ty)
         S.set_state(w.state)
         r0, _ = S.residual(1e-3)
         cfg = S.tune()
