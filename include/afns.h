@@ -51,7 +51,10 @@ typedef enum {
     AF_BC_PERIODIC = 0,
     AF_BC_WALL = 1,        /* no-slip adiabatic wall */
     AF_BC_SYMMETRY = 2,    /* slip wall / symmetry plane */
-    AF_BC_TRANSMISSIVE = 3 /* zero-gradient outflow */
+    AF_BC_TRANSMISSIVE = 3, /* zero-gradient outflow */
+    AF_BC_EXACT = 4         /* 1D: ghost data from the exact moving viscous shock of Sec. 4
+                               (Becker's solution, parameters ex_M0 / ex_uinf of af_opts)
+                               at each stage's time */
 } af_bc_kind;
 
 typedef enum { AF_FP64 = 0, AF_MIXED = 1 } af_precision;
@@ -89,6 +92,8 @@ typedef struct {
     int tile_y;        /* 2D tile height in cells: 8 (default) or 16 (tile_x 16) */
     int source;        /* af_source: manufactured source term added to every stage */
     double src_p0;     /* p0 of the Taylor-Green source (paper: 100) */
+    double ex_M0;      /* AF_BC_EXACT: upstream Mach number of the Becker shock (default 3) */
+    double ex_uinf;    /* AF_BC_EXACT: translation velocity of the shock (default 0.2) */
 } af_opts;
 
 /* Fill *o with the paper's defaults for a problem of dimension dim (except C^v

@@ -41,7 +41,8 @@ class Problem(ctypes.Structure):
                 ("bc", ctypes.c_int * 4), ("limiter", ctypes.c_int),
                 ("c_s", ctypes.c_double), ("cfl_c", ctypes.c_double),
                 ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
-                ("source", ctypes.c_int), ("src_p0", ctypes.c_double), ("time", ctypes.c_double)]
+                ("source", ctypes.c_int), ("src_p0", ctypes.c_double), ("time", ctypes.c_double),
+                ("ex_M0", ctypes.c_double), ("ex_uinf", ctypes.c_double)]
 
 
 _lib = None

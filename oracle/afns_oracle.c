@@ -34,6 +34,10 @@
  *      momentum signs flipped (no-slip: both, symmetry: normal), transmissive is
  *      the unflipped mirror. After every RK stage the wall point values get zero
  *      (normal) momentum with their internal energy kept.
+ *  R15 Exact boundary data (1D viscous shock, Sec. 4): the ghost cell averages
+ *      (5-point Gauss-Legendre) and ghost point values come from the exact Becker
+ *      solution at the stage's time; the boundary point values themselves evolve
+ *      with the scheme like every other point.
  *  R14 CFL numbers of Eq. (13): C^c = 1.04/d as printed; C^v = 0.33 in 1D as
  *      printed, but 0.8 * 0.33/2 in 2D. With 0.33/2 the 2D scheme grows a
  *      high-frequency mode wherever the viscous term dominates the bound (the
@@ -513,6 +517,82 @@ static void fill_ghosts(grid_t *g)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Exact moving viscous shock (Sec. 4, 1D viscous shock wave; Becker's         */
+/* solution): rho_L = w_L = m0 = 1, w_R / w_L = ((gamma-1) + 2/M0^2)/(gamma+1),  */
+/* w0 = sqrt(w_L w_R); the relative velocity w(xi), xi = x - u_inf t, solves      */
+/* xi = 2 mu gamma / ((gamma+1) m0 Pr) [w_L/(w_L-w_R) log((w_L-w)/(w_L-w0))     */
+/*       - w_R/(w_L-w_R) log((w-w_R)/(w0-w_R))],                                */
+/* rho = m0/w, u = u_inf + w, p = (gamma-1) rho e,                               */
+/* e = ((gamma+1)/(gamma-1) w0^2 - w^2)/(2 gamma).                               */
+/* ------------------------------------------------------------------------- */
+
+static double becker_xi(const orc_problem *P, double w)
+{
+    double g = P->gamma, wL = 1.0, m0 = 1.0;
+    double wR = wL * ((g - 1.0) + 2.0 / (P->ex_M0 * P->ex_M0)) / (g + 1.0), w0 = sqrt(wL * wR);
+    double k = 2.0 * P->mu * g / ((g + 1.0) * m0 * P->Pr);
+    return k * (wL / (wL - wR) * log((wL - w) / (wL - w0)) - wR / (wL - wR) * log((w - wR) / (w0 - wR)));
+}
+
+/* Primitive (rho, u, p) of the exact solution at (x, t): xi(w) decreases from
+ * +inf (w -> w_R) to -inf (w -> w_L); bisection to the spacing of doubles. */
+static void becker_prim(const orc_problem *P, double x, double t, double *rho, double *u, double *p)
+{
+    double g = P->gamma, wL = 1.0, m0 = 1.0;
+    double wR = wL * ((g - 1.0) + 2.0 / (P->ex_M0 * P->ex_M0)) / (g + 1.0), w0 = sqrt(wL * wR);
+    double xi = x - P->ex_uinf * t, lo = wR, hi = wL;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (becker_xi(P, mid) > xi) lo = mid;
+        else hi = mid;
+    }
+    double w = 0.5 * (lo + hi);
+    double e = ((g + 1.0) / (g - 1.0) * w0 * w0 - w * w) / (2.0 * g);
+    *rho = m0 / w;
+    *u = P->ex_uinf + w;
+    *p = (g - 1.0) * (*rho) * e;
+}
+
+static void becker_cons(const orc_problem *P, double x, double t, double *U)
+{
+    double rho, u, p;
+    becker_prim(P, x, t, &rho, &u, &p);
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = p / (P->gamma - 1.0) + 0.5 * rho * u * u;
+}
+
+/* 1D sides of kind ORC_BC_EXACT: ghost point and ghost cells from the exact
+ * solution at time t (reading R15). */
+static void exact_ghosts(grid_t *g, double t)
+{
+    const orc_problem *P = g->P;
+    if (g->d != 1) return;
+    static const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
+                                 0.9061798459386640};
+    static const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                                 0.2369268850561891};
+    double h = g->h[0];
+    for (int side = 0; side < 2; ++side) {
+        if (P->bc[side] != ORC_BC_EXACT) continue;
+        double U[MAXC];
+        int a = side ? 2 * g->n[0] + 2 : -2;
+        becker_cons(P, P->lo1 + 0.5 * a * h, t, U);
+        lat_set(g, g->U, a, 0, U);
+        int c0 = side ? g->n[0] : -2;
+        for (int i = c0; i < c0 + 2; ++i) {
+            double A[MAXC] = {0, 0, 0, 0};
+            for (int q = 0; q < 5; ++q) {
+                becker_cons(P, P->lo1 + (i + 0.5 + 0.5 * gx[q]) * h, t, U);
+                for (int c = 0; c < g->nc; ++c) A[c] += 0.5 * gw[q] * U[c];
+            }
+            cell_set(g, i, 0, A);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Cell centres: Simpson inversion (Sec. 2.1 / Sec. 2.2) and the scaling     */
 /* limiter toward the cell average (Remark 3.1, reading R6).                 */
 /* ------------------------------------------------------------------------- */
@@ -866,6 +946,7 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
     int d = g->d, nc = g->nc;
     unpack(g, state);
     fill_ghosts(g);
+    exact_ghosts(g, P->time);
     centres(g);
     node_prims(g);
 
@@ -1029,6 +1110,8 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
 
 void orc_defaults(orc_problem *P)
 {
+    P->ex_M0 = 3.0;
+    P->ex_uinf = 0.2;
     P->limiter = ORC_LIM_S_PP;
     P->source = ORC_SRC_NONE;
     P->src_p0 = 100.0;

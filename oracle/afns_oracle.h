@@ -57,7 +57,11 @@ typedef struct {
     int source;         /* ORC_SRC_*: manufactured source term added to L */
     double src_p0;      /* p0 of the Taylor-Green source (Sec. 4: 100) */
     double time;        /* time of the state given to orc_residual / orc_step */
+    double ex_M0;       /* Becker shock (ORC_BC_EXACT sides): upstream Mach number M0 */
+    double ex_uinf;     /* Becker shock: translation velocity u_inf */
 } orc_problem;
+
+#define ORC_BC_EXACT 4  /* 1D: ghost cells and points from the exact Becker shock at the stage time */
 
 #define ORC_SRC_NONE 0
 #define ORC_SRC_TAYLOR_GREEN 1  /* energy source of the 2D manufactured Taylor-Green vortex (Sec. 4) */

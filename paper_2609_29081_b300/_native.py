@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("limiter", ctypes.c_int), ("c_s", ctypes.c_double),
                 ("cfl_c", ctypes.c_double), ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("source", ctypes.c_int), ("src_p0", ctypes.c_double)]
+                ("source", ctypes.c_int), ("src_p0", ctypes.c_double),
+                ("ex_M0", ctypes.c_double), ("ex_uinf", ctypes.c_double)]
 
 
 _lib = None
@@ -156,6 +157,8 @@ class Solver:
     def from_workload(cls, w, **kw):
         if getattr(w, "source", 0) and "source" not in kw:
             kw.update(source=w.source, src_p0=w.src_p0)
+        if workloads.BC_EXACT in tuple(w.bc) and "ex_M0" not in kw:
+            kw.update(ex_M0=w.ex_M0, ex_uinf=w.ex_uinf)
         return cls(w.dim, w.n, w.lo, w.hi, w.gamma, w.mu, w.Pr, w.bc, **kw)
 
     def _check(self, st):

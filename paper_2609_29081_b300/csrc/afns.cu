@@ -30,6 +30,10 @@ cudaError_t launch_dt1d_fp64(const Layout &L, const double *buf, double gamma, d
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_validate1d_fp64(const Layout &L, const double *buf, double gamma, int *flag, cudaStream_t st);
 cudaError_t launch_ghost1d_f32(const Layout &L, float *buf, cudaStream_t st);
+cudaError_t launch_exact_ghost1d_fp64(const Layout &L, double *buf, const Ctl *ctl, double ct, ExactParams ep,
+                                      cudaStream_t st);
+cudaError_t launch_exact_ghost1d_f32(const Layout &L, float *buf, const Ctl *ctl, double ct, ExactParams ep,
+                                     cudaStream_t st);
 cudaError_t launch_validate1d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st);
 cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st);
 cudaError_t launch_stage1d_mixed(const StageArgs &A, cudaStream_t st);
@@ -227,7 +231,9 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
     if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return *why = "need gamma > 1, mu >= 0, Pr > 0", AF_EINVAL;
     for (int l = 0; l < g->dim; ++l) {
         int a = bc->side[2 * l], b = bc->side[2 * l + 1];
-        if (a < 0 || a > 3 || b < 0 || b > 3) return *why = "unknown boundary kind", AF_EINVAL;
+        if (a < 0 || a > 4 || b < 0 || b > 4) return *why = "unknown boundary kind", AF_EINVAL;
+        if ((a == AF_BC_EXACT || b == AF_BC_EXACT) && g->dim != 1)
+            return *why = "exact boundary data are one-dimensional", AF_EINVAL;
         if ((a == AF_BC_PERIODIC) != (b == AF_BC_PERIODIC)) return *why = "periodic sides come in pairs", AF_EINVAL;
     }
     if (o->precision != AF_FP64 && o->precision != AF_MIXED) return *why = "unknown precision", AF_EINVAL;
@@ -258,6 +264,8 @@ af_status af_opts_default(int dim, af_opts *o)
     o->max_halvings = 30;
     o->source = AF_SRC_NONE;
     o->src_p0 = 100.0;
+    o->ex_M0 = 3.0;
+    o->ex_uinf = 0.2;
     return AF_OK;
 }
 
@@ -423,12 +431,19 @@ static void site_dims(const afns_ctx *c, int s, int *w, int *h)
 }
 
 // Kernel dispatch by dimension.
-static cudaError_t do_ghost(afns_ctx *c, void *buf)
+static cudaError_t do_ghost(afns_ctx *c, void *buf, double ct = 0.0)
 {
     if (c->dim == 1) {
         c->launches += 1;
-        if (c->mixed) return launch_ghost1d_f32(c->L, (float *)buf, c->st);
-        return launch_ghost1d_fp64(c->L, (double *)buf, c->st);
+        cudaError_t e = c->mixed ? launch_ghost1d_f32(c->L, (float *)buf, c->st)
+                                 : launch_ghost1d_fp64(c->L, (double *)buf, c->st);
+        if (e == cudaSuccess && (c->bc[0] == AF_BC_EXACT || c->bc[1] == AF_BC_EXACT)) {
+            c->launches += 1;
+            ExactParams ep{c->gamma, c->mu, c->Pr, c->opts.ex_M0, c->opts.ex_uinf};
+            e = c->mixed ? launch_exact_ghost1d_f32(c->L, (float *)buf, c->ctl, ct, ep, c->st)
+                         : launch_exact_ghost1d_fp64(c->L, (double *)buf, c->ctl, ct, ep, c->st);
+        }
+        return e;
     }
     c->launches += 2;
     if (c->mixed) return launch_ghost2d_f32(c->L, (float *)buf, c->st);
@@ -592,7 +607,7 @@ static StageArgs base_args(afns_ctx *c)
 // One fused stage: ghost fill of the input, then the stage kernel.
 static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &k, double *theta)
 {
-    cudaError_t e = do_ghost(c, in);
+    cudaError_t e = do_ghost(c, in, k.ct);
     if (e != cudaSuccess) return e;
     StageArgs A = base_args(c);
     A.uin = in;

@@ -77,6 +77,11 @@ struct Ctl {
     int err;          // a tile load of a stage kernel timed out (result invalid)
 };
 
+// Parameters of the exact moving viscous shock used as 1D boundary data.
+struct ExactParams {
+    double gamma, mu, Pr, M0, uinf;
+};
+
 // SSP-RK54 stage combination: out = a0 u0 + a1 uin + a2 aux + cl dt L(uin);
 // with acc: aux <- b2 aux + b1 uin + bl dt L(uin). Residual mode writes L itself.
 struct StageCoef {

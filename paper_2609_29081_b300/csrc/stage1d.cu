@@ -19,6 +19,20 @@ cudaError_t launch_ghost1d_f32(const Layout &L, float *buf, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t launch_exact_ghost1d_fp64(const Layout &L, double *buf, const Ctl *ctl, double ct, ExactParams ep,
+                                      cudaStream_t st)
+{
+    k_exact_ghost1d<double><<<1, 32, 0, st>>>(L, buf, ctl, ct, ep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_ghost1d_f32(const Layout &L, float *buf, const Ctl *ctl, double ct, ExactParams ep,
+                                     cudaStream_t st)
+{
+    k_exact_ghost1d<float><<<1, 32, 0, st>>>(L, buf, ctl, ct, ep);
+    return cudaGetLastError();
+}
+
 template <class R>
 static cudaError_t launch_stage1d_t(const StageArgs &A, cudaStream_t st)
 {

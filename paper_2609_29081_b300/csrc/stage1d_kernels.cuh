@@ -51,6 +51,69 @@ __global__ void k_ghost1d(Layout L, S *buf)
     }
 }
 
+// Exact moving viscous shock (Sec. 4, Becker's solution) with rho_L = w_L = m0 = 1:
+// w_R / w_L = ((gamma-1) + 2/M0^2)/(gamma+1), w0 = sqrt(w_L w_R), and the relative
+// velocity w(xi), xi = x - u_inf t, from
+// xi = 2 mu gamma/((gamma+1) m0 Pr) [w_L/(w_L-w_R) log((w_L-w)/(w_L-w0))
+//      - w_R/(w_L-w_R) log((w-w_R)/(w0-w_R))]  (decreasing in w: bisection);
+// rho = m0/w, u = u_inf + w, p = (gamma-1) rho e, e = ((gamma+1)/(gamma-1) w0^2 - w^2)/(2 gamma).
+__device__ inline void becker_cons(const ExactParams &P, double x, double t, double U[3])
+{
+    const double g = P.gamma, wL = 1.0, m0 = 1.0;
+    const double wR = wL * ((g - 1.0) + 2.0 / (P.M0 * P.M0)) / (g + 1.0), w0 = sqrt(wL * wR);
+    const double k = 2.0 * P.mu * g / ((g + 1.0) * m0 * P.Pr);
+    const double xi = x - P.uinf * t;
+    double lo = wR, hi = wL;
+    for (int it = 0; it < 200; ++it) {
+        const double w = 0.5 * (lo + hi);
+        if (w <= lo || w >= hi) break;
+        const double xw = k * (wL / (wL - wR) * log((wL - w) / (wL - w0)) - wR / (wL - wR) * log((w - wR) / (w0 - wR)));
+        if (xw > xi) lo = w;
+        else hi = w;
+    }
+    const double w = 0.5 * (lo + hi);
+    const double e = ((g + 1.0) / (g - 1.0) * w0 * w0 - w * w) / (2.0 * g);
+    const double rho = m0 / w, u = P.uinf + w;
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = (g - 1.0) * rho * e / (g - 1.0) + 0.5 * rho * u * u;
+}
+
+// Sides of kind AF_BC_EXACT: the ghost point and the two ghost cells (5-point
+// Gauss-Legendre averages) from the exact solution at the stage's time
+// t + ct dt. One thread per (side, ghost item).
+template <class S>
+__global__ void k_exact_ghost1d(Layout L, S *buf, const Ctl *ctl, double ct, ExactParams P)
+{
+    const int t = threadIdx.x;
+    if (t >= 6) return;
+    const int side = t / 3, item = t % 3;
+    if (L.bc[side] != 4) return;
+    const double time = ctl->t + ct * ctl->dt, h = L.dx;
+    double U[3];
+    if (item == 0) {
+        const int i = side ? L.n1 + 1 : -1;   // ghost point index (lattice 2i)
+        becker_cons(P, L.lo[0] + i * h, time, U);
+        for (int c = 0; c < 3; ++c) buf[plane_of(L, 1, c) + off1(i)] = (S)U[c];
+    } else {
+        const int i = side ? L.n1 + item - 1 : item - 3;   // ghost cells -2, -1 / n, n+1
+        const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
+                              0.9061798459386640};
+        const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
+                              0.2369268850561891};
+        double A[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < 5; ++q) {
+            becker_cons(P, L.lo[0] + (i + 0.5 + 0.5 * gx[q]) * h, time, U);
+            for (int c = 0; c < 3; ++c) A[c] += 0.5 * gw[q] * U[c];
+        }
+        for (int c = 0; c < 3; ++c) {
+            const S hi = (S)A[c];
+            buf[plane_of(L, 0, c) + off1(i)] = hi;
+            if (L.comp) buf[comp_plane(L, c) + off1(i)] = (S)(A[c] - (double)hi);
+        }
+    }
+}
+
 __device__ __forceinline__ bool admissible1(const double *U, double gm1)
 {
     if (!(U[0] > 0.0)) return false;

@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BC_PERIODIC, BC_WALL, BC_SYMMETRY, BC_TRANSMISSIVE = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_SYMMETRY, BC_TRANSMISSIVE, BC_EXACT = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -35,6 +35,8 @@ class Workload:
     steps: int = 0          # nominal step count of the configuration (0: run to t_end)
     source: int = 0         # manufactured source (0: none, 1: Taylor-Green energy source)
     src_p0: float = 100.0   # p0 of the Taylor-Green source
+    ex_M0: float = 3.0      # BC_EXACT: upstream Mach number of the viscous shock
+    ex_uinf: float = 0.2    # BC_EXACT: translation velocity of the viscous shock
 
     def __post_init__(self):
         periodize(self.state, self.dim, self.n, self.bc)
@@ -157,6 +159,82 @@ def shock_tube_1d(n=4096, mu=1e-3, Pr=0.72, gamma=1.4, t_end=0.2):
     s = project(1, (n,), lo, hi, gamma, f)
     return Workload("shock_tube_1d_N%d" % n, 1, (n,), lo, hi, gamma, mu, Pr,
                     (BC_TRANSMISSIVE,) * 4, t_end, s)
+
+
+def becker_prim(x, t, M0=3.0, mu=1e-2, Pr=0.75, gamma=1.4, u_inf=0.2):
+    """Exact moving viscous shock (Sec. 4, Becker's solution) with rho_L = w_L =
+    m0 = 1: (rho, u, p) at positions x (array) and time t. The relative velocity
+    w(xi), xi = x - u_inf t, is found by bisection of the printed implicit law."""
+    g = gamma
+    wL, m0 = 1.0, 1.0
+    wR = wL * ((g - 1.0) + 2.0 / M0 ** 2) / (g + 1.0)
+    w0 = np.sqrt(wL * wR)
+    k = 2.0 * mu * g / ((g + 1.0) * m0 * Pr)
+
+    def xi_of(w):
+        return k * (wL / (wL - wR) * np.log((wL - w) / (wL - w0)) - wR / (wL - wR) * np.log((w - wR) / (w0 - wR)))
+
+    xi = np.asarray(x, dtype=float) - u_inf * t
+    lo, hi = np.full_like(xi, wR), np.full_like(xi, wL)
+    with np.errstate(divide="ignore"):
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            up = xi_of(mid) > xi
+            lo, hi = np.where(up, mid, lo), np.where(up, hi, mid)
+    w = 0.5 * (lo + hi)
+    e = ((g + 1.0) / (g - 1.0) * w0 * w0 - w * w) / (2.0 * g)
+    rho = m0 / w
+    return rho, u_inf + w, (g - 1.0) * rho * e
+
+
+def becker_1d(n=80, t=0.0, M0=3.0, mu=1e-2, Pr=0.75, gamma=1.4, u_inf=0.2, t_end=0.2, lo=-1.0, hi=1.5):
+    """1D viscous shock wave (Sec. 4) on [lo, hi] (default [-1, 1.5]): the exact
+    Becker profile at time t (shock at x = u_inf t), both ends prescribed from the
+    exact solution (BC_EXACT). M0 = 3, mu = 1e-2 is the paper's unlimited accuracy
+    case; M0 = 20, mu = 1e-3 the limited one."""
+    lo, hi = (float(lo),), (float(hi),)
+
+    def f(x):
+        rho, u, p = becker_prim(x, t, M0, mu, Pr, gamma, u_inf)
+        return rho, [u], p
+
+    s = project(1, (n,), lo, hi, gamma, f)
+    return Workload("becker_1d_N%d_M%g" % (n, M0), 1, (n,), lo, hi, gamma, mu, Pr, (BC_EXACT,) * 4, t_end, s,
+                    ex_M0=M0, ex_uinf=u_inf)
+
+
+def leblanc_1d(n=800, mu=0.0, Pr=0.75, gamma=5.0 / 3.0, t_end=0.4):
+    """1D LeBlanc problem (Sec. 4 example) on [-0.5, 0.5], outflow ends:
+    (rho, u, p) = (1, 0, 6.666667e-2) for x < -0.2, (1e-2, 0, 6.666667e-11)
+    otherwise; gamma = 5/3 (p = (gamma-1) rho e with e = 0.1 and 1e-7)."""
+    lo, hi = (-0.5,), (0.5,)
+
+    def f(x):
+        left = x < -0.2
+        return (np.where(left, 1.0, 1e-2), [np.zeros_like(x)], np.where(left, 6.666667e-2, 6.666667e-11))
+
+    s = project(1, (n,), lo, hi, gamma, f)
+    return Workload("leblanc_1d_N%d_mu%g" % (n, mu), 1, (n,), lo, hi, gamma, mu, Pr,
+                    (BC_TRANSMISSIVE,) * 4, t_end, s)
+
+
+def stokes_first_problem(n=100, mu=1e-2, gamma=1.4, t_end=1.0, ny=4):
+    """First problem of Stokes (Sec. 4 example): a tangential velocity jump that
+    diffuses, on [-0.5, 0.5] with outflow ends; (rho, u, v, p) = (1, 0, -0.1,
+    1/gamma) for x < 0, (1, 0, 0.1, 1/gamma) otherwise; kappa = 0. The solution
+    depends on x only, so it runs as a 2D strip of n x ny cells, periodic in y.
+    kappa = 0 is obtained through Pr = 1e30 (kappa = gamma mu / ((gamma-1) Pr),
+    1e-30 times the viscosity; the heat-conduction term of the CFL bound vanishes
+    likewise). In the incompressible limit v = 0.1 erf(x / (2 sqrt(mu t)))."""
+    h = 1.0 / n
+    lo, hi = (-0.5, 0.0), (0.5, ny * h)
+
+    def f(x, y):
+        return np.ones_like(x), [np.zeros_like(x), np.where(x < 0.0, -0.1, 0.1)], np.full_like(x, 1.0 / gamma)
+
+    st = project(2, (n, ny), lo, hi, gamma, f)
+    return Workload("stokes_first_%dx%d_mu%g" % (n, ny, mu), 2, (n, ny), lo, hi, gamma, mu, 1e30,
+                    (BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_PERIODIC, BC_PERIODIC), t_end, st)
 
 
 def fourier_modes(seed, nmodes=8, amp=0.05, kmax=4):

@@ -65,3 +65,11 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     b.side[1] = 0
     st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
     assert st == N.AF_EINVAL
+    # exact boundary data (AF_BC_EXACT = 4) exist only in 1D
+    g.n[0] = 64
+    b.side[0] = b.side[1] = 4
+    b.side[2] = b.side[3] = 2
+    st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.75, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
+    assert st == N.AF_EINVAL and not ctx.value
+    assert L.af_opts_default(1, ctypes.byref(o)) == N.AF_OK
+    assert o.ex_M0 == 3.0 and o.ex_uinf == 0.2 and o.cfl_v == pytest.approx(0.33)
