@@ -52,9 +52,13 @@ typedef enum {
     AF_BC_WALL = 1,        /* no-slip adiabatic wall */
     AF_BC_SYMMETRY = 2,    /* slip wall / symmetry plane */
     AF_BC_TRANSMISSIVE = 3, /* zero-gradient outflow */
-    AF_BC_EXACT = 4         /* 1D: ghost data from the exact moving viscous shock of Sec. 4
+    AF_BC_EXACT = 4,        /* 1D: ghost data from the exact moving viscous shock of Sec. 4
                                (Becker's solution, parameters ex_M0 / ex_uinf of af_opts)
                                at each stage's time */
+    AF_BC_MOVING_WALL = 5   /* 2D: no-slip adiabatic wall moving tangentially with speed
+                               af_bc.wall_speed[side] (the lid of the Sec. 4 cavity): ghost
+                               velocities mirror about the wall velocity, wall point values
+                               take it after every stage */
 } af_bc_kind;
 
 typedef enum { AF_FP64 = 0, AF_MIXED = 1 } af_precision;
@@ -76,6 +80,8 @@ typedef struct {
 
 typedef struct {
     int side[4];    /* af_bc_kind of x-lo, x-hi, y-lo, y-hi; a periodic side needs a periodic partner */
+    double wall_speed[4]; /* AF_BC_MOVING_WALL sides: tangential wall velocity (the x-velocity of
+                             a y-side, the y-velocity of an x-side); ignored on other kinds */
 } af_bc;
 
 typedef struct {

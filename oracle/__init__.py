@@ -42,7 +42,8 @@ class Problem(ctypes.Structure):
                 ("c_s", ctypes.c_double), ("cfl_c", ctypes.c_double),
                 ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
                 ("source", ctypes.c_int), ("src_p0", ctypes.c_double), ("time", ctypes.c_double),
-                ("ex_M0", ctypes.c_double), ("ex_uinf", ctypes.c_double)]
+                ("ex_M0", ctypes.c_double), ("ex_uinf", ctypes.c_double),
+                ("wall_speed", ctypes.c_double * 4)]
 
 
 _lib = None
@@ -102,7 +103,11 @@ def problem(dim, n1, n2=1, lo=(0.0, 0.0), hi=(1.0, 1.0), gamma=1.4, mu=0.0, Pr=0
     lib().orc_defaults(ctypes.byref(P))
     P.limiter = limiter
     for k, v in kw.items():
-        setattr(P, k, v)
+        if k == "wall_speed":
+            for i in range(4):
+                P.wall_speed[i] = v[i]
+        else:
+            setattr(P, k, v)
     return P
 
 

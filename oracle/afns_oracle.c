@@ -467,10 +467,27 @@ static int image(const grid_t *g, int l, int a, double *sgn)
         return a;
     int kind = P->bc[side];
     if (kind == ORC_BC_PERIODIC) return ((a % n2x) + n2x) % n2x;
-    if (kind == ORC_BC_WALL)
+    if (kind == ORC_BC_WALL || kind == ORC_BC_MOVING)
         for (int k = 0; k < g->d; ++k) sgn[1 + k] = -1.0;
     if (kind == ORC_BC_SYMMETRY) sgn[1 + l] = -1.0;
     return side & 1 ? 2 * n2x - a : -a;
+}
+
+/* Reading R17: a moving no-slip wall mirrors the velocity about the wall velocity,
+ * u_ghost = 2 U_w - u_image (tangential), -u_image (normal), with the internal
+ * energy of the image kept; v holds the image state with both momenta already
+ * negated by image(). Applied to point values and cell averages alike. */
+static void moving_wall_ghost(const grid_t *g, int l, int a, double *v)
+{
+    const orc_problem *P = g->P;
+    if (g->d != 2 || (a >= 0 && a <= 2 * g->n[l])) return;
+    int side = a < 0 ? 2 * l : 2 * l + 1;
+    if (P->bc[side] != ORC_BC_MOVING) return;
+    int t = 1 + (1 - l);  /* tangential momentum component */
+    double m2_old = v[1] * v[1] + v[2] * v[2];
+    v[t] += 2.0 * v[0] * P->wall_speed[side];
+    double m2_new = v[1] * v[1] + v[2] * v[2];
+    v[3] += (m2_new - m2_old) / (2.0 * v[0]);
 }
 
 static void fill_ghosts(grid_t *g)
@@ -498,6 +515,7 @@ static void fill_ghosts(grid_t *g)
                 int s0 = l == 0 ? src : am, s1 = l == 0 ? am : src;
                 lat_get(g, g->U, s0, s1, v);
                 for (int c = 0; c < g->nc; ++c) v[c] *= sg[c];
+                moving_wall_ghost(g, l, al, v);
                 lat_set(g, g->U, a0, a1, v);
             }
         /* cells: ghost i in {-2,-1} and {n, n+1}; image through the lattice centre 2i+1 */
@@ -511,6 +529,7 @@ static void fill_ghosts(grid_t *g)
                 int s0 = l == 0 ? src : im, s1 = l == 0 ? im : src;
                 cell_get(g, s0, s1, v);
                 for (int c = 0; c < g->nc; ++c) v[c] *= sg[c];
+                moving_wall_ghost(g, l, 2 * il + 1, v);
                 cell_set(g, i0, i1, v);
             }
     }
@@ -1112,6 +1131,7 @@ void orc_defaults(orc_problem *P)
 {
     P->ex_M0 = 3.0;
     P->ex_uinf = 0.2;
+    for (int k = 0; k < 4; ++k) P->wall_speed[k] = 0.0;
     P->limiter = ORC_LIM_S_PP;
     P->source = ORC_SRC_NONE;
     P->src_p0 = 100.0;
@@ -1142,14 +1162,16 @@ double orc_dt_max(const orc_problem *P, const double *state)
     return 1.0 / (m1 + m2);
 }
 
-/* R9: wall point values get zero (normal) momentum, internal energy kept. */
+/* R9: wall point values get zero (normal) momentum, internal energy kept; R17:
+ * on a moving wall the tangential momentum is rho U_w (sides in the order x-lo,
+ * x-hi, y-lo, y-hi, so a corner takes the velocity of its y-side). */
 static void wall_fix(const orc_problem *P, double *s)
 {
     int d = P->dim, nc = d + 2;
     int n[2] = {P->n1, d == 2 ? P->n2 : 0};
     for (int side = 0; side < 2 * d; ++side) {
         int kind = P->bc[side];
-        if (kind != ORC_BC_WALL && kind != ORC_BC_SYMMETRY) continue;
+        if (kind != ORC_BC_WALL && kind != ORC_BC_SYMMETRY && kind != ORC_BC_MOVING) continue;
         int l = side / 2, m = 1 - l;
         int al = (side & 1) ? 2 * n[l] : 0;
         int mhi = d == 2 ? 2 * n[m] : 0;
@@ -1165,7 +1187,8 @@ static void wall_fix(const orc_problem *P, double *s)
             double ke_old = 0.0, ke_new = 0.0;
             for (int k = 0; k < d; ++k) ke_old += U[1 + k] * U[1 + k];
             for (int k = 0; k < d; ++k)
-                if (kind == ORC_BC_WALL || k == l) U[1 + k] = 0.0;
+                if (kind != ORC_BC_SYMMETRY || k == l) U[1 + k] = 0.0;
+            if (kind == ORC_BC_MOVING && d == 2) U[1 + m] = U[0] * P->wall_speed[side];
             for (int k = 0; k < d; ++k) ke_new += U[1 + k] * U[1 + k];
             U[d + 1] -= (ke_old - ke_new) / (2.0 * U[0]);
             for (int c = 0; c < nc; ++c) s[o[c]] = U[c];

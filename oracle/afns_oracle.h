@@ -59,9 +59,12 @@ typedef struct {
     double time;        /* time of the state given to orc_residual / orc_step */
     double ex_M0;       /* Becker shock (ORC_BC_EXACT sides): upstream Mach number M0 */
     double ex_uinf;     /* Becker shock: translation velocity u_inf */
+    double wall_speed[4]; /* ORC_BC_MOVING sides: tangential wall velocity (x-velocity of a
+                             y-side, y-velocity of an x-side) */
 } orc_problem;
 
 #define ORC_BC_EXACT 4  /* 1D: ghost cells and points from the exact Becker shock at the stage time */
+#define ORC_BC_MOVING 5 /* 2D: no-slip adiabatic wall moving tangentially with wall_speed[side] */
 
 #define ORC_SRC_NONE 0
 #define ORC_SRC_TAYLOR_GREEN 1  /* energy source of the 2D manufactured Taylor-Green vortex (Sec. 4) */

@@ -39,7 +39,7 @@ class Grid(ctypes.Structure):
 
 
 class BC(ctypes.Structure):
-    _fields_ = [("side", ctypes.c_int * 4)]
+    _fields_ = [("side", ctypes.c_int * 4), ("wall_speed", ctypes.c_double * 4)]
 
 
 class Opts(ctypes.Structure):
@@ -119,7 +119,7 @@ class Solver:
     """One AF-NS problem on cuda:0 (device memory owned by a torch tensor)."""
 
     def __init__(self, dim, n, lo, hi, gamma, mu, Pr, bc, precision=FP64, limiter=LIM_S_PP, stream=None,
-                 **opts):
+                 wall_speed=(0.0, 0.0, 0.0, 0.0), **opts):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libafns needs a CUDA GPU; none is available")
@@ -135,6 +135,7 @@ class Solver:
         b = BC()
         for k in range(4):
             b.side[k] = bc[k] if k < len(bc) else 0
+            b.wall_speed[k] = wall_speed[k]
         self.opts = default_opts(dim, precision, limiter, **opts)
         nbytes = ctypes.c_size_t(0)
         self._check(self.lib.af_workspace_bytes(ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(nbytes)))
@@ -159,6 +160,8 @@ class Solver:
             kw.update(source=w.source, src_p0=w.src_p0)
         if workloads.BC_EXACT in tuple(w.bc) and "ex_M0" not in kw:
             kw.update(ex_M0=w.ex_M0, ex_uinf=w.ex_uinf)
+        if "wall_speed" not in kw:
+            kw["wall_speed"] = tuple(w.wall_speed)
         return cls(w.dim, w.n, w.lo, w.hi, w.gamma, w.mu, w.Pr, w.bc, **kw)
 
     def _check(self, st):
@@ -322,6 +325,7 @@ class BatchSolver:
             grids[k].hi[0], grids[k].hi[1] = w.hi
             for s in range(4):
                 bcs[k].side[s] = w.bc[s]
+                bcs[k].wall_speed[s] = w.wall_speed[s]
         self.opts = default_opts(2, precision, limiter, **opts)
         nb = ctypes.c_size_t(0)
         self._check(self.lib.afb_workspace_bytes(n, ctypes.cast(grids, ctypes.c_void_p),

@@ -135,7 +135,7 @@ static af_status cuda_check(afns_ctx *c, cudaError_t e, const char *where)
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static void make_layout(const af_grid *g, const int *bc, Layout *L)
+static void make_layout(const af_grid *g, const int *bc, Layout *L, const double *wall_speed = nullptr)
 {
     std::memset(L, 0, sizeof(*L));
     L->dim = g->dim;
@@ -148,6 +148,7 @@ static void make_layout(const af_grid *g, const int *bc, Layout *L)
     long long pl = (long long)L->pitch * L->rows;
     L->plane = (pl + 63) / 64 * 64;
     for (int k = 0; k < 4; ++k) L->bc[k] = bc[k];
+    for (int k = 0; k < 4; ++k) L->wall_speed[k] = wall_speed && bc[k] == AF_BC_MOVING_WALL ? wall_speed[k] : 0.0;
     L->dx = (g->hi[0] - g->lo[0]) / g->n[0];
     L->dy = g->dim == 2 ? (g->hi[1] - g->lo[1]) / g->n[1] : 1.0;
     L->lo[0] = g->lo[0];
@@ -231,9 +232,14 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
     if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return *why = "need gamma > 1, mu >= 0, Pr > 0", AF_EINVAL;
     for (int l = 0; l < g->dim; ++l) {
         int a = bc->side[2 * l], b = bc->side[2 * l + 1];
-        if (a < 0 || a > 4 || b < 0 || b > 4) return *why = "unknown boundary kind", AF_EINVAL;
+        if (a < 0 || a > 5 || b < 0 || b > 5) return *why = "unknown boundary kind", AF_EINVAL;
         if ((a == AF_BC_EXACT || b == AF_BC_EXACT) && g->dim != 1)
             return *why = "exact boundary data are one-dimensional", AF_EINVAL;
+        if ((a == AF_BC_MOVING_WALL || b == AF_BC_MOVING_WALL) && g->dim != 2)
+            return *why = "moving walls are two-dimensional", AF_EINVAL;
+        for (int s = 2 * l; s < 2 * l + 2; ++s)
+            if (bc->side[s] == AF_BC_MOVING_WALL && !std::isfinite(bc->wall_speed[s]))
+                return *why = "wall speed must be finite", AF_EINVAL;
         if ((a == AF_BC_PERIODIC) != (b == AF_BC_PERIODIC)) return *why = "periodic sides come in pairs", AF_EINVAL;
     }
     if (o->precision != AF_FP64 && o->precision != AF_MIXED) return *why = "unknown precision", AF_EINVAL;
@@ -313,7 +319,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     for (int k = 0; k < 4; ++k) c->bc[k] = grid->dim == 2 || k < 2 ? bc->side[k] : AF_BC_PERIODIC;
     c->opts = *opts;
     c->st = (cudaStream_t)cuda_stream;
-    make_layout(grid, c->bc, &c->L);
+    make_layout(grid, c->bc, &c->L, bc->wall_speed);
     WsPlan p = plan_ws(c->L, opts);
     if (workspace) {
         if (workspace_bytes < p.total || ((uintptr_t)workspace & 255)) {
@@ -645,7 +651,8 @@ static void harvest_events(afns_ctx *c)
 static cudaError_t run_rk(afns_ctx *c)
 {
     bool walls = false;
-    for (int k = 0; k < 4; ++k) walls |= c->bc[k] == AF_BC_WALL || c->bc[k] == AF_BC_SYMMETRY;
+    for (int k = 0; k < 4; ++k)
+        walls |= c->bc[k] == AF_BC_WALL || c->bc[k] == AF_BC_SYMMETRY || c->bc[k] == AF_BC_MOVING_WALL;
     StageCoef k{};
     k.wall_fix = walls;
     // time of each stage input as a fraction of dt: c(u(s+1)) = a_ss c(u(s)) + b_s

@@ -14,7 +14,7 @@
 
 namespace afns {
 
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_SYMMETRY = 2, BC_TRANSMISSIVE = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_SYMMETRY = 2, BC_TRANSMISSIVE = 3, BC_EXACT = 4, BC_MOVING = 5 };
 enum { LIM_NONE = 0, LIM_PP = 1, LIM_S_PP = 2 };
 
 struct Layout {
@@ -27,6 +27,7 @@ struct Layout {
     int nsite;      // 4 in 2D, 2 in 1D
     int comp;       // compensation planes present (mixed precision)
     int bc[4];
+    double wall_speed[4];  // tangential velocity of BC_MOVING sides
     double lo[2];   // domain origin (x, y)
     double dx, dy;
     // reciprocal stencil factors per direction, set on the host by layout_finish
@@ -127,9 +128,25 @@ __host__ __device__ __forceinline__ int ghost_image(int i, int n, bool pt, int k
 __host__ __device__ __forceinline__ double mirror_sign(int kind, int l, int c, int dim)
 {
     if (c < 1 || c > dim) return 1.0;
-    if (kind == BC_WALL) return -1.0;
+    if (kind == BC_WALL || kind == BC_MOVING) return -1.0;
     if (kind == BC_SYMMETRY && c - 1 == l) return -1.0;
     return 1.0;
+}
+
+// Ghost value across a moving no-slip wall: the mirrored state v (both momenta
+// already negated) gets its tangential velocity shifted by 2 U_w, i.e. the ghost
+// velocity is 2 U_w - u_image, with the internal energy of the image kept.
+template <class S>
+__device__ __forceinline__ void moving_wall_ghost(const Layout &L, int side, S v[4])
+{
+    if (L.bc[side] != BC_MOVING) return;
+    const int t = 1 + (1 - (side >> 1));
+    const double r = v[0], m1 = v[1], m2 = v[2];
+    double w[3] = {0.0, m1, m2};
+    w[t] += 2.0 * r * L.wall_speed[side];
+    const double m2_old = m1 * m1 + m2 * m2, m2_new = w[1] * w[1] + w[2] * w[2];
+    v[t] = (S)w[t];
+    v[3] = (S)((double)v[3] + (m2_new - m2_old) / (2.0 * r));
 }
 
 // Theta of Sec. 3.3 (limiter blending toward the low-order value).

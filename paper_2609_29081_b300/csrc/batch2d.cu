@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -162,10 +163,13 @@ __global__ void k_batch_ghost(BatchProb *probs, int in_idx, int pass)
         }
         if (side < 0) continue;
         int kind = L.bc[2 * l + side];
+        S v[4];
         for (int c = 0; c < 4; ++c) {
-            S v = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
-            buf[plane_of(L, site, c) + cell_off(L, i, j)] = mirror_sign(kind, l, c, 2) < 0 ? -v : v;
+            v[c] = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
+            if (mirror_sign(kind, l, c, 2) < 0) v[c] = -v[c];
         }
+        moving_wall_ghost(L, 2 * l + side, v);
+        for (int c = 0; c < 4; ++c) buf[plane_of(L, site, c) + cell_off(L, i, j)] = v[c];
     }
 }
 
@@ -511,6 +515,11 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
         if (!(gamma[p] > 1.0) || !(mu[p] >= 0.0) || !(Pr[p] > 0.0)) return AF_EINVAL;
         for (int l = 0; l < 2; ++l)
             if ((bcs[p].side[2 * l] == AF_BC_PERIODIC) != (bcs[p].side[2 * l + 1] == AF_BC_PERIODIC)) return AF_EINVAL;
+        for (int k = 0; k < 4; ++k) {
+            const int kind = bcs[p].side[k];
+            if (kind < 0 || kind > AF_BC_MOVING_WALL || kind == AF_BC_EXACT) return AF_EINVAL;
+            if (kind == AF_BC_MOVING_WALL && !std::isfinite(bcs[p].wall_speed[k])) return AF_EINVAL;
+        }
     }
     afb_ctx *c = new (std::nothrow) afb_ctx();
     if (!c) return AF_ENOMEM;
@@ -551,6 +560,7 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
         L.plane = ((long long)L.pitch * L.rows + 63) / 64 * 64;
         L.comp = c->mixed ? 1 : 0;
         for (int k = 0; k < 4; ++k) L.bc[k] = bcs[p].side[k];
+        for (int k = 0; k < 4; ++k) L.wall_speed[k] = bcs[p].side[k] == AF_BC_MOVING_WALL ? bcs[p].wall_speed[k] : 0.0;
         L.dx = (g.hi[0] - g.lo[0]) / g.n[0];
         L.dy = (g.hi[1] - g.lo[1]) / g.n[1];
         L.lo[0] = g.lo[0];

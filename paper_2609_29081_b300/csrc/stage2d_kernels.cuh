@@ -42,11 +42,13 @@ __global__ void k_ghost2d(Layout L, S *buf, int pass)
         }
         if (side < 0) continue;
         int kind = L.bc[2 * l + side];
+        S v[4];
         for (int c = 0; c < 4; ++c) {
-            double sg = mirror_sign(kind, l, c, 2);
-            S v = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
-            buf[plane_of(L, site, c) + cell_off(L, i, j)] = sg < 0 ? -v : v;
+            v[c] = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
+            if (mirror_sign(kind, l, c, 2) < 0) v[c] = -v[c];
         }
+        moving_wall_ghost(L, 2 * l + side, v);
+        for (int c = 0; c < 4; ++c) buf[plane_of(L, site, c) + cell_off(L, i, j)] = v[c];
     }
 }
 
@@ -649,16 +651,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 if (A.k.acc) ((S *)A.aux)[po0 + c * L.plane] = tc.b2 * g2[c] + tc.b1 * U[c] + tc.bldt * res[c];
             }
             if (A.k.wall_fix) {
-                // wall point values: zero (normal) momentum, internal energy kept
+                // wall point values: zero (normal) momentum, internal energy kept;
+                // a moving wall sets the tangential momentum to rho U_w (sides in
+                // order, so a corner takes the velocity of its y-side)
                 for (int side = 0; side < 4; ++side) {
                     const int kind = L.bc[side];
-                    if (kind != BC_WALL && kind != BC_SYMMETRY) continue;
+                    if (kind != BC_WALL && kind != BC_SYMMETRY && kind != BC_MOVING) continue;
                     const int l = side >> 1;
                     const int pos = l == 0 ? a : b, lim = (side & 1) ? 2 * (l == 0 ? L.n1 : L.n2) : 0;
                     if (pos != lim) continue;
                     S ke0 = o[1] * o[1] + o[2] * o[2];
-                    if (kind == BC_WALL || l == 0) o[1] = S(0);
-                    if (kind == BC_WALL || l == 1) o[2] = S(0);
+                    if (kind != BC_SYMMETRY || l == 0) o[1] = S(0);
+                    if (kind != BC_SYMMETRY || l == 1) o[2] = S(0);
+                    if (kind == BC_MOVING) o[2 - l] = (S)((double)o[0] * L.wall_speed[side]);
                     S ke1 = o[1] * o[1] + o[2] * o[2];
                     o[3] -= (ke0 - ke1) / (S(2) * o[0]);
                 }

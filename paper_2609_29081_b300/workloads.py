@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-BC_PERIODIC, BC_WALL, BC_SYMMETRY, BC_TRANSMISSIVE, BC_EXACT = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_WALL, BC_SYMMETRY, BC_TRANSMISSIVE, BC_EXACT, BC_MOVING = 0, 1, 2, 3, 4, 5
 
 
 @dataclass
@@ -37,6 +37,7 @@ class Workload:
     src_p0: float = 100.0   # p0 of the Taylor-Green source
     ex_M0: float = 3.0      # BC_EXACT: upstream Mach number of the viscous shock
     ex_uinf: float = 0.2    # BC_EXACT: translation velocity of the viscous shock
+    wall_speed: tuple = (0.0, 0.0, 0.0, 0.0)  # BC_MOVING sides: tangential wall velocity
 
     def __post_init__(self):
         periodize(self.state, self.dim, self.n, self.bc)
@@ -289,6 +290,72 @@ def taylor_green_2d(n=80, t=0.0, mu=1e-5, Pr=1.0, p0=100.0, gamma=1.4, t_end=0.2
     st = project(2, nn, lo, hi, gamma, f)
     return Workload("taylor_green_2d_%dx%d_t%g" % (nn[0], nn[1], t), 2, nn, lo, hi, gamma, mu, Pr,
                     (BC_PERIODIC,) * 4, t_end, st, 0, SRC_TAYLOR_GREEN, p0)
+
+
+def couette_2d(n=16, U=0.5, mu=1e-2, Pr=0.72, gamma=1.4, p0=1.0, t_end=0.1):
+    """Plane Couette flow on [0,1]^2, periodic in x, a no-slip wall at y = 0 and a
+    wall moving with speed U in x at y = 1: rho = 1, u = U y, v = 0, p = p0. The
+    momentum equations are steady for this field; the energy grows at the
+    viscous-heating rate mu U^2."""
+    lo, hi = (0.0, 0.0), (1.0, 1.0)
+
+    def f(x, y):
+        return np.ones_like(x), [U * y, np.zeros_like(x)], np.full_like(x, p0)
+
+    nn = (n, n) if np.isscalar(n) else tuple(n)
+    st = project(2, nn, lo, hi, gamma, f)
+    return Workload("couette_2d_%dx%d" % nn, 2, nn, lo, hi, gamma, mu, Pr,
+                    (BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_MOVING), t_end, st, wall_speed=(0.0, 0.0, 0.0, U))
+
+
+def moving_plate_2d(n=100, U=0.1, mu=1e-2, gamma=1.4, t_end=1.0, nx=4):
+    """Impulsively started plate (Rayleigh's problem): fluid at rest over y in
+    [0, 1] (rho = 1, p = 1/gamma), the wall at y = 0 set moving with speed U in x
+    at t = 0, outflow at y = 1; run as a strip of nx x n cells periodic in x.
+    Incompressible limit: u = U erfc(y / (2 sqrt(mu t))). kappa = 0 through
+    Pr = 1e30 as in the first problem of Stokes."""
+    h = 1.0 / n
+    lo, hi = (0.0, 0.0), (nx * h, 1.0)
+
+    def f(x, y):
+        return np.ones_like(x), [np.zeros_like(x), np.zeros_like(x)], np.full_like(x, 1.0 / gamma)
+
+    st = project(2, (nx, n), lo, hi, gamma, f)
+    return Workload("moving_plate_%dx%d_mu%g" % (nx, n, mu), 2, (nx, n), lo, hi, gamma, mu, 1e30,
+                    (BC_PERIODIC, BC_PERIODIC, BC_MOVING, BC_TRANSMISSIVE), t_end, st,
+                    wall_speed=(0.0, 0.0, U, 0.0))
+
+
+def lid_driven_cavity(n=128, Re=100.0, Pr=0.72, gamma=1.4, t_end=40.0):
+    """Lid-driven cavity (Sec. 4) on [0,1]^2: rho = 1, u = v = 0, p = 1e4/gamma
+    (Mach 0.01 for the unit lid speed), no-slip adiabatic walls, the top one
+    moving with velocity (1, 0); mu = 1/Re. The paper gives no Prandtl number
+    for this case: 0.72 is taken."""
+    lo, hi = (0.0, 0.0), (1.0, 1.0)
+
+    def f(x, y):
+        return np.ones_like(x), [np.zeros_like(x), np.zeros_like(x)], np.full_like(x, 1e4 / gamma)
+
+    nn = (n, n) if np.isscalar(n) else tuple(n)
+    st = project(2, nn, lo, hi, gamma, f)
+    return Workload("lid_cavity_%dx%d_Re%g" % (nn[0], nn[1], Re), 2, nn, lo, hi, gamma, 1.0 / Re, Pr,
+                    (BC_WALL, BC_WALL, BC_WALL, BC_MOVING), t_end, st, wall_speed=(0.0, 0.0, 0.0, 1.0))
+
+
+def double_shear_layer(n=200, mu=2e-4, Pr=0.72, gamma=1.4, t_end=1.8):
+    """Double shear layer (Sec. 4) on the periodic unit square: rho = 1,
+    p = 1e4/gamma, u = tanh(30 (y - 1/4)) for y <= 1/2 and tanh(30 (3/4 - y))
+    above, v = 0.05 sin(2 pi x); mu = 2e-4 (Re 1e4, Mach 0.01). No Prandtl number
+    is given for this case: 0.72 is taken."""
+    lo, hi = (0.0, 0.0), (1.0, 1.0)
+
+    def f(x, y):
+        u = np.where(y <= 0.5, np.tanh(30.0 * (y - 0.25)), np.tanh(30.0 * (0.75 - y)))
+        return np.ones_like(x), [u, 0.05 * np.sin(2 * np.pi * x)], np.full_like(x, 1e4 / gamma)
+
+    nn = (n, n) if np.isscalar(n) else tuple(n)
+    st = project(2, nn, lo, hi, gamma, f)
+    return Workload("double_shear_layer_%dx%d" % nn, 2, nn, lo, hi, gamma, mu, Pr, (BC_PERIODIC,) * 4, t_end, st)
 
 
 def shock_tube_2d(n=(2000, 1000), mu=1e-3, Pr=0.73, gamma=1.4, t_end=1.0):

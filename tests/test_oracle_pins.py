@@ -744,3 +744,56 @@ def test_becker_paper_domain_converges(orc):
     e = becker_errors(orc, (320, 640), -1.0, 1.5, 0.2)
     orders = np.log2(e[0] / e[1])
     assert orders.min() > 3.6, (e, orders)
+
+
+# ---------------------------------------------------------------------------
+# Moving no-slip wall (the lid of the Sec. 4 cavity, reading R17)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [12, 17])
+@pytest.mark.parametrize("limiter", [0, 2])
+def test_couette_residual_is_viscous_heating_only(orc, n, limiter):
+    """Plane Couette flow u = U y between a wall at y = 0 and one moving with
+    speed U at y = 1 (periodic in x, uniform rho and p) solves the momentum
+    equations exactly, and its energy grows at the viscous-heating rate mu U^2
+    (d/dy of u tau_xy = mu U^2 y). Every field is polynomial of degree <= 2, so
+    with the ghost values continuing the profile through both walls the residual
+    is (0, 0, 0, mu U^2) at every DoF to roundoff. A moving-wall ghost that
+    mirrors about zero instead of U_w, a wrong factor 2 or a dropped energy
+    correction leaves O(mu U / h^2) errors next to the lid."""
+    w = W.couette_2d(n, U=0.5, mu=1e-2)
+    P = orc.problem(2, n, n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, gamma=w.gamma, limiter=limiter,
+                    wall_speed=w.wall_speed)
+    dt = 0.5 * orc.dt_max(P, w.state)
+    L, nb = orc.residual(P, w.state, dt)
+    assert nb == 0
+    for part in W.split_sites(L, 2, n, n):
+        assert np.abs(part[:3]).max() < 1e-12
+        assert np.abs(part[3] - 1e-2 * 0.25).max() < 1e-12
+    # the same profile against a stationary top wall is not steady there
+    P.bc[3] = W.BC_WALL
+    L2, _ = orc.residual(P, w.state, dt)
+    assert np.abs(W.split_sites(L2, 2, n, n)[1][1]).max() > 1.0
+
+
+def test_moving_plate_matches_erfc(orc):
+    """Impulsively started plate (Rayleigh's problem): a wall at y = 0 moving with
+    U = 0.1 under fluid at rest (Mach 0.1, kappa = 0), mu = 1e-3, 4 x 100 cells to
+    t = 1: the x-velocity of the cell averages is within 2e-4 of the incompressible
+    U erfc(y / (2 sqrt(mu t))) (measured 4.7e-5), the same in every column, and
+    the wall's point values carry exactly u = U after the step."""
+    from math import erfc, sqrt
+    w = W.moving_plate_2d(100, U=0.1, mu=1e-3)
+    P = orc.problem(2, *w.n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, gamma=w.gamma, wall_speed=w.wall_speed)
+    s = w.state.copy()
+    rc, ns, nr = orc.advance(P, s, 0.0, 1.0)
+    assert rc == 0
+    parts = W.split_sites(s, 2, *w.n)
+    u = parts[0][1] / parts[0][0]
+    y = (np.arange(100) + 0.5) / 100
+    ex = np.array([0.1 * erfc(yy / (2 * sqrt(1e-3))) for yy in y])
+    assert np.abs(u - u[:, :1]).max() == 0.0
+    assert np.abs(u[:, 0] - ex).max() < 2e-4, np.abs(u[:, 0] - ex).max()
+    for k in (2, 3):                      # y-edge points and vertices on the wall row j = 0
+        wall = parts[k][:, 0]
+        assert np.abs(wall[1] / wall[0] - 0.1).max() < 1e-15 and np.abs(wall[2]).max() == 0.0
