@@ -25,8 +25,8 @@ cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *map, cudaStr
 {
     using T = Tile2<TX, TY>;
     size_t smem = T::template bytes<R>();
-    static bool attr_set = false;
-    if (!attr_set) {
+    static int resident = 0;   // CTAs of this configuration that fit on the GPU at once
+    if (!resident) {
         cudaError_t e = cudaFuncSetAttribute(k_stage2d<R, S, TX, TY, NTH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -35,9 +35,15 @@ cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *map, cudaStr
         e = cudaFuncSetAttribute(k_stage2d<R, S, TX, TY, NTH>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int dev = 0, nsm = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage2d<R, S, TX, TY, NTH>, NTH, smem);
+        if (e != cudaSuccess) return e;
+        resident = std::max(1, nsm * per_sm);
     }
-    dim3 grid((A.L.n1 + TX - 1) / TX, (A.L.n2 + TY - 1) / TY);
+    const long long ntiles = (long long)((A.L.n1 + TX - 1) / TX) * ((A.L.n2 + TY - 1) / TY);
+    const int grid = (int)std::min<long long>(ntiles, resident);
     k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A, *map);
     return cudaGetLastError();
 }

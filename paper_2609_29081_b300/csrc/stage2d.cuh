@@ -220,6 +220,51 @@ __device__ __forceinline__ R pressure2(R rho, R mx, R my, R E, R gm1)
 // above the rounding error of the terms (density 1e-2 of its term magnitude,
 // pressure 1e-3 of its term magnitude), so "true" implies the FP64 answer; a
 // "false" only sends the state to the FP64 island, which decides exactly.
+// Reciprocal, square root, reciprocal square root and exponential of the
+// compute precision. FP32: the hardware approximations (PTX rcp/sqrt/rsqrt
+// .approx.ftz, __expf), within about 2 ulp: their values feed FP32 stencils and
+// screens whose own rounding is larger, and every positivity decision that they
+// could tip is re-taken in FP64. FP64: the correctly rounded operations.
+template <class R>
+__device__ __forceinline__ R frcp(R x)
+{
+    if constexpr (sizeof(R) == 4) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    } else {
+        return 1.0 / x;
+    }
+}
+template <class R>
+__device__ __forceinline__ R fsqrt(R x)
+{
+    if constexpr (sizeof(R) == 4) {
+        float y;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    } else {
+        return sqrt(x);
+    }
+}
+template <class R>
+__device__ __forceinline__ R frsqrt(R x)
+{
+    if constexpr (sizeof(R) == 4) {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    } else {
+        return 1.0 / sqrt(x);
+    }
+}
+template <class R>
+__device__ __forceinline__ R fexp(R x)
+{
+    if constexpr (sizeof(R) == 4) return __expf(x);
+    else return exp(x);
+}
+
 template <class R>
 __device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1, R eps)
 {

@@ -178,7 +178,7 @@ __device__ __forceinline__ void node_flux(int l, R rho, R mx, R my, R E, R u, R 
 // lattice (point low-order update, Sec. 3.4 reading): Eq. (19) with S from
 // central differences on the lattice. FP64.
 template <class R, int TX, int TY>
-__device__ void lattice_llf(const V4<R> *sm, int l, int A, int B, double dx, double dy, double gamma, double mu,
+__device__ __noinline__ void lattice_llf(const V4<R> *sm, int l, int A, int B, double dx, double dy, double gamma, double mu,
                             double ka, double F[4])
 {
     using T = Tile2<TX, TY>;
@@ -253,17 +253,17 @@ __global__ void k_tile_consts(StageArgs A, TileConst<R> *out)
 template <class R>
 __device__ __forceinline__ V4<R> node_prims(const V4<R> &U, R gm1, R gam)
 {
-    const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
+    const R r = frcp(U.x), u = U.y * r, v = U.z * r;
     const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
     const R Tn = p * r;
-    return V4<R>{u, v, Tn, sqrt(gam * Tn)};
+    return V4<R>{u, v, Tn, fsqrt(gam * Tn)};
 }
 
 // (u, v, p, T) of a cell average, one reciprocal of rho.
 template <class R>
 __device__ __forceinline__ V4<R> cell_prims(const V4<R> &U, R gm1)
 {
-    const R r = R(1) / U.x, u = U.y * r, v = U.z * r;
+    const R r = frcp(U.x), u = U.y * r, v = U.z * r;
     const R p = gm1 * (U.w - R(0.5) * (U.y * u + U.z * v));
     return V4<R>{u, v, p, p * r};
 }
@@ -329,13 +329,33 @@ __device__ __forceinline__ void point_node(int t, int &la, int &lb)
     }
 }
 
+// The four TMA copies of tile (bx, by) into the staging area, one per DoF site:
+// columns [i0-2, i0+TX+1], rows [j0-2, j0+TY+1], the site's 4 component planes.
+template <class R, int TX, int TY>
+__device__ __forceinline__ void tile_issue(const StageArgs &A, int bx, int by, R *stg, const void *tmap,
+                                           uint64_t *bar)
+{
+    constexpr int BOX = 4 * (TX + 4) * (TY + 4);
+    mbar_expect_tx(bar, (unsigned)(4 * BOX * sizeof(R)) + (unsigned)A.extra_tx);
+    for (int site = 0; site < 4; ++site) tma_load_3d(stg + site * BOX, tmap, bx * TX, by * TY, 4 * site, bar);
+}
+
+// One tile of the stage. TMA path (persistent CTAs): `it` counts the tiles this
+// CTA has done; the first call sets up the barrier, the per-launch constants and
+// the copies of its own tile; every call copies the NEXT tile (nbx, nby; none if
+// nbx < 0) into the staging area as soon as that area is free (after the point
+// phase), so the copies land while the face and cell phases run. Returns false
+// when the tile's copies did not land in time (reported in Ctl.err): the CTA
+// stops. The element-copy path (batched kernel) loads its own tile and ignores
+// it / nbx / nby.
 template <class R, class S, int TX, int TY, int NTH, bool TMA>
-__device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm, const void *tmap)
+__device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm, const void *tmap,
+                                           int it = 0, int nbx = -1, int nby = -1)
 {
     using T = Tile2<TX, TY>;
     using Q4 = V4<R>;
     constexpr int LX = T::LX, CX = T::CX, QX = T::QX;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_stop;
     __shared__ TileConst<R> tc;
     __shared__ __align__(8) uint64_t s_bar;
     const Layout &L = A.L;
@@ -353,26 +373,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     // ---- P0: load point values and cell averages (two-node / two-cell halo)
     static_assert(sizeof(R) == sizeof(S), "tile and storage precision are the same");
     if constexpr (TMA) {
-        // four 3D tensor copies, one per DoF site: columns [i0-2, i0+TX+1],
-        // rows [j0-2, j0+TY+1], the site's 4 component planes, into a staging
-        // area in the gradient space (unused until P3); then one pass turns the
-        // planes into the 4-component node and cell records
+        // the tile's four 3D tensor copies land in a staging area in the
+        // gradient space (unused outside P3/P4); one pass turns the planes into
+        // the 4-component node and cell records
         constexpr int BX = TX + 4, BY = TY + 4, BOX = 4 * BX * BY;
         static_assert(BX == CX && BY == T::CY, "the box is the cell frame");
         static_assert(4 * BOX * sizeof(R) + 128 <= (size_t)(T::NGX + T::NGY) * sizeof(Q4), "staging fits");
         R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
-        if (tid == 0) mbar_init(&s_bar, 1);
-        __syncthreads();
-        if (tid == 0) {
-            mbar_expect_tx(&s_bar, (unsigned)(4 * BOX * sizeof(R)) + (unsigned)A.extra_tx);
-            for (int site = 0; site < 4; ++site) tma_load_3d(stg + site * BOX, tmap, i0, j0, 4 * site, &s_bar);
+        if (it == 0) {
+            if (tid == 0) {
+                mbar_init(&s_bar, 1);
+                s_stop = 0;
+                s_bad = 0;
+            }
+            __syncthreads();
+            if (tid == 0) tile_issue<R, TX, TY>(A, bx, by, stg, tmap, &s_bar);
+            // while the copies are in flight: the per-launch constants
+            load_tile_consts<R>(tc, A, tid);
         }
-        // while the copies are in flight: the per-tile constants
-        load_tile_consts<R>(tc, A, tid);
-        if (tid == 0) s_bad = 0;
-        // a load that has not landed after 2 s is reported, not waited for forever
-        if (!mbar_wait(&s_bar, 0, 2000000000ull)) atomicOr(&A.ctl->err, 1);
-        cp_async_wait_all();
+        // a copy that has not landed after 2 s is reported, not waited for forever
+        if (!mbar_wait(&s_bar, (unsigned)(it & 1), 2000000000ull)) {
+            atomicOr(&A.ctl->err, 1);
+            s_stop = 1;
+        }
         for (int t = tid; t < NP; t += nth) {
             int la, lb;
             point_node<LX>(t, la, lb);
@@ -454,6 +477,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         }
     }
     __syncthreads();
+    if constexpr (TMA) {
+        if (s_stop) return false;
+    }
     const double dt = A.ctl->dt;
     const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka;
 
@@ -674,8 +700,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
     }
 
     // the lattice state, primitives and gradients are dead from here on: the
-    // low-order cell records overwrite them
+    // low-order cell records overwrite them, and the next tile's copies go to the
+    // staging area (ordered after this tile's generic accesses to it)
     __syncthreads();
+    if constexpr (TMA) {
+        if (tid == 0 && nbx >= 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
+            tile_issue<R, TX, TY>(A, nbx, nby, stg, tmap, &s_bar);
+        }
+    }
 
     // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
     for (int t = tid; t < T::NCQ; t += nth) {
@@ -690,21 +724,21 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         R Fx[4], Fy[4];
         node_flux<R>(0, rho, U.y, U.z, U.w, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fx);
         node_flux<R>(1, rho, U.y, U.z, U.w, u, v, Tc, Sxu, Sxv, SxT, Syu, Syv, SyT, mu, ka, Fy);
-        const R cs = sqrt(gam * Tc);
+        const R cs = fsqrt(gam * Tc);
         // Lemma 3.2 bound b_l with tau_l = (tau_1l, tau_2l), q_l = -kappa dT/dx_l
         const R div = Sxu + Syv;
         const R txx = mu * (R(2) * Sxu - R(2) / R(3) * div), tyy = mu * (R(2) * Syv - R(2) / R(3) * div);
         const R txy = mu * (Syu + Sxv);
         const R re = p / gm1;
         const R qx = -ka * SxT, qy = -ka * SyT;
-        const R ib = R(1) / (R(2) * rho * re);
-        const R bx = (sqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) * ib;
-        const R by = (sqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) * ib;
+        const R ib = frcp(R(2) * rho * re);
+        const R bx = (fsqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) * ib;
+        const R by = (fsqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) * ib;
         // Sec. 3.2 sensors
-        const R px = fabs(We.z - R(2) * p + Ww.z) / fabs(We.z + R(2) * p + Ww.z);
-        const R py = fabs(Wn.z - R(2) * p + Ws.z) / fabs(Wn.z + R(2) * p + Ws.z);
+        const R px = fabs(We.z - R(2) * p + Ww.z) * frcp(fabs(We.z + R(2) * p + Ww.z));
+        const R py = fabs(Wn.z - R(2) * p + Ws.z) * frcp(fabs(Wn.z + R(2) * p + Ws.z));
         const R curl = Sxv - Syu;
-        const R ph2 = -div / sqrt(div * div + curl * curl + R(1e-13));
+        const R ph2 = -div * frsqrt(div * div + curl * curl + R(1e-13));
         sCQ[CQ_FX * T::NCQ + t] = Q4{Fx[0], Fx[1], Fx[2], Fx[3]};
         sCQ[CQ_FY * T::NCQ + t] = Q4{Fy[0], Fy[1], Fy[2], Fy[3]};
         sCQ[CQ_RB * T::NCQ + t] = Q4{fabs(u) + cs, fabs(v) + cs, bx, by};
@@ -761,7 +795,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
                 const R lam = l == 0 ? dmax(rbL.x, rbR.x) + dmax(rbL.z, rbR.z) : dmax(rbL.y, rbR.y) + dmax(rbL.w, rbR.w);
                 if (A.limiter == LIM_S_PP) {
                     const Q4 phL = sCQ[CQ_PH * T::NCQ + qL], phR = sCQ[CQ_PH * T::NCQ + qR];
-                    tsr = exp(-tc.cs * dmax(phL.x, phR.x) * dmax(phL.y, phR.y));
+                    tsr = fexp(-tc.cs * dmax(phL.x, phR.x) * dmax(phL.y, phR.y));
                 }
                 bool done = false;
                 if constexpr (sizeof(R) == 4) {
@@ -919,6 +953,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &A, int bx, int by, V
         }
     }
     if (tid == 0 && s_bad) atomicOr(&A.ctl->notpp, 1);
+    return true;
 }
 
 // Resident CTAs per SM that the register budget must allow: as many as the
@@ -935,14 +970,26 @@ constexpr int stage_min_ctas()
     return m < 1 ? 1 : m;
 }
 
-// One tile per CTA; the tile is loaded by TMA through the tensor map of the
-// stage input (a 3D map: x = element of a row, y = row, z = plane).
+// Persistent CTAs (as many as fit on the GPU at once) walk the tiles in steps
+// of the grid size, x fastest; tiles are loaded by TMA through the tensor map of
+// the stage input (a 3D map: x = element of a row, y = row, z = plane), each
+// tile's copies issued while the previous tile finishes.
 template <class R, class S, int TX, int TY, int NTH>
 __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
     k_stage2d(StageArgs A, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    stage_tile<R, S, TX, TY, NTH, true>(A, blockIdx.x, blockIdx.y, reinterpret_cast<V4<R> *>(smem_raw), &tmap);
+    const int tiles_x = (A.L.n1 + TX - 1) / TX, ntiles = tiles_x * ((A.L.n2 + TY - 1) / TY);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int tn = t + gridDim.x;
+        const bool more = tn < ntiles;
+        if (!stage_tile<R, S, TX, TY, NTH, true>(A, t % tiles_x, t / tiles_x, reinterpret_cast<V4<R> *>(smem_raw),
+                                                 &tmap, it, more ? tn % tiles_x : -1, more ? tn / tiles_x : -1))
+            break;
+        // the next tile's records overwrite this tile's
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
