@@ -449,6 +449,8 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batch", "tube", "ladder"])
     ap.add_argument("--t-end", type=float, default=0.0)
     ap.add_argument("--nprob", type=int, default=256)
+    ap.add_argument("--tile", type=lambda s: tuple(int(v) for v in s.split("x")), default=None,
+                    help="fixed 2D launch configuration TXxTYxTHREADS (e.g. 16x8x128) instead of the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist, rank, ws = dist_setup(args)
@@ -549,6 +551,12 @@ def accuracy_pair(w, nsteps):
                     "initial state, mixed vs FP64" % nsteps}
 
 
+def tile_opts(args):
+    if not args.tile:
+        return {}
+    return {"tile_x": args.tile[0], "tile_y": args.tile[1], "threads": args.tile[2]}
+
+
 def single_run(args, w, precision, dist, ws, e2e):
     """Tune, warm up and time args.steps CFL steps of workload w in one precision;
     optionally the end-to-end loop through host buffers."""
@@ -559,9 +567,10 @@ def single_run(args, w, precision, dist, ws, e2e):
     stream = torch.cuda.Stream()
     out = {}
     with torch.cuda.stream(stream):
-        S = Solver.from_workload(w, precision=prec, stream=stream)
+        S = Solver.from_workload(w, precision=prec, stream=stream, **tile_opts(args))
         S.set_state(w.state)
-        out["tuned"] = S.tune()
+        out["tuned"] = S.tune() if not args.tile else {"tile_x": args.tile[0], "tile_y": args.tile[1],
+                                                         "threads": args.tile[2], "fixed": True}
         if dist:
             dist.barrier()
         torch.cuda.synchronize()

@@ -100,6 +100,8 @@ typedef struct {
     double src_p0;     /* p0 of the Taylor-Green source (paper: 100) */
     double ex_M0;      /* AF_BC_EXACT: upstream Mach number of the Becker shock (default 3) */
     double ex_uinf;    /* AF_BC_EXACT: translation velocity of the shock (default 0.2) */
+    int threads;       /* threads per CTA of the 2D stage kernel: 128 (default) or 256;
+                          af_tune may change tile_x / tile_y / threads */
 } af_opts;
 
 /* Fill *o with the paper's defaults for a problem of dimension dim (except C^v

@@ -44,6 +44,8 @@ cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st);
+cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h,
+                                   cudaStream_t st);
 cudaError_t launch_tile_consts(const StageArgs &A, void *out, int fp32, cudaStream_t st);
 cudaError_t launch_to_f64(const Layout &L, const float *src, double *dst, int use_lo, cudaStream_t st);
 
@@ -93,7 +95,7 @@ struct afns_ctx {
     double *stage64 = nullptr;   // FP64 staging state of the mixed path
     bool mixed = false;
     int tile_x = 16, tile_y = 8; // 2D tile: 16x8, 16x16, or 32x8 (mixed path)
-    int threads = 256;           // threads per CTA of the stage kernel
+    int threads = 128;           // threads per CTA of the stage kernel
     // TMA tensor maps of the five state buffers for the 2D stage kernel, per tile
     // shape (16x8, 32x8, 16x16): 3D (element of a row, row, plane), box (TX+4, TY+4, 4)
     CUtensorMap maps[3][5];
@@ -247,6 +249,8 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
     if (o->source != AF_SRC_NONE && o->source != AF_SRC_TAYLOR_GREEN) return *why = "unknown source", AF_EINVAL;
     if (o->source == AF_SRC_TAYLOR_GREEN && g->dim != 2)
         return *why = "the Taylor-Green source is two-dimensional", AF_EINVAL;
+    if (o->threads != 0 && o->threads != 128 && o->threads != 256)
+        return *why = "threads per CTA must be 128 or 256", AF_EINVAL;
     if (!(o->cfl_c > 0) || !(o->cfl_v > 0) || !(o->eps > 0) || o->max_halvings < 0)
         return *why = "bad CFL numbers, eps or max_halvings", AF_EINVAL;
     return AF_OK;
@@ -272,6 +276,7 @@ af_status af_opts_default(int dim, af_opts *o)
     o->src_p0 = 100.0;
     o->ex_M0 = 3.0;
     o->ex_uinf = 0.2;
+    o->threads = 128;
     return AF_OK;
 }
 
@@ -343,6 +348,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->stage64 = c->mixed ? (double *)q : nullptr;
     c->tile_x = (c->mixed && opts->tile_x == 32) ? 32 : 16;
     c->tile_y = (c->tile_x == 16 && opts->tile_y == 16) ? 16 : 8;
+    c->threads = opts->threads == 256 ? 256 : 128;
     q += p.stage64;
     c->ctl = (Ctl *)q;
     q += p.ctl;
@@ -561,10 +567,28 @@ extern "C" af_status af_set_state_f32(afns_ctx *c, const float *const site[4], i
 {
     if (!c || !site) return fail(c, AF_EINVAL, "null argument");
     if (!c->mixed) return fail(c, AF_EINVAL, "FP32 state arrays need an AF_MIXED context");
-    af_status s = copy_sites_t<float>(c, c->U[0], const_cast<float *const *>(site), on_device, 0);
-    if (s != AF_OK) return s;
+    // host arrays: one contiguous copy per site into the staging area, then a
+    // kernel spreads them over the pitched planes (device arrays: the kernel
+    // reads them in place)
+    cudaError_t e = cudaSuccess;
+    size_t off = 0;
+    for (int s = 0; s < c->L.nsite && e == cudaSuccess; ++s) {
+        if (!site[s]) return fail(c, AF_EINVAL, "null site pointer");
+        int w, h;
+        site_dims(c, s, &w, &h);
+        const size_t bytes = sizeof(float) * (size_t)c->L.nc * w * h;
+        const float *src = site[s];
+        if (!on_device) {
+            float *stg = (float *)((char *)c->stage64 + off);
+            e = cudaMemcpyAsync(stg, site[s], bytes, cudaMemcpyHostToDevice, c->st);
+            src = stg;
+            off += align256(bytes);
+        }
+        if (e == cudaSuccess) e = launch_unpack_site_f32(c->L, src, (float *)c->U[0], s, w, h, c->st);
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "state upload");
     float *lo = (float *)c->U[0] + comp_plane(c->L, 0);
-    cudaError_t e = cudaMemsetAsync(lo, 0, sizeof(float) * (size_t)c->L.nc * c->L.plane, c->st);
+    e = cudaMemsetAsync(lo, 0, sizeof(float) * (size_t)c->L.nc * c->L.plane, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
     if (e == cudaSuccess)
         e = c->dim == 1 ? launch_validate1d_f32(c->L, (const float *)c->U[0], c->gamma, c->flag, c->st)

@@ -291,7 +291,7 @@ __global__ void k_batch_validate(const S *buf, Layout L, double gamma, int *flag
         long long off = cell_off(L, (int)(r % w), (int)(r / w));
         double U[4];
         for (int c = 0; c < 4; ++c) U[c] = (double)buf[plane_of(L, site, c) + off];
-        if (!admissible2(U, gamma - 1.0)) atomicOr(flag, 1);
+        if (!admissible_input2(U)) atomicOr(flag, 1);
     }
 }
 

@@ -8,6 +8,7 @@
 // exits. The paper has no counterpart of this call.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "afns.h"
@@ -106,7 +107,11 @@ extern "C" af_status af_dt_max_noalloc(const af_grid *grid, double gamma, double
     if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return AF_EINVAL;
     const long long cells = (long long)grid->n[0] * grid->n[1];
     const long long nchunks = (cells + kChunk - 1) / kChunk;
-    if (nchunks > kMaxChunks) return AF_EINVAL;   // larger than the static scratch
+    if (nchunks > kMaxChunks) {   // larger than the static scratch
+        std::fprintf(stderr, "af_dt_max_noalloc: %lld cells exceed the fixed scratch limit of %lld cells\n", cells,
+                     (long long)kChunk * kMaxChunks);
+        return AF_EINVAL;
+    }
     af_opts d;
     if (!opts) {
         af_opts_default(2, &d);

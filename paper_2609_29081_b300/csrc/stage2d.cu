@@ -158,6 +158,31 @@ __global__ void k_to_f64(const float *src, double *dst, long long plane, int npl
     }
 }
 
+// One DoF site's packed array (components in turn, x fastest, no ghosts) into the
+// pitched planes of a state buffer: one coalesced pass, so that a host upload is
+// one contiguous copy per site instead of one strided copy per component.
+template <class T>
+__global__ void k_unpack_site(Layout L, const T *src, T *buf, int site, int w, int h)
+{
+    const long long wh = (long long)w * h, n = (long long)L.nc * wh;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / wh);
+        const long long r = e - c * wh;
+        const int j = (int)(r / w), i = (int)(r - (long long)j * w);
+        const long long off = L.dim == 2 ? cell_off(L, i, j) : 2 + i;
+        buf[plane_of(L, site, c) + off] = src[e];
+    }
+}
+
+cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h,
+                                   cudaStream_t st)
+{
+    const long long n = (long long)L.nc * w * h;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148 * 16);
+    k_unpack_site<float><<<blocks, 256, 0, st>>>(L, src, buf, site, w, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st)
 {
     int np = L.nsite * L.nc;

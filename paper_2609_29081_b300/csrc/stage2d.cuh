@@ -149,28 +149,36 @@ __device__ __forceinline__ void tile_const_init(TileConst<R> &t, const StageArgs
 // v = -a cos x sin y, p = p0/(gamma-1) + a^2 b/4 (rho = 1);
 // S_E = (p_t + u p_x + v p_y)/(gamma-1) - 4 mu a^2 cos^2 x cos^2 y - kappa Lap p,
 // p_t = -mu a^2 b, p_x = -a^2 sin(2x)/2, p_y = -a^2 sin(2y)/2, Lap p = -a^2 b.
-__device__ inline double tg_energy_source(const StageArgs &A, double x, double y, double t)
+__device__ inline double tg_energy_source(double mu, double kappa, double gamma, double x, double y, double t)
 {
-    const double a = exp(-2.0 * A.mu * t), a2 = a * a;
+    const double a = exp(-2.0 * mu * t), a2 = a * a;
     const double b = cos(2.0 * x) + cos(2.0 * y);
     const double sx = sin(x), cx = cos(x), sy = sin(y), cy = cos(y);
     const double u = a * sx * cy, v = -a * cx * sy;
-    const double pt = -A.mu * a2 * b, px = -a2 * sin(2.0 * x) / 2.0, py = -a2 * sin(2.0 * y) / 2.0;
-    return (pt + u * px + v * py) / (A.gamma - 1.0) - 4.0 * A.mu * a2 * cx * cx * cy * cy + A.kappa * a2 * b;
+    const double pt = -mu * a2 * b, px = -a2 * sin(2.0 * x) / 2.0, py = -a2 * sin(2.0 * y) / 2.0;
+    return (pt + u * px + v * py) / (gamma - 1.0) - 4.0 * mu * a2 * cx * cx * cy * cy + kappa * a2 * b;
 }
 
-// Its average over the cell [x0, x0 + hx] x [y0, y0 + hy]: 5 x 5 Gauss-Legendre.
-__device__ inline double tg_energy_source_cell(const StageArgs &A, double x0, double y0, double hx, double hy,
-                                               double t)
+// The source at lattice node (a, b) (spacing half a cell) and its 5 x 5
+// Gauss-Legendre average over cell (i, j), at time t, for a grid with origin
+// (x0, y0) and spacing (hx, hy).
+static __device__ __forceinline__ double tg_point_source(double mu, double kappa, double gamma, double x0, double y0,
+                                                      double hx, double hy, int a, int b, double t)
+{
+    return tg_energy_source(mu, kappa, gamma, x0 + 0.5 * a * hx, y0 + 0.5 * b * hy, t);
+}
+static __device__ __forceinline__ double tg_cell_source(double mu, double kappa, double gamma, double x0, double y0,
+                                                     double hx, double hy, int i, int j, double t)
 {
     const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
     const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665,
                           0.2369268850561891};
+    const double xc = x0 + i * hx, yc = y0 + j * hy;
     double s = 0.0;
     for (int q1 = 0; q1 < 5; ++q1)
         for (int q0 = 0; q0 < 5; ++q0)
             s += 0.25 * gw[q0] * gw[q1] *
-                 tg_energy_source(A, x0 + 0.5 * hx * (1.0 + gx[q0]), y0 + 0.5 * hy * (1.0 + gx[q1]), t);
+                 tg_energy_source(mu, kappa, gamma, xc + 0.5 * hx * (1.0 + gx[q0]), yc + 0.5 * hy * (1.0 + gx[q1]), t);
     return s;
 }
 
@@ -283,6 +291,14 @@ __device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1
 }
 
 // Is U admissible (finite, rho > 0, p > 0)? Evaluated in FP64.
+// Check of an input DoF (finite, rho > 0, p > 0) without a division: for
+// rho > 0 and gamma > 1, p > 0 exactly when 2 rho E > |m|^2.
+__device__ __forceinline__ bool admissible_input2(const double *U)
+{
+    const bool fin = isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
+    return fin && U[0] > 0.0 && 2.0 * U[0] * U[3] > U[1] * U[1] + U[2] * U[2];
+}
+
 __device__ __forceinline__ bool admissible2(const double *U, double gm1)
 {
     if (!(U[0] > 0.0)) return false;

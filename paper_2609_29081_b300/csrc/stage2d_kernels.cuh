@@ -380,6 +380,9 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         static_assert(BX == CX && BY == T::CY, "the box is the cell frame");
         static_assert(4 * BOX * sizeof(R) + 128 <= (size_t)(T::NGX + T::NGY) * sizeof(Q4), "staging fits");
         R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
+        // gas constants of the transposition pass: from the per-launch constants
+        // once they are in place (no FP64 instruction per tile)
+        const R gm1_in = it == 0 ? (R)(A.gamma - 1.0) : tc.gm1, gam_in = it == 0 ? (R)A.gamma : tc.gam;
         if (it == 0) {
             if (tid == 0) {
                 mbar_init(&s_bar, 1);
@@ -409,7 +412,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                                                           : benign;
             sU[lb * LX + la] = U;
             // the point's primitives right away (the centres get theirs in P1)
-            sQ[lb * LX + la] = node_prims(U, (R)(A.gamma - 1.0), (R)A.gamma);
+            sQ[lb * LX + la] = node_prims(U, gm1_in, gam_in);
         }
         for (int t = tid; t < T::NCA; t += nth) {
             const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
@@ -623,8 +626,8 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             R r[4];
             point_residual<R, TX, TY>(sm, la, lb, tc, r);
             if (A.source)
-                r[3] += (R)tg_energy_source(A, L.lo[0] + 0.5 * a * L.dx, L.lo[1] + 0.5 * b * L.dy,
-                                            A.ctl->t + A.k.ct * dt);
+                r[3] += (R)tg_point_source(A.mu, A.kappa, A.gamma, L.lo[0], L.lo[1], L.dx, L.dy, a, b,
+                                           A.ctl->t + A.k.ct * dt);
             // the RK combination of point values runs in the storage precision S
             const Q4 Un4 = sU[n];
             const R Un[4] = {Un4.x, Un4.y, Un4.z, Un4.w};
@@ -868,9 +871,8 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                 if (tc.ua0) g0[c] = ld<S>(A.u0, po0 + c * L.plane);
                 if (tc.ua2 || A.k.acc) g2[c] = ld<S>(A.aux, po0 + c * L.plane);
             }
-            const double src = A.source ? tg_energy_source_cell(A, L.lo[0] + (i0 + il) * L.dx,
-                                                                L.lo[1] + (j0 + jl) * L.dy, L.dx, L.dy,
-                                                                A.ctl->t + A.k.ct * dt)
+            const double src = A.source ? tg_cell_source(A.mu, A.kappa, A.gamma, L.lo[0], L.lo[1], L.dx, L.dy,
+                                                         i0 + il, j0 + jl, A.ctl->t + A.k.ct * dt)
                                         : 0.0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -918,23 +920,28 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             const Q4 ui = sA[(jl + 2) * CX + (il + 2)];
             // manufactured energy source (FP64, only when enabled): its weighted
             // contributions enter the compensated sums as float-float values
-            const double src = A.source ? tg_energy_source_cell(A, L.lo[0] + (i0 + il) * L.dx,
-                                                                L.lo[1] + (j0 + jl) * L.dy, L.dx, L.dy,
-                                                                A.ctl->t + A.k.ct * dt)
-                                        : 0.0;
+            float src_f = 0.f;
+            ff src_inc = {0.f, 0.f}, src_acc = {0.f, 0.f};
+            if (A.source) {
+                const double src = tg_cell_source(A.mu, A.kappa, A.gamma, L.lo[0], L.lo[1], L.dx, L.dy, i0 + il,
+                                                  j0 + jl, A.ctl->t + A.k.ct * dt);
+                src_f = (float)src;
+                src_inc = ff_from(A.k.cl * dt * src);
+                src_acc = ff_from(A.k.bl * dt * src);
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float fr = comp(fxr, c), fl = comp(fxl, c), ft = comp(fyt, c), fb = comp(fyb, c);
                 const long long po = plane_of(L, 0, c) + off, pl = comp_plane(L, c) + off;
                 const bool has_src = c == 3 && A.source;
                 if (A.k.residual) {
-                    out[po] = -(fr - fl) * fidx - (ft - fb) * fidy + (has_src ? (float)src : 0.f);
+                    out[po] = -(fr - fl) * fidx - (ft - fb) * fidy + (has_src ? src_f : 0.f);
                     out[pl] = 0.f;
                     continue;
                 }
                 const ff dxf = ff_two_sum(fl, -fr), dyf = ff_two_sum(fb, -ft);   // exact
                 ff inc = ff_add(ff_mul(wx, dxf), ff_mul(wy, dyf));
-                if (has_src) inc = ff_add(inc, ff_from(A.k.cl * dt * src));
+                if (has_src) inc = ff_add(inc, src_inc);
                 const ff uv = {(float)comp(ui, c), ulo[c]};
                 ff v = ff_mul(a1, uv);
                 if (tc.ua0) v = ff_add(v, ff_mul(a0, ff{g0h[c], g0l[c]}));
@@ -942,7 +949,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                 if (A.k.acc) {
                     ff ac = ff_add(ff_mul(b2, ff{g2h[c], g2l[c]}), ff_mul(b1, uv));
                     ac = ff_add(ac, ff_add(ff_mul(bx, dxf), ff_mul(by, dyf)));
-                    if (has_src) ac = ff_add(ac, ff_from(A.k.bl * dt * src));
+                    if (has_src) ac = ff_add(ac, src_acc);
                     aux[po] = ac.h;
                     aux[pl] = ac.l;
                 }
@@ -1106,7 +1113,7 @@ __global__ void k_validate2d(Layout L, const S *buf, double gamma, int *flag)
         long long off = cell_off(L, i, j);
         double U[4];
         for (int c = 0; c < 4; ++c) U[c] = (double)buf[plane_of(L, site, c) + off];
-        if (!admissible2(U, gamma - 1.0)) atomicOr(flag, 1);
+        if (!admissible_input2(U)) atomicOr(flag, 1);
         bool ptx = site == 1 || site == 3, pty = site == 2 || site == 3;
         int si = i, sj = j;
         if (ptx && i == n1 && L.bc[0] == BC_PERIODIC) si = 0;
