@@ -220,14 +220,6 @@ __device__ __forceinline__ void cp_async_elem(T *dst_shared, const T *src_global
 #endif
 }
 
-// Bring the line of a global address into L2 ahead of its use (a hint).
-__device__ __forceinline__ void prefetch_l2(const void *p)
-{
-#ifdef __CUDA_ARCH__
-    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
-#endif
-}
-
 // Wait until every cp.async this thread issued has landed in shared memory
 // (other threads see them after the next barrier).
 __device__ __forceinline__ void cp_async_wait_all()

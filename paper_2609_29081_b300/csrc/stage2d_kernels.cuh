@@ -329,6 +329,49 @@ __device__ __forceinline__ void point_node(int t, int &la, int &lb)
     }
 }
 
+// FP64 island of the point update (Sec. 3.4) for a point whose FP32 screen did
+// not clear it: the exact test of the high-order value U^n + dt r, and where that
+// leaves G_eps the low-order LLF point update on the half lattice and the Theta
+// blend; returns the blended residual. Out of line: few points take it, and
+// inlined, its FP64 conversions were scheduled ahead of the screen for every point.
+template <class S>
+struct PointFix {
+    S r[4];
+    int blended, bad;
+};
+template <class R, class S, int TX, int TY>
+__device__ __noinline__ PointFix<S> point_island(const V4<R> *sm, int n, V4<R> un, V4<R> rr4, double dt, double eps,
+                                                 double gamma, double mu, double kappa, double dx, double dy)
+{
+    constexpr int LX = Tile2<TX, TY>::LX;
+    PointFix<S> f{};
+    const R Un[4] = {un.x, un.y, un.z, un.w}, r[4] = {rr4.x, rr4.y, rr4.z, rr4.w};
+    double Ud[4], UH[4];
+    for (int c = 0; c < 4; ++c) Ud[c] = (double)Un[c], UH[c] = Ud[c] + dt * (double)r[c];
+    const double gm1d = gamma - 1.0;
+    const double pH = gm1d * (UH[3] - (UH[1] * UH[1] + UH[2] * UH[2]) / (2.0 * UH[0]));
+    if (UH[0] >= eps && pH >= eps) return f;
+    double UL[4] = {Ud[0], Ud[1], Ud[2], Ud[3]};
+    for (int l = 0; l < 2; ++l) {
+        const int st = l == 0 ? 1 : LX;
+        double Fr[4], Fl[4];
+        lattice_llf<R, TX, TY>(sm, l, n, n + st, dx, dy, gamma, mu, kappa, Fr);
+        lattice_llf<R, TX, TY>(sm, l, n - st, n, dx, dy, gamma, mu, kappa, Fl);
+        const double rl = dt / (0.5 * (l == 0 ? dx : dy));
+        for (int c = 0; c < 4; ++c) UL[c] -= rl * (Fr[c] - Fl[c]);
+    }
+    if (!admissible2(UL, gm1d)) f.bad = 1;
+    const double thr = theta_fn(UL[0], UH[0], fmin(eps, UL[0]));
+    double Ur[4];
+    for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * UL[c] + thr * UH[c];
+    const double pL = gm1d * (UL[3] - (UL[1] * UL[1] + UL[2] * UL[2]) / (2.0 * UL[0]));
+    const double pr = gm1d * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
+    const double th = thr * theta_fn(pL, pr, fmin(eps, pL));
+    for (int c = 0; c < 4; ++c) f.r[c] = (S)(((1.0 - th) * UL[c] + th * UH[c] - Ud[c]) / dt);
+    f.blended = 1;
+    return f;
+}
+
 // The four TMA copies of tile (bx, by) into the staging area, one per DoF site:
 // columns [i0-2, i0+TX+1], rows [j0-2, j0+TY+1], the site's 4 component planes.
 template <class R, int TX, int TY>
@@ -457,27 +500,6 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         load_tile_consts<R>(tc, A, tid);
         if (tid == 0) s_bad = 0;
         cp_async_wait_all();
-    }
-    // the cell update (last phase) reads u^n, the accumulator and the
-    // compensation words of its cells from global memory: start them towards L2
-    // now, so that the last phase does not wait on DRAM
-    {
-        const bool pu0 = A.k.a0 != 0.0, paux = A.k.a2 != 0.0 || A.k.acc;
-        for (int t = tid; t < ntx * nty && !A.k.residual; t += nth) {
-            const long long off = cell_off(L, i0 + t % ntx, j0 + t / ntx);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const long long po = plane_of(L, 0, c) + off;
-                if (pu0) prefetch_l2((const S *)A.u0 + po);
-                if (paux) prefetch_l2((const S *)A.aux + po);
-                if constexpr (sizeof(S) == 4) {
-                    const long long pl = comp_plane(L, c) + off;
-                    prefetch_l2((const S *)A.uin + pl);
-                    if (pu0) prefetch_l2((const S *)A.u0 + pl);
-                    if (paux) prefetch_l2((const S *)A.aux + pl);
-                }
-            }
-        }
     }
     __syncthreads();
     if constexpr (TMA) {
@@ -641,30 +663,12 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                     mag[c] = fabs(Un[c]) + fabs(tc.dt * r[c]);
                 }
                 if (!surely_above(UHr, mag, gm1, tc.eps)) {
-                    // FP64 island: exact test, then the low-order LLF point update on
-                    // the half lattice and the Theta blend of Sec. 3.4
-                    double Ud[4], UH[4];
-                    for (int c = 0; c < 4; ++c) Ud[c] = (double)Un[c], UH[c] = Ud[c] + dt * (double)r[c];
-                    double gm1d = A.gamma - 1.0;
-                    double pH = gm1d * (UH[3] - (UH[1] * UH[1] + UH[2] * UH[2]) / (2.0 * UH[0]));
-                    if (!(UH[0] >= eps) || !(pH >= eps)) {
-                        double UL[4] = {Ud[0], Ud[1], Ud[2], Ud[3]};
-                        for (int l = 0; l < 2; ++l) {
-                            const int st = l == 0 ? 1 : LX;
-                            double Fr[4], Fl[4];
-                            lattice_llf<R, TX, TY>(sm, l, n, n + st, L.dx, L.dy, A.gamma, A.mu, A.kappa, Fr);
-                            lattice_llf<R, TX, TY>(sm, l, n - st, n, L.dx, L.dy, A.gamma, A.mu, A.kappa, Fl);
-                            double rr = dt / (0.5 * (l == 0 ? L.dx : L.dy));
-                            for (int c = 0; c < 4; ++c) UL[c] -= rr * (Fr[c] - Fl[c]);
-                        }
-                        if (!admissible2(UL, gm1d)) s_bad = 1;
-                        double thr = theta_fn(UL[0], UH[0], fmin(eps, UL[0]));
-                        double Ur[4];
-                        for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * UL[c] + thr * UH[c];
-                        double pL = gm1d * (UL[3] - (UL[1] * UL[1] + UL[2] * UL[2]) / (2.0 * UL[0]));
-                        double pr = gm1d * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
-                        double th = thr * theta_fn(pL, pr, fmin(eps, pL));
-                        for (int c = 0; c < 4; ++c) res[c] = (S)(((1.0 - th) * UL[c] + th * UH[c] - Ud[c]) / dt);
+                    const PointFix<S> f = point_island<R, S, TX, TY>(sm, n, Un4, Q4{r[0], r[1], r[2], r[3]}, dt, eps,
+                                                                      A.gamma, A.mu, A.kappa, L.dx, L.dy);
+                    if (f.bad) s_bad = 1;
+                    if (f.blended) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) res[c] = f.r[c];
                     }
                 }
             }
