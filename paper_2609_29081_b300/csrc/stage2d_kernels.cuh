@@ -372,6 +372,61 @@ __device__ __noinline__ PointFix<S> point_island(const V4<R> *sm, int n, V4<R> u
     return f;
 }
 
+// FP64 island of a cell centre whose FP32 screen did not clear it (Sec. 2.2,
+// Remark 3.1): the Simpson inversion from the cell average ab, the edge points
+// e0..e3 and the vertices v0..v3 in FP64, scaled toward the average when it is
+// below epsilon. Out of line, like the point island.
+template <class R>
+__device__ __noinline__ V4<R> centre_island(V4<R> ab, V4<R> e0, V4<R> e1, V4<R> e2, V4<R> e3, V4<R> v0, V4<R> v1,
+                                            V4<R> v2, V4<R> v3, double g1, double eps)
+{
+    double Ub[4], Ud[4];
+    for (int c = 0; c < 4; ++c) {
+        const double edges = (double)comp(e0, c) + (double)comp(e1, c) + (double)comp(e2, c) + (double)comp(e3, c);
+        const double verts = (double)comp(v0, c) + (double)comp(v1, c) + (double)comp(v2, c) + (double)comp(v3, c);
+        Ub[c] = (double)comp(ab, c);
+        Ud[c] = (36.0 * Ub[c] - 4.0 * edges - verts) / 16.0;
+    }
+    const double pc = g1 * (Ud[3] - (Ud[1] * Ud[1] + Ud[2] * Ud[2]) / (2.0 * Ud[0]));
+    if (!(Ud[0] >= eps) || !(pc >= eps)) {
+        const double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
+        double Ur[4];
+        for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
+        const double pL = g1 * (Ub[3] - (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / (2.0 * Ub[0]));
+        const double pH = g1 * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
+        const double th = thr * theta_fn(pL, pH, fmin(eps, pL));
+        for (int c = 0; c < 4; ++c) Ud[c] = (1.0 - th) * Ub[c] + th * Ud[c];
+    }
+    return V4<R>{(R)Ud[0], (R)Ud[1], (R)Ud[2], (R)Ud[3]};
+}
+
+// FP64 island of a face whose FP32 screen did not clear it (mixed path, Sec. 3.3):
+// face_pp_fp64 on the face's low-order cell fluxes fL / fR, averages uL / uR and
+// high-order flux fh; returns the limited flux, theta^rho theta^p and whether a
+// low-order state left G.
+template <class R>
+struct FaceFix {
+    R F[4];
+    R tpp;
+    int bad;
+};
+template <class R>
+__device__ __noinline__ FaceFix<R> face_island(V4<R> fL, V4<R> fR, V4<R> uL, V4<R> uR, V4<R> fh, R lam, R ts,
+                                               double kk, double g1, double eps)
+{
+    const double FLc[4] = {fL.x, fL.y, fL.z, fL.w}, FRc[4] = {fR.x, fR.y, fR.z, fR.w};
+    const double UbL[4] = {uL.x, uL.y, uL.z, uL.w}, UbR[4] = {uR.x, uR.y, uR.z, uR.w};
+    const double FH[4] = {fh.x, fh.y, fh.z, fh.w};
+    double Fd[4], tpp = 1.0;
+    bool bad = false;
+    face_pp_fp64(FLc, FRc, UbL, UbR, (double)lam, (double)ts, FH, kk, g1, eps, Fd, &tpp, &bad);
+    FaceFix<R> f;
+    for (int c = 0; c < 4; ++c) f.F[c] = (R)Fd[c];
+    f.tpp = (R)tpp;
+    f.bad = bad ? 1 : 0;
+    return f;
+}
+
 // The four TMA copies of tile (bx, by) into the staging area, one per DoF site:
 // columns [i0-2, i0+TX+1], rows [j0-2, j0+TY+1], the site's 4 component planes.
 template <class R, int TX, int TY>
@@ -534,27 +589,8 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                     mag[c] = R(4) * (fabs(comp(ab, c)) + fabs(comp(e0, c)) + fabs(comp(e1, c)) + fabs(comp(e2, c)) +
                                      fabs(comp(e3, c)));
                 if (!surely_above(Uc, mag, gm1, tc.eps)) {
-                    // FP64 island: the centre in FP64 (same expression), then the scaling
-                    // toward the cell average of Remark 3.1 if it is below epsilon
-                    double Ub[4], Ud[4];
-                    for (int c = 0; c < 4; ++c) {
-                        double edges = (double)comp(e0, c) + (double)comp(e1, c) + (double)comp(e2, c) + (double)comp(e3, c);
-                        double verts = (double)comp(v0, c) + (double)comp(v1, c) + (double)comp(v2, c) + (double)comp(v3, c);
-                        Ub[c] = (double)comp(ab, c);
-                        Ud[c] = (36.0 * Ub[c] - 4.0 * edges - verts) / 16.0;
-                    }
-                    double g1 = A.gamma - 1.0;
-                    double pc = g1 * (Ud[3] - (Ud[1] * Ud[1] + Ud[2] * Ud[2]) / (2.0 * Ud[0]));
-                    if (!(Ud[0] >= eps) || !(pc >= eps)) {
-                        double thr = theta_fn(Ub[0], Ud[0], fmin(eps, Ub[0]));
-                        double Ur[4];
-                        for (int c = 0; c < 4; ++c) Ur[c] = (1.0 - thr) * Ub[c] + thr * Ud[c];
-                        double pL = g1 * (Ub[3] - (Ub[1] * Ub[1] + Ub[2] * Ub[2]) / (2.0 * Ub[0]));
-                        double pH = g1 * (Ur[3] - (Ur[1] * Ur[1] + Ur[2] * Ur[2]) / (2.0 * Ur[0]));
-                        double th = thr * theta_fn(pL, pH, fmin(eps, pL));
-                        for (int c = 0; c < 4; ++c) Ud[c] = (1.0 - th) * Ub[c] + th * Ud[c];
-                    }
-                    for (int c = 0; c < 4; ++c) Uc[c] = (R)Ud[c];
+                    const V4<R> cf = centre_island<R>(ab, e0, e1, e2, e3, v0, v1, v2, v3, A.gamma - 1.0, eps);
+                    Uc[0] = cf.x, Uc[1] = cf.y, Uc[2] = cf.z, Uc[3] = cf.w;
                 }
             }
             U = Q4{Uc[0], Uc[1], Uc[2], Uc[3]};
@@ -826,6 +862,17 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                         surely_above(ULm, mag, gm1, tc.eps) && surely_above(UHm, mag, gm1, tc.eps)) {
 #pragma unroll
                         for (int c = 0; c < 4; ++c) Fout[c] = FLs[c];
+                        done = true;
+                    }
+                }
+                if constexpr (sizeof(R) == 4) {
+                    if (!done) {
+                        const FaceFix<R> f = face_island<R>(fL4, fR4, uL4, uR4, fh4, lam, tsr,
+                                                            4.0 * dt / (l == 0 ? L.dx : L.dy), A.gamma - 1.0, eps);
+                        if (f.bad) s_bad = 1;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Fout[c] = f.F[c];
+                        tppr = f.tpp;
                         done = true;
                     }
                 }
