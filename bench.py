@@ -33,19 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "2D cell-stage updates/s and HBM fraction, FP32-mixed vs FP64, at stated L1 error vs oracle"
 UNIT = "cell-stage updates/s"
 N_CELLS = 1024
-# FP64 peak of one B300 (TFLOP/s): the published dense FP64 rate of the part
-# (the FP64 pipe is 1/64 of the FP32 rate on sm_103); see the design doc for its derivation.
-# B300: 148 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.032 GHz (max SM clock)
+# FP64 peak of one B300 (TFLOP/s) from its unit counts (the FP64 pipe is 1/64 of
+# the FP32 rate on sm_103): 148 SMs x 2 FP64 FMA per SM per clock x 2 flops x
+# 2.032 GHz (max SM clock)
 FP64_DERIVED_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # 148 SMs x 128 FP32 lanes x 2 flops x 2.032 GHz
 FP32_DERIVED_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read + write) per stage launch from ncu, with the digest of the
 # kernel sources they were taken on; reported only while the sources match.
 MEASURED_TRAFFIC = {
-    # profiles/stage2d_mixed_smooth1024.md: first RK stage of a step, 32x8 tiles
-    "mixed:1db0a64577a2b414": 129.65e6,
-    # profiles/stage2d_fp64_smooth1024.md: first RK stage of a step, 16x8 tiles
-    "fp64:1db0a64577a2b414": 233.42e6,
+    # ncu capture of one mixed stage launch of a timed step, 16x8 tiles, 128 threads
+    "mixed:38db0e834b60189f": 132.03e6,
+    # ncu capture of one FP64 stage launch of a timed step, 16x8 tiles, 128 threads
+    "fp64:38db0e834b60189f": 229.95e6,
 }
 
 
@@ -622,7 +622,7 @@ def single_run(args, w, precision, dist, ws, e2e):
 
 
 # Algorithmic work of one 2D stage per cell (counted from the operation counts of
-# the stage): FP64 floating-point operations and, for the mixed
+# the stage's equations): floating-point operations and, for the mixed
 # path, the minimum HBM bytes of the stage (3.2 state copies of 16 FP32 words plus
 # 4 compensation words per stage on average over the five SSP-RK54 stages).
 FLOPS_PER_CELL_STAGE = 3000
