@@ -217,6 +217,11 @@ def batch_seed(rank):
     return 5 + rank
 
 
+def workload_name(n):
+    return ("2D smooth periodic NS %dx%d (rho=1+0.2sin(x+y), (u,v)=(1,0.5)+8-mode perturbation, p=1, mu=0.01, "
+            "Pr=0.72), CFL steps, limiter s+pp" % (n, n))
+
+
 def reference_arm(args, rank, ws):
     """The oracle as it stands, on the host cores: each timed step is one full
     SSP-RK54 step of the same flow on a 128 x 128 sample of the grid."""
@@ -239,8 +244,8 @@ def reference_arm(args, rank, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "2D smooth periodic NS, [0,2pi)^2, mu=0.01, Pr=0.72, 8-mode perturbation",
-                       "grid": "%dx%d sample of 1024x1024" % (n, n), "limiter": "s+pp"},
+            "config": {"workload": workload_name(args.n), "precision": "fp64 (oracle)",
+                       "sample": "each timed step: one SSP-RK54 step of the same flow on a %dx%d grid" % (n, n)},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d SSP-RK54 steps on a %dx%d sample of the workload" % (args.steps, n, n)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -486,9 +491,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "2D smooth periodic NS %dx%d (rho=1+0.2sin(x+y), (u,v)=(1,0.5)+8-mode "
-                                   "perturbation, p=1, mu=0.01, Pr=0.72), CFL steps, limiter s+pp"
-                                   % (args.n, args.n),
+            "config": {"workload": workload_name(args.n),
                        "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "working set larger than L2: a stage reads 1-3 state buffers of %.0f MB and writes 1-2"
                              % (w.cells * (20 * 4 if args.precision == "mixed" else 16 * 8) / 1e6),

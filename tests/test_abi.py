@@ -73,3 +73,10 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     assert st == N.AF_EINVAL and not ctx.value
     assert L.af_opts_default(1, ctypes.byref(o)) == N.AF_OK
     assert o.ex_M0 == 3.0 and o.ex_uinf == 0.2 and o.cfl_v == pytest.approx(0.33)
+    # the stage kernel's CTA size: 128 (default) or 256; anything else is refused
+    assert L.af_opts_default(2, ctypes.byref(o)) == N.AF_OK and o.threads == 128
+    b.side[0] = b.side[1] = b.side[2] = b.side[3] = 0
+    o.threads = 64
+    st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), ctypes.byref(o), None, None, 0,
+                     ctypes.byref(ctx))
+    assert st == N.AF_EINVAL and not ctx.value
