@@ -18,6 +18,11 @@
 #include "afns.h"
 #include "stage2d.cuh"
 
+namespace {
+// bytes between the tile-constant records of the five stages of a step
+constexpr int kTconstStride = (int)((sizeof(afns::TileConst<double>) + 255) / 256 * 256);
+}
+
 namespace afns {
 cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map, cudaStream_t st);
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
@@ -41,6 +46,8 @@ cudaError_t launch_dt1d_f32(const Layout &L, const float *buf, double gamma, dou
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map, cudaStream_t st);
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
+cudaError_t launch_tile_consts5(const StageArgs &A, const StageCoef *ks, void *out, int stride_bytes, int fp32,
+                                cudaStream_t st);
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st);
@@ -178,7 +185,7 @@ static WsPlan plan_ws(const Layout &L, const af_opts *o)
     p.flag = align256(sizeof(int) * 4);
     // the mixed path converts to / from the FP64 public layout through a staging state
     p.stage64 = o->precision == AF_MIXED ? align256((size_t)L.nsite * L.nc * (size_t)L.plane * sizeof(double)) : 0;
-    p.tconst = align256(sizeof(TileConst<double>));
+    p.tconst = align256(5 * kTconstStride);
     p.total = 5 * p.state + p.stage64 + p.ctl + p.partial + p.theta + p.flag + p.tconst;
     return p;
 }
@@ -457,7 +464,7 @@ static cudaError_t do_ghost(afns_ctx *c, void *buf, double ct = 0.0)
         }
         return e;
     }
-    c->launches += 2;
+    c->launches += 1;
     if (c->mixed) return launch_ghost2d_f32(c->L, (float *)buf, c->st);
     return launch_ghost2d_fp64(c->L, (double *)buf, c->st);
 }
@@ -635,7 +642,9 @@ static StageArgs base_args(afns_ctx *c)
 }
 
 // One fused stage: ghost fill of the input, then the stage kernel.
-static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &k, double *theta)
+// slot >= 0: the stage's tile constants were formed for the whole step (slot =
+// stage index); slot < 0: form them for this stage alone.
+static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &k, double *theta, int slot = -1)
 {
     cudaError_t e = do_ghost(c, in, k.ct);
     if (e != cudaSuccess) return e;
@@ -648,9 +657,13 @@ static cudaError_t run_stage(afns_ctx *c, void *in, void *out, const StageCoef &
     A.k = k;
     A.extra_tx = c->debug_extra_tx;
     if (c->dim == 2) {
-        A.tconst = c->tconst;
-        if ((e = launch_tile_consts(A, c->tconst, c->mixed ? 1 : 0, c->st)) != cudaSuccess) return e;
-        c->launches += 1;
+        if (slot >= 0) {
+            A.tconst = (char *)c->tconst + (size_t)slot * kTconstStride;
+        } else {
+            A.tconst = c->tconst;
+            if ((e = launch_tile_consts(A, c->tconst, c->mixed ? 1 : 0, c->st)) != cudaSuccess) return e;
+            c->launches += 1;
+        }
     }
     bool prof = c->profiling && c->ev_used < 5;
     if (prof) cudaEventRecord(c->ev[c->ev_used][0], c->st);
@@ -683,23 +696,36 @@ static cudaError_t run_rk(afns_ctx *c)
     // (u(0) = u^n enters every combination at time 0)
     double ct[5] = {0.0};
     for (int s = 1; s < 5; ++s) ct[s] = kRK_a[s - 1][s - 1] * ct[s - 1] + kRK_b[s - 1];
-    cudaError_t e;
+    StageCoef ks[5];
     // u1 = u0 + b0 dt L(u0)
     k.a0 = 0; k.a1 = 1; k.a2 = 0; k.cl = kRK_b[0]; k.ct = ct[0];
-    if ((e = run_stage(c, c->U[0], c->U[1], k, nullptr)) != cudaSuccess) return e;
+    ks[0] = k;
     // u2 = a10 u0 + a11 u1 + b1 dt L(u1)
     k.a0 = kRK_a[1][0]; k.a1 = kRK_a[1][1]; k.cl = kRK_b[1]; k.ct = ct[1];
-    if ((e = run_stage(c, c->U[1], c->U[2], k, nullptr)) != cudaSuccess) return e;
+    ks[1] = k;
     // u3 = a20 u0 + a22 u2 + b2 dt L(u2)
     k.a0 = kRK_a[2][0]; k.a1 = kRK_a[2][2]; k.cl = kRK_b[2]; k.ct = ct[2];
-    if ((e = run_stage(c, c->U[2], c->U[1], k, nullptr)) != cudaSuccess) return e;
+    ks[2] = k;
     // u4 = a30 u0 + a33 u3 + b3 dt L(u3); acc = a42 u2 + a43 u3 + b43 dt L(u3)
     k.a0 = kRK_a[3][0]; k.a1 = kRK_a[3][3]; k.cl = kRK_b[3]; k.ct = ct[3];
     k.acc = 1; k.b2 = kRK_a[4][2]; k.b1 = kRK_a[4][3]; k.bl = kRK_b43;
-    if ((e = run_stage(c, c->U[1], c->U[3], k, nullptr)) != cudaSuccess) return e;
+    ks[3] = k;
     // u5 = acc + a44 u4 + b4 dt L(u4)
     k.acc = 0; k.a0 = 0; k.a2 = 1; k.a1 = kRK_a[4][4]; k.cl = kRK_b[4]; k.ct = ct[4];
-    return run_stage(c, c->U[3], c->U[1], k, nullptr);
+    ks[4] = k;
+    cudaError_t e;
+    int slot0 = -1;
+    if (c->dim == 2) {   // the tile constants of all five stages in one launch
+        if ((e = launch_tile_consts5(base_args(c), ks, c->tconst, kTconstStride, c->mixed ? 1 : 0, c->st)) != cudaSuccess)
+            return e;
+        c->launches += 1;
+        slot0 = 0;
+    }
+    void *const in[5] = {c->U[0], c->U[1], c->U[2], c->U[1], c->U[3]};
+    void *const out[5] = {c->U[1], c->U[2], c->U[1], c->U[3], c->U[1]};
+    for (int st = 0; st < 5; ++st)
+        if ((e = run_stage(c, in[st], out[st], ks[st], nullptr, slot0 < 0 ? -1 : st)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 static af_status read_ctl(afns_ctx *c)

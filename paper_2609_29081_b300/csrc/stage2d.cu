@@ -11,12 +11,8 @@ namespace afns {
 template <class S>
 cudaError_t launch_ghost2d(const Layout &L, S *buf, cudaStream_t st)
 {
-    for (int pass = 0; pass < 2; ++pass) {
-        int span = pass == 0 ? (L.n2 + 1) : (L.n1 + 5);
-        int total = 4 * span * 5;
-        int blocks = (total + 255) / 256;
-        k_ghost2d<S><<<blocks, 256, 0, st>>>(L, buf, pass);
-    }
+    const int total = 4 * 5 * ((L.n2 + 1) + (L.n1 + 5));
+    k_ghost2d_once<S><<<(total + 255) / 256, 256, 0, st>>>(L, buf);
     return cudaGetLastError();
 }
 
@@ -72,6 +68,16 @@ cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, d
 {
     k_dt_partial2d<double><<<nparts, 256, 0, st>>>(L, buf, gamma, mu, Pr, cfl_c, cfl_v, partial);
     k_dt_final<<<1, 256, 0, st>>>(partial, nparts, ctl, clip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_consts5(const StageArgs &A, const StageCoef *ks, void *out, int stride_bytes, int fp32,
+                                cudaStream_t st)
+{
+    StageCoef5 k5;
+    for (int s = 0; s < 5; ++s) k5.k[s] = ks[s];
+    if (fp32) k_tile_consts5<float><<<1, 32, 0, st>>>(A, k5, (char *)out, stride_bytes);
+    else k_tile_consts5<double><<<1, 32, 0, st>>>(A, k5, (char *)out, stride_bytes);
     return cudaGetLastError();
 }
 

@@ -8,46 +8,67 @@
 namespace afns {
 
 // ---------------------------------------------------------------------------
-// Ghost fill: two ghost layers, x pass on interior rows then y pass on all
-// columns (periodic wrap, wall / symmetry / transmissive mirror).
+// Ghost fill: two ghost layers (periodic wrap, wall / symmetry / transmissive
+// mirror, moving-wall shift), in one launch.
 // ---------------------------------------------------------------------------
+// Ghost value of (i, j) in direction l from its image (si, sj), which is read
+// from buf: mirror signs, then the moving-wall shift of side `side`.
 template <class S>
-__global__ void k_ghost2d(Layout L, S *buf, int pass)
+__device__ __forceinline__ void ghost_from_image(const Layout &L, const S *buf, int site, int si, int sj, int l,
+                                                 int side, S v[4])
 {
-    const int nsite = 4;
-    // x pass: (site, row j in [0, n2], ghost column g in 0..4)
-    // y pass: (site, column i in [-2, n1+2], ghost row g in 0..4)
-    int span = pass == 0 ? (L.n2 + 1) : (L.n1 + 5);
-    int total = nsite * span * 5;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        int g = t % 5;
-        int r = (t / 5) % span;
-        int site = t / (5 * span);
-        bool ptx = site == 1 || site == 3;  // xe, vertex are point-like in x
-        bool pty = site == 2 || site == 3;  // ye, vertex are point-like in y
-        int side, i, j, si, sj, l;
-        if (pass == 0) {
+    const int kind = L.bc[2 * l + side];
+    for (int c = 0; c < 4; ++c) {
+        v[c] = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
+        if (mirror_sign(kind, l, c, 2) < 0) v[c] = -v[c];
+    }
+    moving_wall_ghost(L, 2 * l + side, v);
+}
+
+// Ghost fill in one launch, with the values of an x pass followed by a y pass:
+// the x ghosts of the rows that are not y ghosts, and the y-ghost rows over all
+// columns, where a column that is itself an x ghost takes the x transform of its
+// x image (the value an x pass would have stored there), then the y transform.
+template <class S>
+__global__ void k_ghost2d_once(Layout L, S *buf)
+{
+    const int nx = 4 * (L.n2 + 1) * 5, ny = 4 * (L.n1 + 5) * 5;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nx + ny; t += gridDim.x * blockDim.x) {
+        const bool xpass = t < nx;
+        const int u = xpass ? t : t - nx, span = xpass ? (L.n2 + 1) : (L.n1 + 5);
+        const int g = u % 5, r = (u / 5) % span, site = u / (5 * span);
+        const bool ptx = site == 1 || site == 3, pty = site == 2 || site == 3;
+        S v[4];
+        int i, j;
+        if (xpass) {
             j = r;
             if (j > L.n2 - 1 + (pty ? 1 : 0)) continue;
+            int sdy;
+            ghost_image(j, L.n2, pty, L.bc[2], L.bc[3], &sdy);
+            if (sdy >= 0) continue;   // a y-ghost row: the y items write it
             i = g < 2 ? g - 2 : L.n1 + (g - 2);
-            si = ghost_image(i, L.n1, ptx, L.bc[0], L.bc[1], &side);
-            sj = j;
-            l = 0;
+            int side;
+            const int si = ghost_image(i, L.n1, ptx, L.bc[0], L.bc[1], &side);
+            if (side < 0) continue;
+            ghost_from_image(L, buf, site, si, j, 0, side, v);
         } else {
             i = r - 2;
             j = g < 2 ? g - 2 : L.n2 + (g - 2);
-            sj = ghost_image(j, L.n2, pty, L.bc[2], L.bc[3], &side);
-            si = i;
-            l = 1;
+            int side;
+            const int sj = ghost_image(j, L.n2, pty, L.bc[2], L.bc[3], &side);
+            if (side < 0) continue;
+            int sdx;
+            const int si = ghost_image(i, L.n1, ptx, L.bc[0], L.bc[1], &sdx);
+            if (sdx < 0) {
+                ghost_from_image(L, buf, site, i, sj, 1, side, v);
+            } else {
+                S w[4];
+                ghost_from_image(L, buf, site, si, sj, 0, sdx, w);   // the x pass's value at (i, sj)
+                const int kind = L.bc[2 + side];
+                for (int c = 0; c < 4; ++c) v[c] = mirror_sign(kind, 1, c, 2) < 0 ? -w[c] : w[c];
+                moving_wall_ghost(L, 2 + side, v);
+            }
         }
-        if (side < 0) continue;
-        int kind = L.bc[2 * l + side];
-        S v[4];
-        for (int c = 0; c < 4; ++c) {
-            v[c] = buf[plane_of(L, site, c) + cell_off(L, si, sj)];
-            if (mirror_sign(kind, l, c, 2) < 0) v[c] = -v[c];
-        }
-        moving_wall_ghost(L, 2 * l + side, v);
         for (int c = 0; c < 4; ++c) buf[plane_of(L, site, c) + cell_off(L, i, j)] = v[c];
     }
 }
@@ -246,6 +267,21 @@ template <class R>
 __global__ void k_tile_consts(StageArgs A, TileConst<R> *out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) tile_const_init<R>(*out, A, A.ctl->dt);
+}
+
+// The constants of all five stages of a step in one launch (thread s: stage s),
+// written stride_bytes apart.
+struct StageCoef5 {
+    StageCoef k[5];
+};
+template <class R>
+__global__ void k_tile_consts5(StageArgs A, StageCoef5 ks, char *out, int stride_bytes)
+{
+    const int s = threadIdx.x;
+    if (blockIdx.x != 0 || s >= 5) return;
+    StageArgs B = A;
+    B.k = ks.k[s];
+    tile_const_init<R>(*reinterpret_cast<TileConst<R> *>(out + (size_t)s * stride_bytes), B, A.ctl->dt);
 }
 
 // (u, v, T, c) of a lattice node, one reciprocal of rho: u = m_x/rho,
