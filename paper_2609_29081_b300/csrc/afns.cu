@@ -40,7 +40,6 @@ cudaError_t launch_exact_ghost1d_fp64(const Layout &L, double *buf, const Ctl *c
 cudaError_t launch_exact_ghost1d_f32(const Layout &L, float *buf, const Ctl *ctl, double ct, ExactParams ep,
                                      cudaStream_t st);
 cudaError_t launch_validate1d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st);
-cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st);
 cudaError_t launch_stage1d_mixed(const StageArgs &A, cudaStream_t st);
 cudaError_t launch_dt1d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
@@ -51,7 +50,7 @@ cudaError_t launch_tile_consts5(const StageArgs &A, const StageCoef *ks, void *o
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st);
-cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h,
+cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h, int *flag,
                                    cudaStream_t st);
 cudaError_t launch_tile_consts(const StageArgs &A, void *out, int fp32, cudaStream_t st);
 cudaError_t launch_to_f64(const Layout &L, const float *src, double *dst, int use_lo, cudaStream_t st);
@@ -577,7 +576,7 @@ extern "C" af_status af_set_state_f32(afns_ctx *c, const float *const site[4], i
     // host arrays: one contiguous copy per site into the staging area, then a
     // kernel spreads them over the pitched planes (device arrays: the kernel
     // reads them in place)
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
     size_t off = 0;
     for (int s = 0; s < c->L.nsite && e == cudaSuccess; ++s) {
         if (!site[s]) return fail(c, AF_EINVAL, "null site pointer");
@@ -591,15 +590,14 @@ extern "C" af_status af_set_state_f32(afns_ctx *c, const float *const site[4], i
             src = stg;
             off += align256(bytes);
         }
-        if (e == cudaSuccess) e = launch_unpack_site_f32(c->L, src, (float *)c->U[0], s, w, h, c->st);
+        if (e == cudaSuccess) e = launch_unpack_site_f32(c->L, src, (float *)c->U[0], s, w, h, c->flag, c->st);
     }
     if (e != cudaSuccess) return cuda_check(c, e, "state upload");
     float *lo = (float *)c->U[0] + comp_plane(c->L, 0);
     e = cudaMemsetAsync(lo, 0, sizeof(float) * (size_t)c->L.nc * c->L.plane, c->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
-    if (e == cudaSuccess)
-        e = c->dim == 1 ? launch_validate1d_f32(c->L, (const float *)c->U[0], c->gamma, c->flag, c->st)
-                        : launch_validate2d_f32(c->L, (const float *)c->U[0], c->gamma, c->flag, c->st);
+    // 2D: the unpack pass has checked the values; 1D: one validation pass
+    if (e == cudaSuccess && c->dim == 1)
+        e = launch_validate1d_f32(c->L, (const float *)c->U[0], c->gamma, c->flag, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_check(c, e, "af_set_state_f32");

@@ -110,10 +110,6 @@ cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double ga
     return launch_validate2d<double>(L, buf, gamma, flag, st);
 }
 
-cudaError_t launch_validate2d_f32(const Layout &L, const float *buf, double gamma, int *flag, cudaStream_t st)
-{
-    return launch_validate2d<float>(L, buf, gamma, flag, st);
-}
 
 }  // namespace afns
 
@@ -166,26 +162,42 @@ __global__ void k_to_f64(const float *src, double *dst, long long plane, int npl
 
 // One DoF site's packed array (components in turn, x fastest, no ghosts) into the
 // pitched planes of a state buffer: one coalesced pass, so that a host upload is
-// one contiguous copy per site instead of one strided copy per component.
+// one contiguous copy per site instead of one strided copy per component. In 2D
+// the same pass checks the uploaded values (bit 1 of *flag: a DoF that is not
+// finite, has rho <= 0 or p <= 0; bit 2: a periodic duplicate point that differs
+// from its partner), so no separate validation pass reads the state again.
 template <class T>
-__global__ void k_unpack_site(Layout L, const T *src, T *buf, int site, int w, int h)
+__global__ void k_unpack_site(Layout L, const T *src, T *buf, int site, int w, int h, int *flag)
 {
-    const long long wh = (long long)w * h, n = (long long)L.nc * wh;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e / wh);
-        const long long r = e - c * wh;
-        const int j = (int)(r / w), i = (int)(r - (long long)j * w);
+    const int wh = w * h, nc = L.nc;
+    const bool ptx = site == 1 || site == 3, pty = site == 2 || site == 3;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < wh; e += gridDim.x * blockDim.x) {
+        const int j = e / w, i = e - j * w;
         const long long off = L.dim == 2 ? cell_off(L, i, j) : 2 + i;
-        buf[plane_of(L, site, c) + off] = src[e];
+        double U[4];
+        for (int c = 0; c < nc; ++c) {
+            const T v = src[(long long)c * wh + e];
+            buf[plane_of(L, site, c) + off] = v;
+            U[c] = (double)v;
+        }
+        if (L.dim != 2 || !flag) continue;
+        if (!admissible_input2(U)) atomicOr(flag, 1);
+        const int si = (ptx && i == L.n1 && L.bc[0] == BC_PERIODIC) ? 0 : i;
+        const int sj = (pty && j == L.n2 && L.bc[2] == BC_PERIODIC) ? 0 : j;
+        if (si != i || sj != j) {
+            const int e2 = sj * w + si;
+            for (int c = 0; c < nc; ++c)
+                if (src[(long long)c * wh + e2] != src[(long long)c * wh + e]) atomicOr(flag, 2);
+        }
     }
 }
 
-cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h,
+cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h, int *flag,
                                    cudaStream_t st)
 {
-    const long long n = (long long)L.nc * w * h;
+    const long long n = (long long)w * h;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 148 * 16);
-    k_unpack_site<float><<<blocks, 256, 0, st>>>(L, src, buf, site, w, h);
+    k_unpack_site<float><<<blocks, 256, 0, st>>>(L, src, buf, site, w, h, flag);
     return cudaGetLastError();
 }
 

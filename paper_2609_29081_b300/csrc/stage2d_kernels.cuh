@@ -1089,6 +1089,20 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
 // ---------------------------------------------------------------------------
 // CFL time step of Eq. (13): per-block maxima, then one finalising block.
 // ---------------------------------------------------------------------------
+// Cell (i, j) of linear cell index t (x fastest); 32-bit division when the grid
+// allows it (64-bit division is a long instruction sequence).
+__device__ __forceinline__ void cell_ij(const Layout &L, long long t, bool small, int &i, int &j)
+{
+    if (small) {
+        const int tt = (int)t;
+        j = tt / L.n1;
+        i = tt - j * L.n1;
+    } else {
+        j = (int)(t / L.n1);
+        i = (int)(t - (long long)j * L.n1);
+    }
+}
+
 template <class S>
 __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, double Pr, double cfl_c,
                                double cfl_v, double *partial)
@@ -1096,6 +1110,7 @@ __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, 
     double m1 = 0.0, m2 = 0.0;
     const long long nc = (long long)L.n1 * L.n2;
     const double g1 = gamma - 1.0;
+    const bool small = nc < (1ll << 31);   // 32-bit index arithmetic suffices
     if constexpr (sizeof(S) == 4) {
         // mixed path: FP32 arithmetic with one reciprocal per cell (the step size
         // needs no more than FP32 accuracy); maxima merged in FP64 below
@@ -1106,7 +1121,8 @@ __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, 
         float f1 = 0.f, f2 = 0.f;
         for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
              t += (long long)gridDim.x * blockDim.x) {
-            int i = (int)(t % L.n1), j = (int)(t / L.n1);
+            int i, j;
+            cell_ij(L, t, small, i, j);
             long long off = cell_off(L, i, j);
             float rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
             float my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
@@ -1121,7 +1137,8 @@ __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, 
     } else {
         for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
              t += (long long)gridDim.x * blockDim.x) {
-            int i = (int)(t % L.n1), j = (int)(t / L.n1);
+            int i, j;
+            cell_ij(L, t, small, i, j);
             long long off = cell_off(L, i, j);
             double rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
             double my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];

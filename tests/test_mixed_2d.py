@@ -151,3 +151,28 @@ def test_f32_state_io():
     F = Solver.from_workload(w, precision=FP64)
     with pytest.raises(AfnsError):
         F.set_state_f32(s32)
+
+
+def test_f32_upload_checks_values():
+    """An FP32 upload is checked as it is unpacked: a negative density, a negative
+    pressure or a NaN anywhere, and a periodic duplicate point that differs from
+    its partner, are refused; a clean state after a refused one is accepted
+    (the check starts from zero on every call)."""
+    from paper_2609_29081_b300 import MIXED, AfnsError, Solver
+    w = W.random_smooth_2d((33, 17), seed=4)
+    S = Solver.from_workload(w, precision=MIXED)
+    n1, n2 = w.n
+    avg = 4 * n1 * n2
+    xe = avg + 4 * n2 * (n1 + 1)
+    for where, value in ((5, -1.0), (avg + 7, np.nan), (3 * n1 * n2 + 11, -50.0)):
+        bad = w.state.astype(np.float32)
+        bad[where] = value
+        with pytest.raises(AfnsError):
+            S.set_state_f32(bad)
+        S.set_state_f32(w.state.astype(np.float32))
+    bad = w.state.astype(np.float32)
+    bad[xe - 4 * n2 * (n1 + 1) + n1] *= 1.001     # x-edge density at i = n1 (duplicate of i = 0), row 0
+    with pytest.raises(AfnsError):
+        S.set_state_f32(bad)
+    S.set_state_f32(w.state.astype(np.float32))
+    assert np.array_equal(S.get_state_f32(), w.state.astype(np.float32))
