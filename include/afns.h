@@ -102,6 +102,9 @@ typedef struct {
     double ex_uinf;    /* AF_BC_EXACT: translation velocity of the shock (default 0.2) */
     int threads;       /* threads per CTA of the 2D stage kernel: 128 (default) or 256;
                           af_tune may change tile_x / tile_y / threads */
+    int kappa_off;     /* 1: no heat conduction, kappa = 0 exactly (the Sec. 4 first problem
+                          of Stokes), and no conduction term in the CFL bound of Eq. (13);
+                          single-problem contexts (af_create); default 0 */
 } af_opts;
 
 /* Fill *o with the paper's defaults for a problem of dimension dim (except C^v

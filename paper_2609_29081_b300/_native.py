@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("cfl_c", ctypes.c_double), ("cfl_v", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("source", ctypes.c_int), ("src_p0", ctypes.c_double),
-                ("ex_M0", ctypes.c_double), ("ex_uinf", ctypes.c_double), ("threads", ctypes.c_int)]
+                ("ex_M0", ctypes.c_double), ("ex_uinf", ctypes.c_double), ("threads", ctypes.c_int),
+                ("kappa_off", ctypes.c_int)]
 
 
 _lib = None

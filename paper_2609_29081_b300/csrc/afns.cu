@@ -90,6 +90,7 @@ struct afns_ctx {
     int n1 = 0, n2 = 1;
     double lo[2] = {0, 0}, hi[2] = {1, 1};
     double gamma = 1.4, mu = 0, Pr = 1, kappa = 0;
+    double Pr_cfl = 1;           // Pr in the CFL bound (infinite without heat conduction)
     int bc[4] = {0, 0, 0, 0};
     af_opts opts{};
     cudaStream_t st = nullptr;
@@ -255,6 +256,7 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
     if (o->source != AF_SRC_NONE && o->source != AF_SRC_TAYLOR_GREEN) return *why = "unknown source", AF_EINVAL;
     if (o->source == AF_SRC_TAYLOR_GREEN && g->dim != 2)
         return *why = "the Taylor-Green source is two-dimensional", AF_EINVAL;
+    if (o->kappa_off != 0 && o->kappa_off != 1) return *why = "kappa_off must be 0 or 1", AF_EINVAL;
     if (o->threads != 0 && o->threads != 128 && o->threads != 256)
         return *why = "threads per CTA must be 128 or 256", AF_EINVAL;
     if (!(o->cfl_c > 0) || !(o->cfl_v > 0) || !(o->eps > 0) || o->max_halvings < 0)
@@ -283,6 +285,7 @@ af_status af_opts_default(int dim, af_opts *o)
     o->ex_M0 = 3.0;
     o->ex_uinf = 0.2;
     o->threads = 128;
+    o->kappa_off = 0;
     return AF_OK;
 }
 
@@ -326,7 +329,8 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->gamma = gamma;
     c->mu = mu;
     c->Pr = Pr;
-    c->kappa = gamma * mu / ((gamma - 1.0) * Pr);
+    c->kappa = opts->kappa_off ? 0.0 : gamma * mu / ((gamma - 1.0) * Pr);
+    c->Pr_cfl = opts->kappa_off ? INFINITY : Pr;
     for (int k = 0; k < 4; ++k) c->bc[k] = grid->dim == 2 || k < 2 ? bc->side[k] : AF_BC_PERIODIC;
     c->opts = *opts;
     c->st = (cudaStream_t)cuda_stream;
@@ -764,15 +768,15 @@ static cudaError_t launch_dt(afns_ctx *c, int clip)
 {
     c->launches += 2;
     if (c->dim == 1 && c->mixed)
-        return launch_dt1d_f32(c->L, (const float *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+        return launch_dt1d_f32(c->L, (const float *)c->U[0], c->gamma, c->mu, c->Pr_cfl, c->opts.cfl_c, c->opts.cfl_v,
                                c->partial, c->nparts, c->ctl, clip, c->st);
     if (c->dim == 1)
-        return launch_dt1d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+        return launch_dt1d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr_cfl, c->opts.cfl_c, c->opts.cfl_v,
                                 c->partial, c->nparts, c->ctl, clip, c->st);
     if (c->mixed)
-        return launch_dt2d_f32(c->L, (const float *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+        return launch_dt2d_f32(c->L, (const float *)c->U[0], c->gamma, c->mu, c->Pr_cfl, c->opts.cfl_c, c->opts.cfl_v,
                                c->partial, c->nparts, c->ctl, clip, c->st);
-    return launch_dt2d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr, c->opts.cfl_c, c->opts.cfl_v,
+    return launch_dt2d_fp64(c->L, (const double *)c->U[0], c->gamma, c->mu, c->Pr_cfl, c->opts.cfl_c, c->opts.cfl_v,
                             c->partial, c->nparts, c->ctl, clip, c->st);
 }
 

@@ -80,3 +80,8 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), ctypes.byref(o), None, None, 0,
                      ctypes.byref(ctx))
     assert st == N.AF_EINVAL and not ctx.value
+    assert o.kappa_off == 0
+    o.threads, o.kappa_off = 128, 2
+    st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), ctypes.byref(o), None, None, 0,
+                     ctypes.byref(ctx))
+    assert st == N.AF_EINVAL and not ctx.value

@@ -183,3 +183,29 @@ def test_becker_strong_shock_limited(orc, prec):
     for U in W.split_sites(S.get_state(), 1, 400):
         p = (w.gamma - 1) * (U[2] - 0.5 * U[1] ** 2 / U[0])
         assert np.isfinite(U).all() and U[0].min() > 0 and p.min() > 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stokes_kappa_off_equals_vanishing_conduction(prec):
+    """af_opts.kappa_off removes heat conduction exactly (and its CFL term): with
+    Pr = 0.72 and kappa_off the strip evolves as with Pr = 1e30 (kappa 1e-30 of
+    mu) to 1e-12 of each component's scale after 20 CFL steps, and differently
+    from Pr = 0.72 with conduction on."""
+    from paper_2609_29081_b300 import FP64, MIXED, Solver
+    p = FP64 if prec == "fp64" else MIXED
+    w = W.stokes_first_problem(100, mu=1e-3)
+    ref = Solver.from_workload(w, precision=p)
+    ref.set_state(w.state)
+    off = Solver(w.dim, w.n, w.lo, w.hi, w.gamma, w.mu, 0.72, w.bc, precision=p, kappa_off=1)
+    off.set_state(w.state)
+    on = Solver(w.dim, w.n, w.lo, w.hi, w.gamma, w.mu, 0.72, w.bc, precision=p)
+    on.set_state(w.state)
+    for _ in range(20):
+        ref.step(0.0)
+        off.step(0.0)
+        on.step(0.0)
+    a, b, c = ref.get_state(), off.get_state(), on.get_state()
+    assert ref.t == off.t
+    err, where = max_rel_err(b, a, 2, w.n)
+    assert err < 1e-12, (err, where)
+    assert max_rel_err(c, a, 2, w.n)[0] > 1e-9
