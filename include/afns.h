@@ -143,7 +143,9 @@ af_status af_get_state(afns_ctx *ctx, double *const site[4], int on_device, doub
  * half the bytes of the FP64 calls. af_set_state_f32 starts the compensation
  * words of the cell averages at zero and validates like af_set_state;
  * af_get_state_f32 returns every value rounded to FP32 (for a cell average, the
- * rounding of its compensated value hi + lo).
+ * rounding of its compensated value hi + lo). Host arrays go through the
+ * context's staging area as one contiguous copy per site; device arrays are read
+ * or written in place. Both calls synchronise the context's stream.
  */
 af_status af_set_state_f32(afns_ctx *ctx, const float *const site[4], int on_device, double t);
 af_status af_get_state_f32(afns_ctx *ctx, float *const site[4], int on_device, double *t);
