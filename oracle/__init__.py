@@ -65,6 +65,8 @@ def lib():
         L.orc_dt_max.argtypes = [pp, dp]
         L.orc_dt_max.restype = ctypes.c_double
         L.orc_step.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int, dp, ip]
+        L.orc_point_low_order.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+        L.orc_point_low_order.restype = None
         L.orc_advance.argtypes = [pp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ip, ip]
         L.orc_rk_table.argtypes = [dp, dp]
@@ -136,6 +138,14 @@ def residual(P, state, dt, with_theta=False):
 def dt_max(P, state):
     s = np.ascontiguousarray(state, dtype=np.float64)
     return lib().orc_dt_max(ctypes.byref(P), _dp(s))
+
+
+def point_low_order(P, state, dt, a0, a1=0):
+    """Low-order point update (reading R7) of lattice node (a0, a1)."""
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    out = np.zeros(P.dim + 2)
+    lib().orc_point_low_order(ctypes.byref(P), _dp(s), dt, a0, a1, _dp(out))
+    return out
 
 
 def step(P, state, dt, max_halvings=30):

@@ -956,6 +956,22 @@ static void source_cell(const orc_problem *P, double x0, double y0, double hx, d
         }
 }
 
+/* The low-order point update of lattice node (a0, a1) (reading R7), exposed so
+ * that tests can pin it: the lattice is prepared exactly as for a residual
+ * (ghosts, centres, node primitives), then point_low_order. */
+void orc_point_low_order(const orc_problem *P, const double *state, double dt, int a0, int a1, double *UL)
+{
+    grid_t G, *g = &G;
+    grid_init(g, P);
+    unpack(g, state);
+    fill_ghosts(g);
+    exact_ghosts(g, P->time);
+    centres(g);
+    node_prims(g);
+    point_low_order(g, a0, a1, dt, UL);
+    grid_free(g);
+}
+
 int orc_residual(const orc_problem *P, const double *state, double dt, double *L, double *theta_s,
                  double *theta_pp, int *notpp)
 {

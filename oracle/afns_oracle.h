@@ -85,6 +85,11 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
 /* CFL time step of Eq. (13) on the cell averages. */
 double orc_dt_max(const orc_problem *P, const double *state);
 
+/* Low-order point update (Sec. 3.4, reading R7) of lattice node (a0, a1) (a1 = 0
+ * in 1D; even lattice indices are point nodes), as the limiter would form it for
+ * step dt; UL receives dim + 2 conservative values. */
+void orc_point_low_order(const orc_problem *P, const double *state, double dt, int a0, int a1, double *UL);
+
 /* One SSP-RK54 step of size dt with the halving restart of Remark 3.2. */
 int orc_step(const orc_problem *P, double *state, double dt, int max_halvings,
              double *dt_taken, int *halvings);

@@ -797,3 +797,78 @@ def test_moving_plate_matches_erfc(orc):
     for k in (2, 3):                      # y-edge points and vertices on the wall row j = 0
         wall = parts[k][:, 0]
         assert np.abs(wall[1] / wall[0] - 0.1).max() < 1e-15 and np.abs(wall[2]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Low-order point update (Sec. 3.4, reading R7) against a textbook restatement
+# ---------------------------------------------------------------------------
+
+def _half_lattice_1d(state, n):
+    """Lattice values of a 1D state: point values at even nodes, unlimited cell
+    centres from Simpson's rule (Sec. 2.1) at odd nodes."""
+    avg, pts = W.split_sites(state, 1, n)
+    lat = np.zeros((3, 2 * n + 1))
+    lat[:, 0::2] = pts
+    lat[:, 1::2] = (6.0 * avg - pts[:, :-1] - pts[:, 1:]) / 4.0
+    return lat
+
+
+def _rusanov_point_update(lat, a, dt, h, g, mu, Pr):
+    """First-order LLF (Rusanov) update of lattice node a on the half lattice
+    (spacing h/2) with the total flux F^c - F^v: the viscous flux from central
+    differences of Z = (u, T = p/rho) over the neighbouring nodes, and the
+    numerical viscosity alpha + beta of Eq. (19) with beta from the bound b of
+    Lemma 3.2."""
+    kappa = g * mu / ((g - 1.0) * Pr)
+
+    def prim(U):
+        rho, m, E = U
+        u = m / rho
+        p = (g - 1.0) * (E - 0.5 * m * u)
+        return rho, u, p
+
+    def node(k):
+        U = lat[:, k]
+        rho, u, p = prim(U)
+        _, ue, pe = prim(lat[:, k + 1])
+        _, uw, pw = prim(lat[:, k - 1])
+        ux, Tx = (ue - uw) / h, (pe / lat[0, k + 1] - pw / lat[0, k - 1]) / h
+        tau, q = 4.0 / 3.0 * mu * ux, -kappa * Tx
+        F = np.array([U[1], U[1] * u + p, (U[2] + p) * u]) - np.array([0.0, tau, u * tau - q])
+        e = p / ((g - 1.0) * rho)
+        b = (np.sqrt(rho ** 2 * q ** 2 + 2 * rho ** 2 * e * tau ** 2) + rho * abs(q)) / (2 * rho ** 2 * e)
+        return U, F, abs(u) + np.sqrt(g * p / rho), b
+
+    def flux(A, B):
+        UA, FA, aA, bA = node(A)
+        UB, FB, aB, bB = node(B)
+        return 0.5 * (FA + FB) - 0.5 * (max(aA, aB) + max(bA, bB)) * (UB - UA)
+
+    return lat[:, a] - dt / (0.5 * h) * (flux(a, a + 1) - flux(a - 1, a))
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.05])
+def test_point_low_order_update_is_rusanov_on_the_half_lattice(orc, mu):
+    """Reading R7 (the paper names the low-order point update only through a
+    cited stencil): the oracle's update equals a direct first-order LLF step on
+    the half lattice, inviscid and viscous, at every interior point node, to
+    roundoff. A wrong spacing (h instead of h/2), a dropped viscous bound beta,
+    a sign error in F^v or neighbours taken from the point lattice only would
+    each fail."""
+    n, g, Pr = 24, 1.4, 0.72
+    lo, hi = (0.0,), (2 * np.pi,)
+
+    def f(x):
+        return 1.0 + 0.3 * np.sin(x), [0.8 + 0.4 * np.cos(2 * x)], 1.0 + 0.2 * np.sin(3 * x + 1.0)
+
+    state = W.project(1, (n,), lo, hi, g, f)
+    P = orc.problem(1, n, lo=lo, hi=hi, mu=mu, Pr=Pr, gamma=g, limiter=0)
+    dt = 0.4 * orc.dt_max(P, state)
+    h = (hi[0] - lo[0]) / n
+    lat = _half_lattice_1d(state, n)
+    worst = 0.0
+    for a in range(2, 2 * n - 1, 2):
+        ref = _rusanov_point_update(lat, a, dt, h, g, mu, Pr)
+        got = orc.point_low_order(P, state, dt, a)
+        worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
+    assert worst < 1e-13, worst
