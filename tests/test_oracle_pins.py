@@ -872,3 +872,79 @@ def test_point_low_order_update_is_rusanov_on_the_half_lattice(orc, mu):
         got = orc.point_low_order(P, state, dt, a)
         worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
     assert worst < 1e-13, worst
+
+
+def _half_lattice_2d(state, n1, n2):
+    """Lattice values [c, b, a] of a 2D state: vertices at (even, even), x-edge
+    points at (even a, odd b), y-edge points at (odd a, even b), unlimited cell
+    centres from the 2D Simpson rule (Sec. 2.2) at (odd, odd)."""
+    avg, xe, ye, vx = W.split_sites(state, 2, n1, n2)
+    lat = np.zeros((4, 2 * n2 + 1, 2 * n1 + 1))
+    lat[:, 0::2, 0::2] = vx
+    lat[:, 1::2, 0::2] = xe
+    lat[:, 0::2, 1::2] = ye
+    edges = xe[:, :, :-1] + xe[:, :, 1:] + ye[:, :-1, :] + ye[:, 1:, :]
+    verts = vx[:, :-1, :-1] + vx[:, :-1, 1:] + vx[:, 1:, :-1] + vx[:, 1:, 1:]
+    lat[:, 1::2, 1::2] = (36.0 * avg - 4.0 * edges - verts) / 16.0
+    return lat
+
+
+def test_point_low_order_update_2d_is_rusanov_on_the_half_lattice(orc):
+    """The same pin in 2D: both directions' LLF flux differences on the half
+    lattice, the viscous fluxes from central differences of (u, v, T) in both
+    directions (so the transverse stress tau_xy and the full |tau_l| of the bound
+    b_l of Lemma 3.2 enter), at interior point nodes of all three kinds."""
+    n1, n2, g, mu, Pr = 12, 10, 1.4, 0.03, 0.72
+    w = W.random_smooth_2d((n1, n2), seed=7, mu=mu)
+    P = orc.problem(2, n1, n2, lo=w.lo, hi=w.hi, mu=mu, Pr=Pr, bc=w.bc, gamma=g, limiter=0)
+    dt = 0.4 * orc.dt_max(P, w.state)
+    h = [(w.hi[0] - w.lo[0]) / n1, (w.hi[1] - w.lo[1]) / n2]
+    lat = _half_lattice_2d(w.state, n1, n2)
+    kappa = g * mu / ((g - 1.0) * Pr)
+
+    def prim(a, b):
+        rho, mx, my, E = lat[:, b, a]
+        u, v = mx / rho, my / rho
+        return rho, u, v, (g - 1.0) * (E - 0.5 * (mx * u + my * v))
+
+    def node(a, b, l):
+        U = lat[:, b, a]
+        rho, u, v, p = prim(a, b)
+        grads = []
+        for (da, db), hm in (((1, 0), h[0]), ((0, 1), h[1])):
+            _, ue, ve, pe = prim(a + da, b + db)
+            _, uw, vw, pw = prim(a - da, b - db)
+            Te, Tw = pe / lat[0, b + db, a + da], pw / lat[0, b - db, a - da]
+            grads.append(((ue - uw) / hm, (ve - vw) / hm, (Te - Tw) / hm))
+        (ux, vx_, Tx), (uy, vy, Ty) = grads
+        div = ux + vy
+        txx, tyy, txy = mu * (2 * ux - 2 / 3 * div), mu * (2 * vy - 2 / 3 * div), mu * (uy + vx_)
+        if l == 0:
+            q, t1, t2, ul = -kappa * Tx, txx, txy, u
+            Fc = np.array([U[1], U[1] * u + p, U[2] * u, (U[3] + p) * u])
+        else:
+            q, t1, t2, ul = -kappa * Ty, txy, tyy, v
+            Fc = np.array([U[2], U[1] * v, U[2] * v + p, (U[3] + p) * v])
+        Fv = np.array([0.0, t1, t2, u * t1 + v * t2 - q])
+        e = p / ((g - 1.0) * rho)
+        b_ = (np.sqrt(rho ** 2 * q ** 2 + 2 * rho ** 2 * e * (t1 ** 2 + t2 ** 2)) + rho * abs(q)) / (2 * rho ** 2 * e)
+        return U, Fc - Fv, abs(ul) + np.sqrt(g * p / rho), b_
+
+    def flux(A, B, l):
+        UA, FA, aA, bA = node(*A, l)
+        UB, FB, aB, bB = node(*B, l)
+        return 0.5 * (FA + FB) - 0.5 * (max(aA, aB) + max(bA, bB)) * (UB - UA)
+
+    worst, kinds = 0.0, set()
+    for b in range(2, 2 * n2 - 1):
+        for a in range(2, 2 * n1 - 1):
+            if a % 2 and b % 2:
+                continue   # a cell centre, not a point
+            ref = lat[:, b, a].copy()
+            for l, (da, db) in enumerate(((1, 0), (0, 1))):
+                ref -= dt / (0.5 * h[l]) * (flux((a, b), (a + da, b + db), l) - flux((a - da, b - db), (a, b), l))
+            got = orc.point_low_order(P, w.state, dt, a, b)
+            worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
+            kinds.add((a % 2, b % 2))
+    assert kinds == {(0, 0), (0, 1), (1, 0)}
+    assert worst < 1e-13, worst
