@@ -67,6 +67,8 @@ def lib():
         L.orc_step.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int, dp, ip]
         L.orc_point_low_order.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
         L.orc_point_low_order.restype = None
+        L.orc_face_low_order.argtypes = [pp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.orc_face_low_order.restype = None
         L.orc_advance.argtypes = [pp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ip, ip]
         L.orc_rk_table.argtypes = [dp, dp]
@@ -145,6 +147,14 @@ def point_low_order(P, state, dt, a0, a1=0):
     s = np.ascontiguousarray(state, dtype=np.float64)
     out = np.zeros(P.dim + 2)
     lib().orc_point_low_order(ctypes.byref(P), _dp(s), dt, a0, a1, _dp(out))
+    return out
+
+
+def face_low_order(P, state, l, f0, f1=0):
+    """Low-order LLF face flux of Eq. (19) of face (f0, f1) in direction l."""
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    out = np.zeros(P.dim + 2)
+    lib().orc_face_low_order(ctypes.byref(P), _dp(s), l, f0, f1, _dp(out))
     return out
 
 

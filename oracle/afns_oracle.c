@@ -956,6 +956,38 @@ static void source_cell(const orc_problem *P, double x0, double y0, double hx, d
         }
 }
 
+/* Eq. (19): the LLF total flux of the face between cells L and R in direction l,
+ * from their total fluxes, wave speeds rho_l and viscous bounds b_l (Lemma 3.2). */
+static void face_llf(int nc, int l, const cellq_t *qL, const cellq_t *qR, const double *UbL, const double *UbR,
+                     double *FL)
+{
+    double al = fmax(qL->rho_l[l], qR->rho_l[l]);
+    double be = fmax(qL->b_l[l], qR->b_l[l]);
+    double lam = al + be;
+    for (int c = 0; c < nc; ++c) FL[c] = 0.5 * (qL->F[l][c] + qR->F[l][c]) - 0.5 * lam * (UbR[c] - UbL[c]);
+}
+
+/* The low-order face flux of Eq. (19) of face (f0, f1) in direction l (between
+ * cells f - e_l and f), exposed so that tests can pin it. */
+void orc_face_low_order(const orc_problem *P, const double *state, int l, int f0, int f1, double *FL)
+{
+    grid_t G, *g = &G;
+    grid_init(g, P);
+    unpack(g, state);
+    fill_ghosts(g);
+    exact_ghosts(g, P->time);
+    int L0, L1;
+    cell_step(l, -1, f0, f1, &L0, &L1);
+    cellq_t qL, qR;
+    cell_quantities(g, L0, L1, &qL);
+    cell_quantities(g, f0, f1, &qR);
+    double UbL[MAXC], UbR[MAXC];
+    cell_get(g, L0, L1, UbL);
+    cell_get(g, f0, f1, UbR);
+    face_llf(g->nc, l, &qL, &qR, UbL, UbR, FL);
+    grid_free(g);
+}
+
 /* The low-order point update of lattice node (a0, a1) (reading R7), exposed so
  * that tests can pin it: the lattice is prepared exactly as for a residual
  * (ghosts, centres, node primitives), then point_low_order. */
@@ -1033,12 +1065,8 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
                     cell_get(g, L0, L1, UbL);
                     cell_get(g, R0, R1, UbR);
                     /* low-order LLF total flux, Eq. (19) */
-                    double al = fmax(qL->rho_l[l], qR->rho_l[l]);
-                    double be = fmax(qL->b_l[l], qR->b_l[l]);
-                    double lam = al + be;
                     double FL[MAXC], dF[MAXC], FLs[MAXC];
-                    for (int c = 0; c < nc; ++c)
-                        FL[c] = 0.5 * (qL->F[l][c] + qR->F[l][c]) - 0.5 * lam * (UbR[c] - UbL[c]);
+                    face_llf(nc, l, qL, qR, UbL, UbR, FL);
                     /* smoothness-based blending, Sec. 3.2, Eq. (22) */
                     if (P->limiter == ORC_LIM_S_PP) {
                         double p1 = fmax(qL->phi1, qR->phi1), p2 = fmax(qL->phi2, qR->phi2);

@@ -90,6 +90,10 @@ double orc_dt_max(const orc_problem *P, const double *state);
  * step dt; UL receives dim + 2 conservative values. */
 void orc_point_low_order(const orc_problem *P, const double *state, double dt, int a0, int a1, double *UL);
 
+/* Low-order LLF total flux of Eq. (19) of face (f0, f1) in direction l, the face
+ * between cells f - e_l and f (f1 = 0 in 1D); FL receives dim + 2 values. */
+void orc_face_low_order(const orc_problem *P, const double *state, int l, int f0, int f1, double *FL);
+
 /* One SSP-RK54 step of size dt with the halving restart of Remark 3.2. */
 int orc_step(const orc_problem *P, double *state, double dt, int max_halvings,
              double *dt_taken, int *halvings);

@@ -948,3 +948,60 @@ def test_point_low_order_update_2d_is_rusanov_on_the_half_lattice(orc):
             kinds.add((a % 2, b % 2))
     assert kinds == {(0, 0), (0, 1), (1, 0)}
     assert worst < 1e-13, worst
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.03])
+def test_face_low_order_flux_is_llf_of_eq_19(orc, mu):
+    """Eq. (19) with Sec. 3.1's S (central differences of Z(U-bar) over the
+    neighbouring cells, reading R5): the oracle's low-order face flux equals a
+    direct restatement, F^c - F^v at both cells, numerical viscosity
+    max(rho_l) + max(b_l) of Lemma 3.2, on every interior x- and y-face of a
+    smooth periodic 2D state. (This is the flux the limiters of Sec. 3.2/3.3 blend
+    toward; a transposed stress, a one-sided S or a missing beta fails it.)"""
+    n1, n2, g, Pr = 10, 9, 1.4, 0.72
+    w = W.random_smooth_2d((n1, n2), seed=9, mu=max(mu, 1e-3))
+    P = orc.problem(2, n1, n2, lo=w.lo, hi=w.hi, mu=mu, Pr=Pr, bc=w.bc, gamma=g, limiter=2)
+    h = [(w.hi[0] - w.lo[0]) / n1, (w.hi[1] - w.lo[1]) / n2]
+    avg = W.split_sites(w.state, 2, n1, n2)[0]
+    kappa = g * mu / ((g - 1.0) * Pr)
+
+    def cell(i, j):
+        return avg[:, j % n2, i % n1]
+
+    def prim(U):
+        rho, mx, my, E = U
+        u, v = mx / rho, my / rho
+        return rho, u, v, (g - 1.0) * (E - 0.5 * (mx * u + my * v))
+
+    def quantities(i, j, l):
+        U = cell(i, j)
+        rho, u, v, p = prim(U)
+        gr = []
+        for (di, dj), hm in (((1, 0), h[0]), ((0, 1), h[1])):
+            re, ue, ve, pe = prim(cell(i + di, j + dj))
+            rw, uw, vw, pw = prim(cell(i - di, j - dj))
+            gr.append(((ue - uw) / (2 * hm), (ve - vw) / (2 * hm), (pe / re - pw / rw) / (2 * hm)))
+        (ux, vx_, Tx), (uy, vy, Ty) = gr
+        div = ux + vy
+        txx, tyy, txy = mu * (2 * ux - 2 / 3 * div), mu * (2 * vy - 2 / 3 * div), mu * (uy + vx_)
+        if l == 0:
+            q, t1, t2, ul = -kappa * Tx, txx, txy, u
+            Fc = np.array([U[1], U[1] * u + p, U[2] * u, (U[3] + p) * u])
+        else:
+            q, t1, t2, ul = -kappa * Ty, txy, tyy, v
+            Fc = np.array([U[2], U[1] * v, U[2] * v + p, (U[3] + p) * v])
+        F = Fc - np.array([0.0, t1, t2, u * t1 + v * t2 - q])
+        e = p / ((g - 1.0) * rho)
+        b_ = (np.sqrt(rho ** 2 * q ** 2 + 2 * rho ** 2 * e * (t1 ** 2 + t2 ** 2)) + rho * abs(q)) / (2 * rho ** 2 * e)
+        return U, F, abs(ul) + np.sqrt(g * p / rho), b_
+
+    worst = 0.0
+    for l, (di, dj) in enumerate(((1, 0), (0, 1))):
+        for j in range(1, n2 - 1):
+            for i in range(1, n1 - 1):
+                UL, FLc, aL, bL = quantities(i - di, j - dj, l)
+                UR, FRc, aR, bR = quantities(i, j, l)
+                ref = 0.5 * (FLc + FRc) - 0.5 * (max(aL, aR) + max(bL, bR)) * (UR - UL)
+                got = orc.face_low_order(P, w.state, l, i, j)
+                worst = max(worst, np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+    assert worst < 1e-13, worst
