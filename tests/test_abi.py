@@ -85,3 +85,15 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), ctypes.byref(o), None, None, 0,
                      ctypes.byref(ctx))
     assert st == N.AF_EINVAL and not ctx.value
+    # a moving wall is two-dimensional and needs a finite speed
+    o.kappa_off = 0
+    g1 = N.Grid()
+    g1.dim, g1.n[0], g1.n[1] = 1, 32, 1
+    g1.lo[0], g1.hi[0] = 0.0, 1.0
+    b.side[0], b.side[1] = 5, 3
+    st = L.af_create(ctypes.byref(g1), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
+    assert st == N.AF_EINVAL and not ctx.value
+    b.side[0], b.side[1], b.side[2], b.side[3] = 1, 1, 1, 5
+    b.wall_speed[3] = float("nan")
+    st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
+    assert st == N.AF_EINVAL and not ctx.value
