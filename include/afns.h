@@ -90,8 +90,9 @@ typedef struct {
     double c_s;        /* smoothness-limiter strength C_s (Sec. 3.2); paper: 1 */
     double cfl_c;      /* inviscid CFL number C^c of Eq. (13); paper: 1.04/d */
     double cfl_v;      /* viscous CFL number C^v of Eq. (13); default 0.33 in 1D (the
-                          paper's), 0.8 x 0.33/2 in 2D: the paper's 0.33/2 is unstable
-                          for 2D flows whose bound is dominated by the viscous term */
+                          paper's), 0.13 in 2D: the von Neumann limit of the 2D viscous
+                          operator under SSP-RK54 is 0.1307 where heat conduction
+                          dominates the bound, so the paper's 0.33/2 is unstable there */
     double eps;        /* positivity floor cap epsilon (Sec. 3.3); paper: 1e-13 */
     int max_halvings;  /* restarts allowed per step (Remark 3.2); default 30 */
     int tile_x;        /* 2D tile width in cells: 16 (default) or 32 (AF_MIXED, tile_y 8) */
@@ -228,22 +229,29 @@ const char *af_last_error(const afns_ctx *ctx);
  * owned by a host framework's pool allocator, or that runs where an allocation
  * (with the device-wide synchronisation it can imply) is not allowed.
  *  grid, gamma, mu, Pr: as for af_create (grid->dim must be 2).
- *  opts: NULL = af_opts_default(2); only cfl_c and cfl_v are used.
+ *  opts: NULL = af_opts_default(2); only cfl_c, cfl_v and kappa_off are used
+ *    (kappa_off = 1 drops the conduction term from the bound, as af_create does).
  *  avg_dev: device pointer to the cell averages in the layout of site[0] of
  *    af_set_state, avg[4][n2][n1]; the caller owns it.
- *  dt_dev: device pointer that receives one double; the caller owns it.
+ *  dt_dev: device pointer that receives one double; the caller owns it. If any
+ *    cell average is non-finite or has rho <= 0 or p <= 0 (outside the set where
+ *    Eq. (13) is defined), *dt_dev receives NaN: the call does not wait for the
+ *    GPU, so it cannot return AF_EINVAL for the values themselves.
  *  cuda_stream: the two kernels of the call are issued there, asynchronously;
  *    nothing is synchronised (read dt_dev after the stream has reached it).
+ * Returns AF_EINVAL for a bad argument or an oversized grid (nothing launched),
+ * AF_ECUDA if the address lookup or a launch of this call failed.
  * Scratch: one file-scope device array inside the library, two doubles per chunk
  * of AF_NOALLOC_CHUNK cells for at most AF_NOALLOC_MAX_CHUNKS chunks (256 KiB).
  * Every GPU that loads the library holds it until the process exits. Grids with
  * more than AF_NOALLOC_CHUNK * AF_NOALLOC_MAX_CHUNKS cells (67,108,864) are
  * rejected with AF_EINVAL before anything is launched. The first call on a device
- * looks up the array's device address for that device (once); make that first
- * call before any stream capture. Every call writes each slot it later reads, so
- * nothing needs clearing between calls; but all calls share the one array, so
- * calls that overlap on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.
+ * (and the first after the device's context was reset) looks up the array's
+ * device address for that device and context; make that first call before any
+ * stream capture. Every call writes each slot it later reads, so nothing needs
+ * clearing between calls; but all calls share the one array, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
  */
 /*
  * Measured FMA throughput of the current device (the paper has no counterpart):

@@ -238,3 +238,75 @@ def wave_speed(P, U, l):
 
 def theta(zL, zH, eps):
     return lib().orc_theta(zL, zH, eps)
+
+
+# ---------------------------------------------------------------------------
+# Operation counts (opcount.cpp: this source compiled as C++ with a counting
+# scalar). Categories and kinds as documented there.
+# ---------------------------------------------------------------------------
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "liboracle_opcount.so")
+OPC_CATEGORIES = ("add", "mul", "div", "sqrt", "trans", "other")
+OPC_KINDS = ("counted", "repeated", "trivial")
+OPC_NPH = 12
+OPC_PHASES = {0: "ghost fill", 1: "centres + centre limiter", 2: "node primitives",
+              3: "point residual", 4: "high-order face flux", 5: "low-order cell and face quantities",
+              6: "face limiter", 7: "point scaling limiter", 8: "cell residual", 9: "CFL bound",
+              10: "RK combination", 11: "other"}
+
+_opc = None
+
+
+def opcount_build(force: bool = False) -> str:
+    stale = not os.path.exists(_OPC_LIB) or any(
+        os.path.getmtime(p) > os.path.getmtime(_OPC_LIB) for p in (_SRC, _HDR, _OPC_SRC))
+    if force or stale:
+        tmp = _OPC_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _OPC_SRC])
+        os.replace(tmp, _OPC_LIB)
+    return _OPC_LIB
+
+
+def _opc_lib():
+    global _opc
+    if _opc is None:
+        L = ctypes.CDLL(opcount_build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(Problem)
+        L.orc_opcount_reset.argtypes = []
+        L.orc_opcount_get.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_opcount_residual.argtypes = [pp, dp, ctypes.c_double, dp]
+        L.orc_opcount_step.argtypes = [pp, dp, ctypes.c_double]
+        L.orc_opcount_dt_max.argtypes = [pp, dp]
+        L.orc_opcount_dt_max.restype = ctypes.c_double
+        _opc = L
+    return _opc
+
+
+def _opc_tally():
+    L = _opc_lib()
+    n = OPC_NPH * len(OPC_CATEGORIES) * len(OPC_KINDS)
+    buf = (ctypes.c_longlong * n)()
+    L.orc_opcount_get(buf)
+    return np.array(buf, dtype=np.int64).reshape(OPC_NPH, len(OPC_CATEGORIES), len(OPC_KINDS))
+
+
+def opcount(P, state, what="step", dt=None, out=None):
+    """Operation tallies [phase, category, kind] of one stage residual
+    (what="residual"; its values go to `out` if given), one SSP-RK54 step
+    ("step", five residuals plus the combinations) or the CFL bound ("dt")."""
+    L = _opc_lib()
+    s = np.ascontiguousarray(state, dtype=np.float64).copy()
+    if dt is None:
+        dt = dt_max(P, s)
+    L.orc_opcount_reset()
+    if what == "residual":
+        rc = L.orc_opcount_residual(ctypes.byref(P), _dp(s), dt, _dp(out) if out is not None else None)
+    elif what == "step":
+        rc = L.orc_opcount_step(ctypes.byref(P), _dp(s), dt)
+    else:
+        L.orc_opcount_dt_max(ctypes.byref(P), _dp(s))
+        rc = 0
+    assert rc == 0
+    return _opc_tally()

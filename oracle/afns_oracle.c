@@ -39,11 +39,13 @@
  *      solution at the stage's time; the boundary point values themselves evolve
  *      with the scheme like every other point.
  *  R14 CFL numbers of Eq. (13): C^c = 1.04/d as printed; C^v = 0.33 in 1D as
- *      printed, but 0.8 * 0.33/2 in 2D. With 0.33/2 the 2D scheme grows a
- *      high-frequency mode wherever the viscous term dominates the bound (the
- *      cross-derivative terms of Eq. (12) widen the viscous spectrum beyond d
- *      times the 1D one); 0.8 x keeps those runs bounded. The 1D limit of
- *      exactly 0.33 is reproduced (pinned in the tests).
+ *      printed, but 0.13 in 2D. The von Neumann limit of the 2D viscous
+ *      operator of Eq. (12) under SSP-RK54 is 0.1307 where heat conduction
+ *      dominates the bound (its largest eigenvalue is 40.8 / dx^2 against
+ *      2 x 16 / dx^2 for two 1D operators: the Simpson centres and edge
+ *      averages couple the directions), so the printed 0.33/2 lets such flows
+ *      grow a high-frequency mode. The 1D limit of 0.333 is the printed one
+ *      (both pinned in the tests).
  */
 #include "afns_oracle.h"
 
@@ -52,6 +54,19 @@
 #include <string.h>
 
 #define MAXC 4 /* at most 4 conservative components (2D) */
+
+/* Operation-count hooks. Here they do nothing. The op-counting build
+ * (opcount.cpp, the same source compiled as C++ with a counting scalar type)
+ * defines ORC_PHASE(k) to attribute the operations that follow to step k of a
+ * stage, and ORC_PURE(id, a, na, b, nb, i, j) to mark the rest of a function as
+ * a pure evaluation keyed by its inputs (arrays a[na], b[nb], integers i, j),
+ * so that a repeated evaluation with the same inputs is counted apart. */
+#ifndef ORC_PHASE
+#define ORC_PHASE(k) ((void)0)
+#endif
+#ifndef ORC_PURE
+#define ORC_PURE(id, a, na, b, nb, i, j) ((void)0)
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* Physics: Sec. 1 Eqs. (1)-(3), Sec. 2.1 Eqs. (4)-(5), Sec. 2.2 K matrices.   */
@@ -66,6 +81,7 @@ static double kappa_of(const orc_problem *P)
 
 double orc_pressure(const orc_problem *P, const double *U)
 {
+    ORC_PURE(1, U, P->dim + 2, (const double *)0, 0, 0, 0);
     /* Def. 3.1, Eq. (14): p = (gamma-1) (E - |rho u|^2 / (2 rho)) */
     int d = P->dim;
     double m2 = 0.0;
@@ -76,6 +92,7 @@ double orc_pressure(const orc_problem *P, const double *U)
 /* W = (rho, u_1..u_d, p) (Eq. (5) and Sec. 2.2) */
 static void primitive(const orc_problem *P, const double *U, double *W)
 {
+    ORC_PURE(2, U, P->dim + 2, (const double *)0, 0, 0, 0);
     int d = P->dim;
     W[0] = U[0];
     for (int k = 0; k < d; ++k) W[1 + k] = U[1 + k] / U[0];
@@ -85,6 +102,7 @@ static void primitive(const orc_problem *P, const double *U, double *W)
 /* Z = (0, u_1..u_d, T) with T = p/rho (Eq. (5), Sec. 1 nondimensional form) */
 static void zvars(const orc_problem *P, const double *W, double *Z)
 {
+    ORC_PURE(3, W, P->dim + 2, (const double *)0, 0, 0, 0);
     int d = P->dim;
     Z[0] = 0.0;
     for (int k = 0; k < d; ++k) Z[1 + k] = W[1 + k];
@@ -93,6 +111,7 @@ static void zvars(const orc_problem *P, const double *W, double *Z)
 
 void orc_inviscid_flux(const orc_problem *P, const double *U, int l, double *F)
 {
+    ORC_PURE(4, U, P->dim + 2, (const double *)0, 0, l, 0);
     /* Eq. (2): F^c_l = (rho u_l, rho u u_l + p e_l, (E + p) u_l) */
     int d = P->dim;
     double W[MAXC];
@@ -145,6 +164,7 @@ static void kmatrix(const orc_problem *P, const double *W, int l, int m, double 
 /* out = K_lm(W) z (matrix-vector product, nc components) */
 static void kapply(const orc_problem *P, const double *W, int l, int m, const double *z, double *out)
 {
+    ORC_PURE(5, W, P->dim + 2, z, P->dim + 2, l, m);
     double K[MAXC][MAXC];
     int nc = P->dim + 2;
     kmatrix(P, W, l, m, K);
@@ -157,6 +177,7 @@ static void kapply(const orc_problem *P, const double *W, int l, int m, const do
 
 void orc_viscous_flux(const orc_problem *P, const double *U, const double *grad, int l, double *F)
 {
+    ORC_PURE(6, U, P->dim + 2, grad, P->dim * (P->dim + 2), l, 0);
     /* Sec. 2.2: F^v_l = sum_m K_lm(W) dZ/dx_m (Sec. 2.1 in 1D: K(W) Z_x) */
     int nc = P->dim + 2;
     double W[MAXC], t[MAXC];
@@ -170,6 +191,7 @@ void orc_viscous_flux(const orc_problem *P, const double *U, const double *grad,
 
 double orc_wave_speed(const orc_problem *P, const double *U, int l)
 {
+    ORC_PURE(7, U, P->dim + 2, (const double *)0, 0, l, 0);
     /* Lemma 3.1 / Sec. 2.3: rho_l = |u_l| + c, c = sqrt(gamma p / rho) */
     double W[MAXC];
     primitive(P, U, W);
@@ -187,6 +209,7 @@ static double visc_eigen(const orc_problem *P, const double *U)
 
 double orc_visc_bound(const orc_problem *P, const double *U, const double *grad, int l)
 {
+    ORC_PURE(8, U, P->dim + 2, grad, P->dim * (P->dim + 2), l, 0);
     /* Lemma 3.2: b_l = (sqrt(rho^2 q_l^2 + 2 rho^2 e |tau_l|^2) + rho |q_l|) / (2 rho^2 e),
      * with tau from Eq. (3) and q = -kappa grad T.  grad[m*nc + k] = d Z_k / d x_m. */
     int d = P->dim, nc = d + 2;
@@ -690,6 +713,7 @@ static void step_node(int l, int k, int a0, int a1, int *b0, int *b1)
 /* D_c along direction m of Z at node (a0,a1) (Eq. (8) on the lattice line) */
 static void grad_Z(const grid_t *g, int m, int a0, int a1, double *dz)
 {
+    ORC_PURE(9, (const double *)0, 0, (const double *)0, 0, m, a0 * 65536 + a1);
     for (int c = 0; c < g->nc; ++c) {
         double z5[5];
         for (int k = -2; k <= 2; ++k) {
@@ -736,16 +760,18 @@ static void point_residual(const grid_t *g, int a0, int a1, double *R)
             orc_op_dminus(fm, dx, &dm);
             R[c] -= dp + dm;
         }
-        /* viscous, same direction: D^{(l),2}(K_ll, Z), Eq. (9) with matrix K */
+        /* viscous, same direction: D^{(l),2}(K_ll, Z), Eq. (9) with matrix K:
+         * sum_m sum_n b_mn K(W_m) Z_n, with K(W_m) taken out of the sum over n */
         {
             double b[25], s[MAXC] = {0, 0, 0, 0};
             orc_op_bmatrix(b);
-            for (int m = 0; m < 5; ++m)
-                for (int n = 0; n < 5; ++n) {
-                    double t[MAXC];
-                    kapply(P, W5[m], l, l, Z5[n], t);
-                    for (int c = 0; c < nc; ++c) s[c] += b[m * 5 + n] * t[c];
-                }
+            for (int m = 0; m < 5; ++m) {
+                double y[MAXC] = {0, 0, 0, 0}, t[MAXC];
+                for (int n = 0; n < 5; ++n)
+                    for (int c = 0; c < nc; ++c) y[c] += b[m * 5 + n] * Z5[n][c];
+                kapply(P, W5[m], l, l, y, t);
+                for (int c = 0; c < nc; ++c) s[c] += t[c];
+            }
             for (int c = 0; c < nc; ++c) R[c] += 4.0 / (dx * dx) * s[c];
         }
         /* viscous, mixed: D_c^{(l)} (K_lm D_c^{(m)} Z), m != l (Sec. 2.2) */
@@ -1012,10 +1038,14 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
     grid_init(g, P);
     int d = g->d, nc = g->nc;
     unpack(g, state);
+    ORC_PHASE(0); /* ghost fill */
     fill_ghosts(g);
     exact_ghosts(g, P->time);
+    ORC_PHASE(1); /* cell centres and centre scaling limiter */
     centres(g);
+    ORC_PHASE(2); /* node primitives W, Z */
     node_prims(g);
+    ORC_PHASE(5); /* low-order cell quantities and smoothness sensors */
 
     /* cell quantities on cells [-1, n_l] */
     int ce0 = g->n[0] + 2, ce1 = d == 2 ? g->n[1] + 2 : 1;
@@ -1038,6 +1068,7 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
             for (int f0 = 0; f0 < nf0; ++f0) {
                 size_t fid = (size_t)f1 * nf0 + f0;
                 /* high-order total flux: Simpson average along the face (Sec. 2.2) */
+                ORC_PHASE(4);
                 double FH[MAXC] = {0, 0, 0, 0};
                 if (d == 1) {
                     node_total_flux(g, 0, 2 * f0, 0, FH);
@@ -1065,8 +1096,10 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
                     cell_get(g, L0, L1, UbL);
                     cell_get(g, R0, R1, UbR);
                     /* low-order LLF total flux, Eq. (19) */
+                    ORC_PHASE(5);
                     double FL[MAXC], dF[MAXC], FLs[MAXC];
                     face_llf(nc, l, qL, qR, UbL, UbR, FL);
+                    ORC_PHASE(6); /* monolithic limiter of the face */
                     /* smoothness-based blending, Sec. 3.2, Eq. (22) */
                     if (P->limiter == ORC_LIM_S_PP) {
                         double p1 = fmax(qL->phi1, qR->phi1), p2 = fmax(qL->phi2, qR->phi2);
@@ -1111,6 +1144,7 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
     }
 
     /* cell-average residual: Eq. (6a) / Eq. (12) / Eq. (23) */
+    ORC_PHASE(8);
     for (int i1 = 0; i1 < imax(g, 1); ++i1)
         for (int i0 = 0; i0 < g->n[0]; ++i0)
             for (int c = 0; c < nc; ++c) {
@@ -1134,6 +1168,7 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
         for (int a0 = 0; a0 <= amax(g, 0); ++a0) {
             if (is_centre(g, a0, a1)) continue;
             double R[MAXC], U[MAXC], UH[MAXC];
+            ORC_PHASE(3);
             point_residual(g, a0, a1, R);
             if (P->source != ORC_SRC_NONE) {
                 double S[MAXC];
@@ -1141,6 +1176,7 @@ int orc_residual(const orc_problem *P, const double *state, double dt, double *L
                 for (int c = 0; c < nc; ++c) R[c] += S[c];
             }
             if (P->limiter != ORC_LIM_NONE) {
+                ORC_PHASE(7); /* point scaling limiter */
                 lat_get(g, g->U, a0, a1, U);
                 for (int c = 0; c < nc; ++c) UH[c] = U[c] + dt * R[c];
                 double pH = orc_pressure(P, UH);
@@ -1182,7 +1218,7 @@ void orc_defaults(orc_problem *P)
     P->time = 0.0;
     P->c_s = 1.0;
     P->cfl_c = 1.04 / P->dim;
-    P->cfl_v = P->dim == 1 ? 0.33 : 0.8 * 0.33 / 2.0;   /* reading R14 */
+    P->cfl_v = P->dim == 1 ? 0.33 : 0.13;   /* reading R14 */
     P->eps = 1e-13;
 }
 
@@ -1262,6 +1298,7 @@ int orc_step(const orc_problem *P, double *state, double dt, int max_halvings, d
             Q.time = P->time + cst[s] * dt;
             orc_residual(&Q, u[s], dt, Lk[s], NULL, NULL, &nb);
             if (nb) bad = 1;
+            ORC_PHASE(10); /* SSP-RK54 combination */
             for (size_t x = 0; x < n; ++x) {
                 double v = 0.0;
                 for (int k = 0; k <= s; ++k) v += a[s][k] * u[k][x] + b[s][k] * dt * Lk[k][x];

@@ -238,6 +238,11 @@ static af_status check_args(const af_grid *g, double gamma, double mu, double Pr
         if (g->n[l] < 4) return *why = "need at least 4 cells per direction", AF_EINVAL;
         if (!(g->hi[l] > g->lo[l])) return *why = "need hi > lo", AF_EINVAL;
     }
+    // the per-site kernels index one site's elements (ghosts included) with
+    // 32-bit integers; such grids would not fit in device memory anyway
+    if (g->dim == 2 && (long long)(g->n[0] + 5) * (g->n[1] + 5) >= (1ll << 31))
+        return *why = "grid too large: (n1+5)(n2+5) must stay below 2^31", AF_EINVAL;
+    if (g->dim == 1 && g->n[0] >= (1 << 30)) return *why = "grid too large: n1 must stay below 2^30", AF_EINVAL;
     if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return *why = "need gamma > 1, mu >= 0, Pr > 0", AF_EINVAL;
     for (int l = 0; l < g->dim; ++l) {
         int a = bc->side[2 * l], b = bc->side[2 * l + 1];
@@ -274,10 +279,12 @@ af_status af_opts_default(int dim, af_opts *o)
     o->limiter = AF_LIM_S_PP;
     o->c_s = 1.0;
     o->cfl_c = 1.04 / dim;
-    // C^v of Eq. (13): 0.33 in 1D as printed; in 2D 0.8 x 0.33/2, because with
-    // 0.33/2 the cross-derivative terms of Eq. (12) let a high-frequency mode grow
-    // wherever the viscous term dominates the bound
-    o->cfl_v = dim == 1 ? 0.33 : 0.8 * 0.33 / 2.0;
+    // C^v of Eq. (13): 0.33 in 1D as printed; in 2D 0.13, just below the von
+    // Neumann limit 0.1307 of the 2D viscous operator of Eq. (12) under SSP-RK54
+    // where heat conduction dominates the bound (the Simpson centres and edge
+    // averages couple the directions, so the printed 0.33/2 lets a high-frequency
+    // mode grow)
+    o->cfl_v = dim == 1 ? 0.33 : 0.13;
     o->eps = 1e-13;
     o->max_halvings = 30;
     o->source = AF_SRC_NONE;

@@ -566,13 +566,13 @@ def test_viscous_cfl_limit_1d_is_the_papers():
 
 def test_viscous_cfl_2d_default_is_stable_where_papers_is_not():
     """Reading of Eq. (13) in 2D: with C^v = 0.33/2 a viscosity-dominated 2D flow
-    (mu = 3, 24^2) departs within 100 steps (the cross-derivative terms of Eq. (12)
-    widen the viscous spectrum beyond twice the 1D one); the default
-    C^v = 0.8 x 0.33/2 keeps it bounded for 300 steps."""
+    (mu = 3, 24^2) departs within 100 steps (the 2D viscous operator's spectrum
+    reaches 1.27 times twice the 1D one); the default C^v = 0.13, below the von
+    Neumann limit 0.1307, keeps it bounded for 300 steps."""
     import oracle as orc
     w = W.smooth_2d(24, mu=3.0)
     P = orc.problem(2, 24, 24)
-    assert P.cfl_v == pytest.approx(0.8 * 0.33 / 2) and P.cfl_c == pytest.approx(1.04 / 2)
+    assert P.cfl_v == 0.13 and P.cfl_c == pytest.approx(1.04 / 2)
     assert _steps_until_blowup(orc, w, 100, cfl_v=0.33 / 2) < 100
     assert _steps_until_blowup(orc, w, 300) == 300
 
