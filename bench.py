@@ -98,11 +98,12 @@ def stage_roofline(precision, cells, stage_ms, peaks, alu_pk):
     if t_alu >= t_hbm:
         achieved = FLOPS_PER_CELL_STAGE * cells / sec / 1e12
         r = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s", "frac": achieved / alu,
-             "work_per_cell": "%d flops" % FLOPS_PER_CELL_STAGE, "peak_source": alu_src}
+             "work_per_cell": "%.0f flops (counted: oracle/opcount_smooth2d.json)" % FLOPS_PER_CELL_STAGE,
+             "peak_source": alu_src}
     else:
         achieved = bpc * cells / sec / 1e9
         r = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-             "work_per_cell": "%d bytes" % bpc, "peak_source": hbm_src}
+             "work_per_cell": "%.1f bytes" % bpc, "peak_source": hbm_src}
     r.update(common)
     return r
 
@@ -266,6 +267,60 @@ def cpu_baseline(w, S, args):
                               % (w.n[0], w.n[1], sec)}
 
 
+def host_description():
+    """nproc and the CPU model of this host (from lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def _oracle_sample_step(n):
+    """One SSP-RK54 step of the benchmark flow on an n x n grid in the oracle
+    (runs in a spawned worker process); returns its seconds."""
+    import oracle as O
+    from paper_2609_29081_b300 import workloads as W
+    w = W.smooth_2d(n)
+    P = O.problem(2, n, n, lo=w.lo, hi=w.hi, mu=w.mu, Pr=w.Pr, bc=w.bc, gamma=w.gamma)
+    s = w.state.copy()
+    t0 = time.perf_counter()
+    O.step(P, s, O.dt_max(P, s))
+    return time.perf_counter() - t0
+
+
+def cpu_all_cores(n=128):
+    """The oracle as it stands on every host core: nproc independent processes
+    (spawned), each one SSP-RK54 step of the benchmark flow on an n x n sample;
+    cell-stage updates of all of them over the wall time."""
+    import multiprocessing as mp
+    import oracle as O
+    O.build()
+    k = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(k) as pool:
+        pool.map(_oracle_sample_step, [16] * k)          # workers up and the library loaded
+        t0 = time.perf_counter()
+        pool.map(_oracle_sample_step, [n] * k)
+        sec = time.perf_counter() - t0
+    return {"value": k * n * n * 5 / sec, "unit": UNIT, "cores": k, "kind": "oracle",
+            "sample": "%d independent processes, each one SSP-RK54 step of the same flow on a %dx%d grid (%.1f s)"
+                      % (k, n, n, sec)}
+
+
 def tube_arm(args, dist, rank, ws):
     """2D viscous shock tube in a walled box (no-slip walls, symmetry on top),
     2000 x 1000 cells, Re = 1000: K timed CFL steps after the warm-up; with
@@ -376,16 +431,18 @@ def ladder_arm(args, rank):
                           "ladder": out}), flush=True)
 
 
-def batch_arm(args, dist, rank, ws):
-    """Batched form: 256 independent periodic problems of uneven sizes (mixed
+def batch_measure(args, dist, rank, ws, steps, warmup, nprob):
+    """Batched form: nprob independent periodic problems of uneven sizes (mixed
     precision, persistent stage kernel, CUDA graph, autotuned configuration),
-    against the same problems advanced one by one in FP64 (bounded sample)."""
+    timed over `steps` graph-replayed batch steps; the same problems advanced one
+    by one in FP64 on a bounded sample. Restarted (rejected) problem steps count
+    as time, not as updates."""
     import torch
     from paper_2609_29081_b300 import BatchSolver, Solver, build, workloads as W
     from paper_2609_29081_b300._native import FP64, MIXED
     build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    wls = W.batch_problems(nprob=args.nprob, seed=batch_seed(rank))
+    wls = W.batch_problems(nprob=nprob, seed=batch_seed(rank))
     B = BatchSolver(wls, precision=MIXED)
     for i, w in enumerate(wls):
         B.set_state(i, w.state)
@@ -395,11 +452,12 @@ def batch_arm(args, dist, rank, ws):
     torch.cuda.synchronize()
     cp, cpath = clocks_start()
     time.sleep(0.4)
-    warm_done = preheat(lambda: (B.step_all(1, graph=True), B.sync()), args.warmup)
+    warm_done = preheat(lambda: (B.step_all(1, graph=True), B.sync()), warmup)
     acc0 = [B.stats(i)["accepted"] for i in range(len(wls))]
+    rst0 = [B.stats(i)["restarts"] for i in range(len(wls))]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(B.stream)
-    B.step_all(args.steps, graph=True)
+    B.step_all(steps, graph=True)
     ev1.record(B.stream)
     nlaunch = B.sync()
     torch.cuda.synchronize()
@@ -407,10 +465,12 @@ def batch_arm(args, dist, rank, ws):
     ms = ev0.elapsed_time(ev1)
     st = [B.stats(i) for i in range(len(wls))]
     updates = sum(w.cells * 5 * (s["accepted"] - a0) for w, s, a0 in zip(wls, st, acc0))
-    restarts = sum(s["restarts"] for s in st)
+    restarts = sum(s["restarts"] - r0 for s, r0 in zip(st, rst0))
+    failed = sum(s["failed"] for s in st)
+    B.close()
     ms, updates = reduce_over_ranks(dist, [ms, updates], ["max", "sum"])
     value = updates / (ms / 1e3)
-    # FP64 one by one on a bounded sample (first 16 problems, 2 steps each)
+    # FP64 one by one on a bounded sample (first 16 problems, 2 timed steps each)
     one_cells, one_ms = 0, 0.0
     for w in wls[:16]:
         S = Solver.from_workload(w, precision=FP64)
@@ -424,18 +484,44 @@ def batch_arm(args, dist, rank, ws):
         one_ms += 1e3 * (time.perf_counter() - t0)
         one_cells += w.cells * 5 * 2
         S.close()
-    if rank != 0:
-        return
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "batched: %d periodic 2D problems, sides from {64..512}, mu log-uniform "
-                                   "[1e-4,1e-2], Mach 0.1-3, 25%% near-vacuum blasts (seed 5 + rank)" % len(wls),
-                       "cells": int(sum(w.cells for w in wls)), "tuned": cfg, "restarts": restarts,
-                       "graph": True, "warmup_steps_run": warm_done},
-            "clocks": clocks, "gpu_launches": nlaunch * args.steps,
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs") or 6400.0
+    alu = measure_alu_peaks().get("fp32") or FP32_DERIVED_TFLOPS
+    sec = ms / 1e3
+    t_hbm = updates * BYTES_PER_CELL_STAGE_MIXED / (hbm * 1e9)
+    t_alu = updates * FLOPS_PER_CELL_STAGE / (alu * 1e12)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": updates * FLOPS_PER_CELL_STAGE / sec / 1e12, "peak": alu,
+                "unit": "TFLOP/s", "frac": t_alu / sec}
+    else:
+        roof = {"bound": "hbm", "achieved": updates * BYTES_PER_CELL_STAGE_MIXED / sec / 1e9, "peak": hbm,
+                "unit": "GB/s", "frac": t_hbm / sec}
+    roof.update({"hbm_frac": t_hbm / sec, "alu_frac": t_alu / sec,
+                 "work_per_cell": "%.0f flops (counted) / %.0f bytes per accepted cell-stage"
+                                  % (FLOPS_PER_CELL_STAGE, BYTES_PER_CELL_STAGE_MIXED),
+                 "time": "whole batch steps (CFL, ghost, stage and commit kernels, graph replay)",
+                 "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs; FP32 FMA chains (af_alu_peak)"})
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup_steps_run": warm_done,
+            "workload": "batched: %d periodic 2D problems, sides from {64..512}, mu log-uniform [1e-4,1e-2], "
+                        "Mach 0.1-3, 25%% near-vacuum blasts (seed 5 + rank)" % len(wls),
+            "cells": int(sum(w.cells for w in wls)), "tuned": cfg, "restarts": restarts, "failed": failed,
+            "graph": True, "gpu_launches": nlaunch * steps, "clocks": clocks, "roofline": roof,
             "fp64_one_by_one": {"value": one_cells / (one_ms / 1e3), "unit": UNIT,
                                 "sample": "first 16 problems, 2 FP64 steps each, one problem at a time"}}
+
+
+def batch_arm(args, dist, rank, ws):
+    """The batched workload as the bench line's headline (--workload batch)."""
+    b = batch_measure(args, dist, rank, ws, args.steps, args.warmup, args.nprob)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": b["workload"], "cells": b["cells"], "tuned": b["tuned"],
+                       "restarts": b["restarts"], "graph": True, "warmup_steps_run": b["warmup_steps_run"]},
+            "roofline": b["roofline"], "clocks": b["clocks"], "gpu_launches": b["gpu_launches"],
+            "fp64_one_by_one": b["fp64_one_by_one"]}
     print(json.dumps(line), flush=True)
 
 
@@ -451,6 +537,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_CELLS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-ladder", dest="ladder", action="store_false",
+                    help="skip the accuracy ladder at the run length (128^2 .. 2048^2, FP64 and mixed)")
+    ap.add_argument("--no-batch", dest="batch", action="store_false",
+                    help="skip the batched sub-record of the default line")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "tube", "ladder"])
     ap.add_argument("--t-end", type=float, default=0.0)
     ap.add_argument("--nprob", type=int, default=256)
@@ -499,7 +589,10 @@ def main():
             "roofline": stage_roofline(args.precision, cells, r["stage_ms"], peaks, alu_pk),
             "clocks": r["clocks"],
             "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["state_bytes"],
-                    "d2h_bytes_per_step": r["state_bytes"]},
+                    "d2h_bytes_per_step": r["state_bytes"], "ms_per_step_parts": r["e2e_parts_ms"],
+                    "what": "af_set_state_f32 from pinned host memory, af_step, af_get_state_f32 to pinned "
+                            "host memory, every step" if args.precision == "mixed" else
+                            "af_set_state from pinned host memory, af_step, af_get_state, every step"},
             "gpu_launches": r["launches"],
             "stage_ms": r["stage_ms"]}
     if cmp_run:
@@ -507,7 +600,17 @@ def main():
         line[other] = {"value": c["value"], "unit": UNIT, "ms_per_step": c["ms"] / args.steps,
                        "stage_ms": c["stage_ms"], "tuned": c["tuned"], "restarts": c["restarts"],
                        "roofline": stage_roofline(other, cells, c["stage_ms"], peaks, alu_pk)}
-        line["l1_mixed_vs_fp64"] = accuracy_pair(w, ACCURACY_STEPS)
+    if args.ladder:
+        acc = accuracy_ladder(args.n, ACCURACY_STEPS)
+        key = str(args.n)
+        line["accuracy"] = acc
+        line["l1_mixed_vs_fp64"] = {"value": acc["mixed_vs_fp64_l1"][key],
+                                    "linf": acc["mixed_vs_fp64_linf"][key],
+                                    "discretisation_l1": acc["discretisation_l1"].get(key),
+                                    "mixed_below_discretisation_up_to": acc["mixed_below_discretisation_up_to"],
+                                    "what": "relative L1 / Linf distance of the cell averages after %d CFL "
+                                            "steps (t = %.4g), mixed vs FP64, beside the FP64 discretisation "
+                                            "error of the grid" % (ACCURACY_STEPS, acc["t_end"])}
     if not args.no_cpu:
         from paper_2609_29081_b300 import Solver
         from paper_2609_29081_b300._native import FP64, MIXED
@@ -522,36 +625,78 @@ def main():
         u0 = W.split_sites(w0.state, 2, *w0.n)[0]
         avg_r = u0 + b0 * dt * W.split_sites(Lr, 2, *w0.n)[0]
         avg_g = u0 + b0 * dt * W.split_sites(Lg, 2, *w0.n)[0]
-        line["cpu_baseline"] = cb
+        line["cpu_baseline"] = cpu_all_cores()
+        line["cpu_baseline"]["host"] = host_description()
+        line["cpu_baseline"]["single_core"] = cb
         line["l1_vs_oracle"] = {"what": "relative L1 / Linf distance of the first stage update u + b0 dt L(u) of "
                                         "the cell averages, GPU (%s) vs oracle, full grid" % args.precision,
                                 "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum()),
                                 "linf": float(np.abs(avg_g - avg_r).max() / np.abs(avg_r).max())}
+    if args.batch:
+        b = batch_measure(args, None, 0, 1, args.steps, args.warmup, args.nprob)
+        line["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "workload", "cells", "tuned",
+                                           "restarts", "failed", "graph", "gpu_launches", "roofline",
+                                           "fp64_one_by_one", "clocks")}
     print(json.dumps(line), flush=True)
 
 
-ACCURACY_STEPS = 20
+ACCURACY_STEPS = 200   # the run length of the 2D smooth periodic configuration
 
 
-def accuracy_pair(w, nsteps):
-    """The same nsteps CFL steps from the initial state in both precisions (not
-    timed). The FP64 path equals the oracle to 1e-10 (parity tests), so this is
-    the mixed path's error against the oracle after nsteps."""
+def accuracy_ladder(n_main, steps, grids=(32, 64, 128, 256, 512, 1024, 2048)):
+    """Accuracy of the mixed path at the configuration's run length (not timed).
+    t_end is the time the FP64 path reaches in `steps` CFL steps on n_main^2; on
+    every grid of the ladder both paths advance to t_end (the FP64 path equals
+    the oracle to 1e-10, parity tests). Reported per grid N: the discretisation
+    error, relative L1 distance of the FP64 cell averages from the 2N solution
+    restricted by 2x2 averaging, and the mixed path's error, relative L1 (and
+    Linf) distance of its cell averages from FP64's; and the largest grid on
+    which the mixed error stays below the discretisation error."""
     from paper_2609_29081_b300 import Solver, workloads as W
     from paper_2609_29081_b300._native import FP64, MIXED
-    fin = {}
-    for name, p in (("mixed", MIXED), ("fp64", FP64)):
-        S = Solver.from_workload(w, precision=p)
-        S.set_state(w.state)
-        for _ in range(nsteps):
-            S.step(0.0)
-        fin[name] = W.split_sites(S.get_state(), 2, *w.n)[0]
-        S.close()
-    d = np.abs(fin["mixed"] - fin["fp64"])
-    return {"value": float(d.sum() / np.abs(fin["fp64"]).sum()),
-            "linf": float(d.max() / np.abs(fin["fp64"]).max()),
-            "what": "relative L1 / Linf distance of the cell averages after %d CFL steps from the "
-                    "initial state, mixed vs FP64" % nsteps}
+    import torch
+    w = W.smooth_2d(n_main)
+    S = Solver.from_workload(w, precision=FP64)
+    S.set_state(w.state)
+    for _ in range(steps):
+        S.step(0.0)
+    S.get_state()
+    t_end = S.t
+    S.close()
+    sol = {"fp64": {}, "mixed": {}}
+    nsteps = {}
+    t0 = time.perf_counter()
+    for n in grids:
+        for name, p in (("fp64", FP64), ("mixed", MIXED)):
+            wn = W.smooth_2d(n)
+            S = Solver.from_workload(wn, precision=p)
+            S.set_state(wn.state)
+            k, _ = S.advance(t_end)
+            sol[name][n] = W.split_sites(S.get_state(), 2, n, n)[0]
+            nsteps[n] = k
+            S.close()
+            torch.cuda.empty_cache()
+    disc, mixed, mixed_inf = {}, {}, {}
+    for n in grids:
+        f = sol["fp64"][n]
+        d = np.abs(sol["mixed"][n] - f)
+        mixed[n] = float(d.sum() / np.abs(f).sum())
+        mixed_inf[n] = float(d.max() / np.abs(f).max())
+        if 2 * n in sol["fp64"]:
+            g = sol["fp64"][2 * n]
+            r = 0.25 * (g[:, 0::2, 0::2] + g[:, 1::2, 0::2] + g[:, 0::2, 1::2] + g[:, 1::2, 1::2])
+            disc[n] = float(np.abs(f - r).sum() / np.abs(r).sum())
+    below = [n for n in disc if mixed[n] < disc[n]]
+    return {"t_end": t_end, "steps_at": {str(n): nsteps[n] for n in grids},
+            "discretisation_l1": {str(n): v for n, v in disc.items()},
+            "mixed_vs_fp64_l1": {str(n): v for n, v in mixed.items()},
+            "mixed_vs_fp64_linf": {str(n): v for n, v in mixed_inf.items()},
+            "mixed_below_discretisation_up_to": max(below) if below else None,
+            "seconds": time.perf_counter() - t0,
+            "what": "cell averages at t_end = time of %d FP64 CFL steps on %d^2; discretisation error of grid N: "
+                    "relative L1 distance from the 2N solution restricted by 2x2 averaging (FP64); mixed error: "
+                    "relative L1 / Linf distance of the mixed cell averages from FP64's on the same grid"
+                    % (steps, n_main)}
 
 
 def tile_opts(args):
@@ -610,27 +755,47 @@ def single_run(args, w, precision, dist, ws, e2e):
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()
+            # each call returns with its work done (the uploads and downloads
+            # synchronise the stream, the step reads its restart flag), so host
+            # time stamps between them split the step into its three parts
+            parts = [0.0, 0.0, 0.0]
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
+                ta = time.perf_counter()
                 put(host_in.numpy())
+                tb = time.perf_counter()
                 S.step(0.0)
+                tc = time.perf_counter()
                 get(host_out.numpy())
+                td = time.perf_counter()
+                parts[0] += tb - ta
+                parts[1] += tc - tb
+                parts[2] += td - tc
             torch.cuda.synchronize()
             e2e_sec = time.perf_counter() - t0
             e2e_sec = reduce_over_ranks(dist, [e2e_sec], ["max"])[0]
             out["e2e"] = w.cells * 5 * args.e2e_steps * ws / e2e_sec
+            out["e2e_parts_ms"] = {k: 1e3 * v / args.e2e_steps for k, v in zip(("upload", "step", "download"), parts)}
             out["state_bytes"] = host_in.numel() * host_in.element_size()
         S.close()
     return out
 
 
-# Algorithmic work of one 2D stage per cell (counted from the operation counts of
-# the stage's equations): floating-point operations and, for the mixed
-# path, the minimum HBM bytes of the stage (3.2 state copies of 16 FP32 words plus
-# 4 compensation words per stage on average over the five SSP-RK54 stages).
-FLOPS_PER_CELL_STAGE = 3000
-BYTES_PER_CELL_STAGE_MIXED = 256
-BYTES_PER_CELL_STAGE_FP64 = 410
+# Algorithmic work of one 2D stage per cell. Flops: counted by the op-counting
+# build of the oracle on this flow (oracle/opcount_smooth2d.json, written by
+# oracle/count_ops.py): every distinct evaluation of the paper's formulas once,
+# trivial operations (exact 0 / +-1 operands) left out. Bytes: the minimum HBM
+# traffic of a stage, 3.2 state copies per stage on average over the five
+# SSP-RK54 stages, of 16 FP64 words (FP64 path) or 16 FP32 words plus 4 FP32
+# compensation words of the cell averages (mixed path).
+def _counted_flops():
+    with open(os.path.join(ROOT, "oracle", "opcount_smooth2d.json")) as f:
+        return float(json.load(f)["flops_per_cell_stage"])
+
+
+FLOPS_PER_CELL_STAGE = _counted_flops()
+BYTES_PER_CELL_STAGE_MIXED = 3.2 * 20 * 4
+BYTES_PER_CELL_STAGE_FP64 = 3.2 * 16 * 8
 
 
 if __name__ == "__main__":

@@ -51,16 +51,16 @@ class Opts(ctypes.Structure):
                 ("kappa_off", ctypes.c_int)]
 
 
-_lib = None
+_libs = {}
 
 
 def load(path: str = LIB_PATH):
-    """Load libafns.so (raises if it was not built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    """Load libafns.so, or the build at `path` (raises if it was not built)."""
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
-        raise RuntimeError("libafns.so is missing: build it with paper_2609_29081_b300.build.build()")
+        raise RuntimeError("%s is missing: build it with paper_2609_29081_b300.build.build()"
+                           % os.path.basename(path))
     L = ctypes.CDLL(path)
     vp, dp, ip, sp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), \
         ctypes.POINTER(ctypes.c_size_t)
@@ -92,7 +92,7 @@ def load(path: str = LIB_PATH):
     for f in EXPORTED:
         if f != "af_last_error":
             getattr(L, f).restype = ctypes.c_int
-    _lib = L
+    _libs[path] = L
     return L
 
 
@@ -106,9 +106,9 @@ def alu_peak(precision) -> float:
     return v.value
 
 
-def default_opts(dim, precision=FP64, limiter=LIM_S_PP, **kw) -> Opts:
+def default_opts(dim, precision=FP64, limiter=LIM_S_PP, lib=None, **kw) -> Opts:
     o = Opts()
-    load().af_opts_default(dim, ctypes.byref(o))
+    (lib or load()).af_opts_default(dim, ctypes.byref(o))
     o.precision = precision
     o.limiter = limiter
     for k, v in kw.items():
@@ -120,12 +120,12 @@ class Solver:
     """One AF-NS problem on cuda:0 (device memory owned by a torch tensor)."""
 
     def __init__(self, dim, n, lo, hi, gamma, mu, Pr, bc, precision=FP64, limiter=LIM_S_PP, stream=None,
-                 wall_speed=(0.0, 0.0, 0.0, 0.0), **opts):
+                 wall_speed=(0.0, 0.0, 0.0, 0.0), lib_path=LIB_PATH, **opts):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libafns needs a CUDA GPU; none is available")
         self.torch = torch
-        self.lib = load()
+        self.lib = load(lib_path)
         self.dim = dim
         self.n = (int(n[0]), int(n[1]) if dim == 2 else 1)
         g = Grid()
@@ -137,7 +137,7 @@ class Solver:
         for k in range(4):
             b.side[k] = bc[k] if k < len(bc) else 0
             b.wall_speed[k] = wall_speed[k]
-        self.opts = default_opts(dim, precision, limiter, **opts)
+        self.opts = default_opts(dim, precision, limiter, lib=self.lib, **opts)
         nbytes = ctypes.c_size_t(0)
         self._check(self.lib.af_workspace_bytes(ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(nbytes)))
         self.ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")

@@ -50,6 +50,7 @@ cudaError_t launch_tile_consts5(const StageArgs &A, const StageCoef *ks, void *o
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_to_f32(const Layout &L, const double *src, float *dst, cudaStream_t st);
+cudaError_t launch_pack_site_f32(const Layout &L, const float *buf, float *dst, int site, int w, int h, cudaStream_t st);
 cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h, int *flag,
                                    cudaStream_t st);
 cudaError_t launch_tile_consts(const StageArgs &A, void *out, int fp32, cudaStream_t st);
@@ -626,9 +627,20 @@ extern "C" af_status af_get_state_f32(afns_ctx *c, float *const site[4], int on_
     if (!c->has_state) return fail(c, AF_ESTATE, "no state set");
     cudaError_t e = do_ghost(c, c->U[0]);
     if (e != cudaSuccess) return cuda_check(c, e, "ghost fill");
-    af_status s = copy_sites_t<float>(c, c->U[0], site, on_device, 1);
-    if (s != AF_OK) return s;
-    e = cudaStreamSynchronize(c->st);
+    // one pass packs each site (device arrays: straight into them; host arrays:
+    // into the staging area, then one contiguous copy per site)
+    size_t off = 0;
+    for (int s = 0; s < c->L.nsite && e == cudaSuccess; ++s) {
+        if (!site[s]) return fail(c, AF_EINVAL, "null site pointer");
+        int w, h;
+        site_dims(c, s, &w, &h);
+        const size_t bytes = sizeof(float) * (size_t)c->L.nc * w * h;
+        float *dst = on_device ? site[s] : (float *)((char *)c->stage64 + off);
+        e = launch_pack_site_f32(c->L, (const float *)c->U[0], dst, s, w, h, c->st);
+        if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(site[s], dst, bytes, cudaMemcpyDeviceToHost, c->st);
+        off += align256(bytes);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_check(c, e, "af_get_state_f32");
     if (t) *t = c->t;
     return AF_OK;

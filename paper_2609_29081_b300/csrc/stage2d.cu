@@ -192,6 +192,28 @@ __global__ void k_unpack_site(Layout L, const T *src, T *buf, int site, int w, i
     }
 }
 
+// The inverse of k_unpack_site for a download: one DoF site's pitched planes
+// into a packed array (components in turn, x fastest, no ghosts), so that the
+// host copy is one contiguous transfer instead of one strided copy per component.
+template <class T>
+__global__ void k_pack_site(Layout L, const T *buf, T *dst, int site, int w, int h)
+{
+    const int wh = w * h, nc = L.nc;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < wh; e += gridDim.x * blockDim.x) {
+        const int j = e / w, i = e - j * w;
+        const long long off = L.dim == 2 ? cell_off(L, i, j) : 2 + i;
+        for (int c = 0; c < nc; ++c) dst[(long long)c * wh + e] = buf[plane_of(L, site, c) + off];
+    }
+}
+
+cudaError_t launch_pack_site_f32(const Layout &L, const float *buf, float *dst, int site, int w, int h, cudaStream_t st)
+{
+    const long long n = (long long)w * h;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148 * 16);
+    k_pack_site<float><<<blocks, 256, 0, st>>>(L, buf, dst, site, w, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unpack_site_f32(const Layout &L, const float *src, float *buf, int site, int w, int h, int *flag,
                                    cudaStream_t st)
 {

@@ -69,9 +69,24 @@ struct Tile2 {
     static_assert(4 * NCQ <= NL, "low-order cell records fit in the lattice state");
     template <class R>
     static constexpr size_t bytes() { return (size_t)total * 4 * sizeof(R); }
+    // Lattice records are stored row by row with every row de-interleaved: its HE
+    // even columns first, then its odd ones. Items on every other column (edge
+    // points, centres, face nodes) are then consecutive records, so the threads of
+    // a warp that take consecutive such items touch consecutive records (no
+    // shared-memory bank conflicts); lattice x-neighbours la +- 2 are records +- 1.
+    static constexpr int HE = (LX + 1) / 2;
+    __host__ __device__ static constexpr int col(int la) { return (la & 1) ? HE + (la >> 1) : (la >> 1); }
+    __host__ __device__ static constexpr int node(int la, int lb) { return lb * LX + col(la); }
+    // lattice column of position c of a de-interleaved row
+    __host__ __device__ static constexpr int col_inv(int c) { return c < HE ? 2 * c : 2 * (c - HE) + 1; }
+    // x gradients on columns [2, LX-3] of every row, de-interleaved likewise (the
+    // GXE even columns first); y gradients on rows [2, LY-3], full rows
+    static constexpr int GXE = (LX - 3) / 2;
+    __host__ __device__ static constexpr int gxcol(int la) { return (la & 1) ? GXE + ((la - 3) >> 1) : ((la - 2) >> 1); }
+    __host__ __device__ static constexpr int gxcol_inv(int c) { return c < GXE ? 2 + 2 * c : 3 + 2 * (c - GXE); }
     // index of the x / y gradient of lattice node (la, lb)
-    __host__ __device__ static constexpr int gx(int la, int lb) { return lb * GXW + (la - 2); }
-    __host__ __device__ static constexpr int gy(int la, int lb) { return (lb - 2) * LX + la; }
+    __host__ __device__ static constexpr int gx(int la, int lb) { return lb * GXW + gxcol(la); }
+    __host__ __device__ static constexpr int gy(int la, int lb) { return (lb - 2) * LX + col(la); }
 };
 
 // Four values of one lattice node, cell or face, stored together so that one

@@ -88,19 +88,23 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
 {
     using T = Tile2<TX, TY>;
     constexpr int LX = T::LX;
-    const int n = lb * LX + la;
+    const int n = T::node(la, lb);
+    // the x-line la-2 .. la+2 in the de-interleaved rows: the same-parity
+    // neighbours are records n -+ 1, the others sit in the row's other half
+    const int row = lb * LX;
+    const int xl[5] = {n - 1, row + T::col(la - 1), n, row + T::col(la + 1), n + 1};
     const V4<R> *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
     const R mu = tc.mu, ka = tc.ka;
     res[0] = res[1] = res[2] = res[3] = R(0);
     const R mu43 = R(4) / R(3) * mu, mu23 = R(2) / R(3) * mu;
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
-        const int st = l == 0 ? 1 : LX;
         V4<R> q[5], u[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            q[k] = sQ[n + (k - 2) * st];
-            u[k] = sU[n + (k - 2) * st];
+            const int m = l == 0 ? xl[k] : n + (k - 2) * LX;
+            q[k] = sQ[m];
+            u[k] = sU[m];
         }
         // --- inviscid: D_+ F^+ + D_- F^- = [sum_k dc_k F_k + alpha d4_k U_k] / (6 h)
         R al = R(0);
@@ -154,13 +158,13 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
         for (int k = 0; k < 5; ++k) {
             if (k == 2) continue;
             const R wc = (R)kDC[k];
-            if (l == 0) {   // K_12 d_y Z at the x-neighbours
-                const V4<R> gy = sGY[T::gy(la + k - 2, lb)];
+            if (l == 0) {   // K_12 d_y Z at the x-neighbours (y gradients: rows from 2)
+                const V4<R> gy = sGY[xl[k] - 2 * LX];
                 g1 += wc * (-mu23 * gy.y);
                 g2 += wc * (mu * gy.x);
                 g3 += wc * (mu * q[k].y * gy.x - mu23 * q[k].x * gy.y);
             } else {        // K_21 d_x Z at the y-neighbours
-                const V4<R> gx = sGX[T::gx(la, lb + k - 2)];
+                const V4<R> gx = sGX[T::gx(la, lb) + (k - 2) * T::GXW];
                 g1 += wc * (mu * gx.y);
                 g2 += wc * (-mu23 * gx.x);
                 g3 += wc * (-mu23 * q[k].y * gx.x + mu * q[k].x * gx.y);
@@ -199,8 +203,8 @@ __device__ __forceinline__ void node_flux(int l, R rho, R mx, R my, R E, R u, R 
 // lattice (point low-order update, Sec. 3.4 reading): Eq. (19) with S from
 // central differences on the lattice. FP64.
 template <class R, int TX, int TY>
-__device__ __noinline__ void lattice_llf(const V4<R> *sm, int l, int A, int B, double dx, double dy, double gamma, double mu,
-                            double ka, double F[4])
+__device__ __noinline__ void lattice_llf(const V4<R> *sm, int l, int laA, int lbA, int laB, int lbB, double dx,
+                                         double dy, double gamma, double mu, double ka, double F[4])
 {
     using T = Tile2<TX, TY>;
     constexpr int LX = T::LX;
@@ -208,10 +212,11 @@ __device__ __noinline__ void lattice_llf(const V4<R> *sm, int l, int A, int B, d
     double Fs[2][4], Us[2][4], rs[2], bs[2];
     const double gm1 = gamma - 1.0;
     for (int s = 0; s < 2; ++s) {
-        const int n = s == 0 ? A : B;
+        const int la = s == 0 ? laA : laB, lb = s == 0 ? lbA : lbB;
+        const int n = T::node(la, lb);
         const V4<R> un = sU[n];
         double Uv[4] = {(double)un.x, (double)un.y, (double)un.z, (double)un.w};
-        const V4<R> qe = sQ[n + 1], qw = sQ[n - 1], qn = sQ[n + LX], qs = sQ[n - LX];
+        const V4<R> qe = sQ[T::node(la + 1, lb)], qw = sQ[T::node(la - 1, lb)], qn = sQ[n + LX], qs = sQ[n - LX];
         // S: central differences on the lattice (spacing h/2, so 2 * (h/2) = h)
         double Sx[3] = {((double)qe.x - (double)qw.x) / dx, ((double)qe.y - (double)qw.y) / dx,
                         ((double)qe.z - (double)qw.z) / dx};
@@ -311,7 +316,6 @@ template <class R, int TX, int TY>
 __device__ __forceinline__ void face_high_order(V4<R> *sm, int f, int ntx, int nty, R mu, R ka)
 {
     using T = Tile2<TX, TY>;
-    constexpr int LX = T::LX;
     int l, fl, el;   // direction, face index along l (local), index along the face (local)
     if (f < T::NFX) {
         l = 0;
@@ -331,7 +335,7 @@ __device__ __forceinline__ void face_high_order(V4<R> *sm, int f, int ntx, int n
     for (int s = 0; s < 3; ++s) {
         const int la = l == 0 ? 2 + 2 * fl : 2 + 2 * el + s;
         const int lb = l == 0 ? 2 + 2 * el + s : 2 + 2 * fl;
-        const int n = lb * LX + la;
+        const int n = T::node(la, lb);
         const V4<R> U = sU[n], Qn = sQ[n], gx = sGX[T::gx(la, lb)], gy = sGY[T::gy(la, lb)];
         R Fn[4];
         node_flux<R>(l, U.x, U.y, U.z, U.w, Qn.x, Qn.y, Qn.z, gx.x, gx.y, gx.z, gy.x, gy.y, gy.z, mu, ka, Fn);
@@ -344,8 +348,9 @@ __device__ __forceinline__ void face_high_order(V4<R> *sm, int f, int ntx, int n
 }
 
 // Point nodes of the tile lattice (all nodes but the cell centres), numbered
-// compactly row pair by row pair: an even lattice row holds LX points (vertices
-// and y-edges), the odd row after it (LX + 1) / 2 (x-edges).
+// compactly row pair by row pair in the order of the de-interleaved records: an
+// even lattice row holds (LX + 1) / 2 vertices and then (LX - 1) / 2 y-edges,
+// the odd row after it (LX + 1) / 2 x-edges.
 template <int LX, int LY>
 __host__ __device__ constexpr int point_count()
 {
@@ -354,11 +359,11 @@ __host__ __device__ constexpr int point_count()
 template <int LX>
 __device__ __forceinline__ void point_node(int t, int &la, int &lb)
 {
-    constexpr int PAIR = LX + (LX + 1) / 2;
+    constexpr int HE = (LX + 1) / 2, PAIR = LX + HE;
     const int pr = t / PAIR, r = t - pr * PAIR;
     if (r < LX) {
         lb = 2 * pr;
-        la = r;
+        la = r < HE ? 2 * r : 2 * (r - HE) + 1;
     } else {
         lb = 2 * pr + 1;
         la = 2 * (r - LX);
@@ -376,10 +381,10 @@ struct PointFix {
     int blended, bad;
 };
 template <class R, class S, int TX, int TY>
-__device__ __noinline__ PointFix<S> point_island(const V4<R> *sm, int n, V4<R> un, V4<R> rr4, double dt, double eps,
-                                                 double gamma, double mu, double kappa, double dx, double dy)
+__device__ __noinline__ PointFix<S> point_island(const V4<R> *sm, int la, int lb, V4<R> un, V4<R> rr4, double dt,
+                                                 double eps, double gamma, double mu, double kappa, double dx,
+                                                 double dy)
 {
-    constexpr int LX = Tile2<TX, TY>::LX;
     PointFix<S> f{};
     const R Un[4] = {un.x, un.y, un.z, un.w}, r[4] = {rr4.x, rr4.y, rr4.z, rr4.w};
     double Ud[4], UH[4];
@@ -389,10 +394,10 @@ __device__ __noinline__ PointFix<S> point_island(const V4<R> *sm, int n, V4<R> u
     if (UH[0] >= eps && pH >= eps) return f;
     double UL[4] = {Ud[0], Ud[1], Ud[2], Ud[3]};
     for (int l = 0; l < 2; ++l) {
-        const int st = l == 0 ? 1 : LX;
+        const int ea = l == 0 ? 1 : 0, eb = l == 0 ? 0 : 1;
         double Fr[4], Fl[4];
-        lattice_llf<R, TX, TY>(sm, l, n, n + st, dx, dy, gamma, mu, kappa, Fr);
-        lattice_llf<R, TX, TY>(sm, l, n - st, n, dx, dy, gamma, mu, kappa, Fl);
+        lattice_llf<R, TX, TY>(sm, l, la, lb, la + ea, lb + eb, dx, dy, gamma, mu, kappa, Fr);
+        lattice_llf<R, TX, TY>(sm, l, la - ea, lb - eb, la, lb, dx, dy, gamma, mu, kappa, Fl);
         const double rl = dt / (0.5 * (l == 0 ? dx : dy));
         for (int c = 0; c < 4; ++c) UL[c] -= rl * (Fr[c] - Fl[c]);
     }
@@ -544,9 +549,9 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             const R *g = stg + site * BOX + (j - j0 + 2) * BX + (i - i0 + 2);
             const Q4 U = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]}
                                                           : benign;
-            sU[lb * LX + la] = U;
+            sU[T::node(la, lb)] = U;
             // the point's primitives right away (the centres get theirs in P1)
-            sQ[lb * LX + la] = node_prims(U, gm1_in, gam_in);
+            sQ[T::node(la, lb)] = node_prims(U, gm1_in, gam_in);
         }
         for (int t = tid; t < T::NCA; t += nth) {
             const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
@@ -559,7 +564,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         for (int t = tid; t < NP; t += nth) {
             int la, lb;
             point_node<LX>(t, la, lb);
-            const int t_ = lb * LX + la;
+            const int t_ = T::node(la, lb);
             const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
             const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
             const int site = ea ? (eb ? 3 : 1) : 2;
@@ -607,10 +612,13 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         Q4 U;
         if (t < T::NCQ) {
             const int qi = t % QX, qj = t / QX;
-            n = (2 * qj + 1) * LX + (2 * qi + 1);
+            // centre (2 qi + 1, 2 qj + 1); its x-neighbours 2 qi, 2 qi + 2 are the
+            // consecutive records w, w + 1 of the row's even half
+            n = T::node(2 * qi + 1, 2 * qj + 1);
+            const int w = (2 * qj + 1) * LX + qi;
             const Q4 ab = sA[(qj + 1) * CX + (qi + 1)];
-            const Q4 e0 = sU[n - 1], e1 = sU[n + 1], e2 = sU[n - LX], e3 = sU[n + LX];
-            const Q4 v0 = sU[n - LX - 1], v1 = sU[n - LX + 1], v2 = sU[n + LX - 1], v3 = sU[n + LX + 1];
+            const Q4 e0 = sU[w], e1 = sU[w + 1], e2 = sU[n - LX], e3 = sU[n + LX];
+            const Q4 v0 = sU[w - LX], v1 = sU[w + 1 - LX], v2 = sU[w + LX], v3 = sU[w + 1 + LX];
             R Uc[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -634,7 +642,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         } else {
             int la, lb;
             point_node<LX>(t - T::NCQ, la, lb);
-            n = lb * LX + la;
+            n = T::node(la, lb);
             U = sU[n];
         }
         sQ[n] = node_prims(U, gm1, gam);
@@ -646,8 +654,9 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     {
         const R i6x = tc.i6[0], i6y = tc.i6[1];
         for (int t = tid; t < T::NGX; t += nth) {
-            const int n = (t / T::GXW) * LX + 2 + t % T::GXW;
-            const Q4 a = sQ[n - 2], b = sQ[n - 1], c = sQ[n + 1], d = sQ[n + 2];
+            const int lb = t / T::GXW, la = T::gxcol_inv(t - lb * T::GXW), row = lb * LX;
+            const int n = T::node(la, lb);
+            const Q4 a = sQ[n - 1], b = sQ[row + T::col(la - 1)], c = sQ[row + T::col(la + 1)], d = sQ[n + 1];
             sGX[t] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6x, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6x,
                         (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6x, R(0)};
         }
@@ -681,8 +690,9 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             int la, lb;
             if (t < nreg) {
                 if (t < 2 * ncell) {
+                    // an even row: its ntx vertices, then its ntx y-edges
                     const int rw = t / (2 * ntx), k = t - rw * (2 * ntx);
-                    la = 2 + k;
+                    la = k < ntx ? 2 + 2 * k : 3 + 2 * (k - ntx);
                     lb = 2 + 2 * rw;
                 } else {
                     const int cc = t - 2 * ncell, jl = cc / ntx;
@@ -699,7 +709,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                 la = 2 + 2 * ntx;
                 lb = 2 + 2 * nty;
             }
-            const int n = lb * LX + la;
+            const int n = T::node(la, lb);
             // global position of the point; the combination inputs (u^n, the
             // auxiliary state) are loaded first so that their latency hides
             // behind the residual
@@ -735,8 +745,8 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                     mag[c] = fabs(Un[c]) + fabs(tc.dt * r[c]);
                 }
                 if (!surely_above(UHr, mag, gm1, tc.eps)) {
-                    const PointFix<S> f = point_island<R, S, TX, TY>(sm, n, Un4, Q4{r[0], r[1], r[2], r[3]}, dt, eps,
-                                                                      A.gamma, A.mu, A.kappa, L.dx, L.dy);
+                    const PointFix<S> f = point_island<R, S, TX, TY>(sm, la, lb, Un4, Q4{r[0], r[1], r[2], r[3]}, dt,
+                                                                      eps, A.gamma, A.mu, A.kappa, L.dx, L.dy);
                     if (f.bad) s_bad = 1;
                     if (f.blended) {
 #pragma unroll
@@ -1103,52 +1113,83 @@ __device__ __forceinline__ void cell_ij(const Layout &L, long long t, bool small
     }
 }
 
+// Per-block maxima of the two terms of Eq. (13) over the cell averages. Each
+// thread takes DT_UNROLL cells a block width apart (coalesced) and issues all of
+// their loads before any arithmetic, so that enough loads are in flight to
+// stream the four cell-average planes at HBM speed.
+constexpr int DT_UNROLL = 4;
 template <class S>
 __global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, double Pr, double cfl_c,
                                double cfl_v, double *partial)
 {
     double m1 = 0.0, m2 = 0.0;
     const long long nc = (long long)L.n1 * L.n2;
-    const double g1 = gamma - 1.0;
     const bool small = nc < (1ll << 31);   // 32-bit index arithmetic suffices
+    const long long stride = (long long)gridDim.x * blockDim.x * DT_UNROLL;
     if constexpr (sizeof(S) == 4) {
         // mixed path: FP32 arithmetic with one reciprocal per cell (the step size
         // needs no more than FP32 accuracy); maxima merged in FP64 below
-        const float gf = (float)gamma, g1f = (float)g1, muf = (float)mu;
+        const float gf = (float)gamma, g1f = (float)(gamma - 1.0), muf = (float)mu;
         const float rvc = fmaxf(4.f / 3.f, (float)(gamma / Pr)) * muf;
         const float ix = (float)(1.0 / (cfl_c * L.dx)), iy = (float)(1.0 / (cfl_c * L.dy));
         const float vx = (float)(1.0 / (cfl_v * L.dx * L.dx)), vy = (float)(1.0 / (cfl_v * L.dy * L.dy));
         float f1 = 0.f, f2 = 0.f;
-        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
-             t += (long long)gridDim.x * blockDim.x) {
-            int i, j;
-            cell_ij(L, t, small, i, j);
-            long long off = cell_off(L, i, j);
-            float rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
-            float my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
-            float r = 1.f / rho, u = mx * r, v = my * r;
-            float p = g1f * (E - 0.5f * (mx * u + my * v));
-            float c = sqrtf(gf * p * r);
-            f1 = fmaxf(f1, fmaxf((fabsf(u) + c) * ix, (fabsf(v) + c) * iy));
-            f2 = fmaxf(f2, rvc * r * fmaxf(vx, vy));
+        for (long long t0 = (long long)blockIdx.x * blockDim.x * DT_UNROLL + threadIdx.x; t0 < nc; t0 += stride) {
+            float rho[DT_UNROLL], mx[DT_UNROLL], my[DT_UNROLL], E[DT_UNROLL];
+#pragma unroll
+            for (int u = 0; u < DT_UNROLL; ++u) {
+                const long long t = t0 + (long long)u * blockDim.x;
+                rho[u] = 1.f, mx[u] = 0.f, my[u] = 0.f, E[u] = 0.f;
+                if (t < nc) {
+                    int i, j;
+                    cell_ij(L, t, small, i, j);
+                    const long long off = cell_off(L, i, j);
+                    rho[u] = buf[plane_of(L, 0, 0) + off], mx[u] = buf[plane_of(L, 0, 1) + off];
+                    my[u] = buf[plane_of(L, 0, 2) + off], E[u] = buf[plane_of(L, 0, 3) + off];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < DT_UNROLL; ++u) {
+                if (t0 + (long long)u * blockDim.x >= nc) continue;
+                const float r = 1.f / rho[u], uu = mx[u] * r, vv = my[u] * r;
+                const float p = g1f * (E[u] - 0.5f * (mx[u] * uu + my[u] * vv));
+                const float c = sqrtf(gf * p * r);
+                f1 = fmaxf(f1, fmaxf((fabsf(uu) + c) * ix, (fabsf(vv) + c) * iy));
+                f2 = fmaxf(f2, rvc * r * fmaxf(vx, vy));
+            }
         }
         m1 = f1;
         m2 = f2;
     } else {
-        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
-             t += (long long)gridDim.x * blockDim.x) {
-            int i, j;
-            cell_ij(L, t, small, i, j);
-            long long off = cell_off(L, i, j);
-            double rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
-            double my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
-            double p = g1 * (E - (mx * mx + my * my) / (2.0 * rho));
-            double c = sqrt(gamma * p / rho);
-            double rv = fmax(4.0 * mu / (3.0 * rho), gamma * mu / (Pr * rho));
-            double a = fmax((fabs(mx / rho) + c) / (cfl_c * L.dx), (fabs(my / rho) + c) / (cfl_c * L.dy));
-            double b = fmax(rv / (cfl_v * L.dx * L.dx), rv / (cfl_v * L.dy * L.dy));
-            m1 = fmax(m1, a);
-            m2 = fmax(m2, b);
+        // FP64: one division per cell (the reciprocal of rho), the CFL numbers and
+        // grid spacings folded into host-side constants
+        const double g1 = gamma - 1.0;
+        const double ix = 1.0 / (cfl_c * L.dx), iy = 1.0 / (cfl_c * L.dy);
+        const double vx = 1.0 / (cfl_v * L.dx * L.dx), vy = 1.0 / (cfl_v * L.dy * L.dy);
+        const double rvc = fmax(4.0 * mu / 3.0, gamma * mu / Pr) * fmax(vx, vy);
+        for (long long t0 = (long long)blockIdx.x * blockDim.x * DT_UNROLL + threadIdx.x; t0 < nc; t0 += stride) {
+            double rho[DT_UNROLL], mx[DT_UNROLL], my[DT_UNROLL], E[DT_UNROLL];
+#pragma unroll
+            for (int u = 0; u < DT_UNROLL; ++u) {
+                const long long t = t0 + (long long)u * blockDim.x;
+                rho[u] = 1.0, mx[u] = 0.0, my[u] = 0.0, E[u] = 0.0;
+                if (t < nc) {
+                    int i, j;
+                    cell_ij(L, t, small, i, j);
+                    const long long off = cell_off(L, i, j);
+                    rho[u] = buf[plane_of(L, 0, 0) + off], mx[u] = buf[plane_of(L, 0, 1) + off];
+                    my[u] = buf[plane_of(L, 0, 2) + off], E[u] = buf[plane_of(L, 0, 3) + off];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < DT_UNROLL; ++u) {
+                if (t0 + (long long)u * blockDim.x >= nc) continue;
+                const double r = 1.0 / rho[u], uu = mx[u] * r, vv = my[u] * r;
+                const double p = g1 * (E[u] - 0.5 * (mx[u] * uu + my[u] * vv));
+                const double c = sqrt(gamma * p * r);
+                m1 = fmax(m1, fmax((fabs(uu) + c) * ix, (fabs(vv) + c) * iy));
+                m2 = fmax(m2, rvc * r);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
