@@ -95,14 +95,15 @@ typedef struct {
                           dominates the bound, so the paper's 0.33/2 is unstable there */
     double eps;        /* positivity floor cap epsilon (Sec. 3.3); paper: 1e-13 */
     int max_halvings;  /* restarts allowed per step (Remark 3.2); default 30 */
-    int tile_x;        /* 2D tile width in cells: 16 (default) or 32 (AF_MIXED, tile_y 8) */
-    int tile_y;        /* 2D tile height in cells: 8 (default) or 16 (tile_x 16) */
+    int tile_x;        /* 2D tile width in cells: 16 (default) or 32 (AF_MIXED only) */
+    int tile_y;        /* 2D tile height in cells: 8 (default) or 16 */
     int source;        /* af_source: manufactured source term added to every stage */
     double src_p0;     /* p0 of the Taylor-Green source (paper: 100) */
     double ex_M0;      /* AF_BC_EXACT: upstream Mach number of the Becker shock (default 3) */
     double ex_uinf;    /* AF_BC_EXACT: translation velocity of the shock (default 0.2) */
-    int threads;       /* threads per CTA of the 2D stage kernel: 128 (default) or 256;
-                          af_tune may change tile_x / tile_y / threads */
+    int threads;       /* threads per CTA of the 2D stage kernel: 128 (default) or 256 (a
+                          32x16 tile always runs 512); af_tune may change tile_x / tile_y /
+                          threads */
     int kappa_off;     /* 1: no heat conduction, kappa = 0 exactly (the Sec. 4 first problem
                           of Stokes), and no conduction term in the CFL bound of Eq. (13);
                           single-problem contexts (af_create); default 0 */
@@ -183,8 +184,9 @@ af_status af_residual(afns_ctx *ctx, double dt, double *const L[4], int on_devic
 af_status af_get_limiter(afns_ctx *ctx, double *theta_s, double *theta_pp);
 
 /*
- * Autotuner of the 2D stage kernel launch (tiles of 16x8, 16x16 or 32x8 cells,
- * 256 or 128 threads per CTA; 32x8 tiles only in AF_MIXED): times each candidate
+ * Autotuner of the 2D stage kernel launch (tiles of 16x8, 16x16, 32x8 or 32x16
+ * cells, 256 or 128 threads per CTA, 512 for 32x16; 32-wide tiles only in
+ * AF_MIXED): times each candidate
  * on residual evaluations of the current state (the state is not changed) and
  * keeps the fastest for the following steps. Results do not depend on the
  * choice. Needs a state (AF_ESTATE otherwise). Outputs may be NULL.
@@ -218,6 +220,8 @@ af_status af_sizes(const afns_ctx *ctx, size_t *cells, size_t *faces, size_t *si
 af_status af_set_profiling(afns_ctx *ctx, int on);
 af_status af_get_profile(afns_ctx *ctx, double *stage_ms, long long *stage_launches, long long *launches);
 
+/* Description of the context's last failure; af_last_error(NULL) describes why
+ * the calling thread's last af_create refused its arguments. */
 const char *af_last_error(const afns_ctx *ctx);
 
 /*

@@ -46,7 +46,9 @@ def main():
         slope = (a - b) / (1.0 / n1 - 1.0 / n2)
         return b + slope * (1.0 / N_TARGET - 1.0 / n2)
 
-    step = extrap(s1, s2) + extrap(d1, d2)
+    # (a category absent at both sizes stays exactly zero; round-off of the
+    # extrapolation is cut at zero)
+    step = np.maximum(extrap(s1, s2) + extrap(d1, d2), 0.0)
     cats = O.OPC_CATEGORIES
     phases = {}
     for ph, name in O.OPC_PHASES.items():

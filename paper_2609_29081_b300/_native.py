@@ -167,7 +167,8 @@ class Solver:
 
     def _check(self, st):
         if st != AF_OK:
-            msg = self.lib.af_last_error(getattr(self, "ctx", None)) if getattr(self, "ctx", None) else b""
+            # without a context: why the last af_create refused its arguments
+            msg = self.lib.af_last_error(getattr(self, "ctx", None) or None)
             raise AfnsError(st, (msg or b"").decode())
         return st
 

@@ -64,6 +64,22 @@ __global__ void k_set_ctl(Ctl *ctl, double dt, double t, double t_end)
     ctl->notpp = 0;
     ctl->err = 0;
 }
+// The CFL step of Eq. (13) from the maxima the previous step's last stage
+// merged into the control block (same formula as k_dt_final), clipped to t_end
+// when asked; the rest as k_set_ctl.
+__global__ void k_set_ctl_cfl(Ctl *ctl, double t, double t_end, int clip)
+{
+    const double m1 = __longlong_as_double((long long)ctl->cfl_mx[0]);
+    const double m2 = __longlong_as_double((long long)ctl->cfl_mx[1]);
+    double dt = 1.0 / (m1 + m2);
+    ctl->dt_cfl = dt;
+    if (clip && t_end > t && t + dt > t_end) dt = t_end - t;
+    ctl->dt = dt;
+    ctl->t = t;
+    ctl->t_end = t_end;
+    ctl->notpp = 0;
+    ctl->err = 0;
+}
 __global__ void k_halve_ctl(Ctl *ctl)
 {
     ctl->dt *= 0.5;
@@ -106,7 +122,7 @@ struct afns_ctx {
     int threads = 128;           // threads per CTA of the stage kernel
     // TMA tensor maps of the five state buffers for the 2D stage kernel, per tile
     // shape (16x8, 32x8, 16x16): 3D (element of a row, row, plane), box (TX+4, TY+4, 4)
-    CUtensorMap maps[3][5];
+    CUtensorMap maps[4][5];      // per tile shape (16x8, 32x8, 16x16, 32x16) and buffer
     void *map_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // buffer of maps[.][k] (U[] rotates)
     void *tconst = nullptr;      // per-stage tile constants (2D stage kernel)
     int debug_extra_tx = 0;      // test hook of af_debug_tile_wait
@@ -127,6 +143,8 @@ struct afns_ctx {
     long long launches = 0;
     double t = 0;
     bool has_state = false;
+    CflConst cflk{};             // constants of Eq. (13)
+    bool cfl_ready = false;      // Ctl.cfl_mx holds the maxima of the current state (2D, after a step)
     std::string err;
 };
 
@@ -230,6 +248,10 @@ static bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t es
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Why the calling thread's last af_create was refused (there is no context to
+// hold the message).
+static thread_local std::string g_create_error;
+
 static af_status check_args(const af_grid *g, double gamma, double mu, double Pr, const af_bc *bc, const af_opts *o,
                             std::string *why)
 {
@@ -325,7 +347,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     std::string why;
     af_status s = check_args(grid, gamma, mu, Pr, bc, opts, &why);
     if (s != AF_OK) {
-        std::fprintf(stderr, "af_create: %s\n", why.c_str());
+        g_create_error = why;   // af_last_error(NULL) returns it
         return s;
     }
     afns_ctx *c = new (std::nothrow) afns_ctx();
@@ -343,6 +365,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->opts = *opts;
     c->st = (cudaStream_t)cuda_stream;
     make_layout(grid, c->bc, &c->L, bc->wall_speed);
+    c->cflk = cfl_const(gamma, mu, c->Pr_cfl, opts->cfl_c, opts->cfl_v, c->L.dx, c->L.dy);
     WsPlan p = plan_ws(c->L, opts);
     if (workspace) {
         if (workspace_bytes < p.total || ((uintptr_t)workspace & 255)) {
@@ -365,7 +388,7 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     c->L.comp = c->mixed ? 1 : 0;
     c->stage64 = c->mixed ? (double *)q : nullptr;
     c->tile_x = (c->mixed && opts->tile_x == 32) ? 32 : 16;
-    c->tile_y = (c->tile_x == 16 && opts->tile_y == 16) ? 16 : 8;
+    c->tile_y = opts->tile_y == 16 ? 16 : 8;
     c->threads = opts->threads == 256 ? 256 : 128;
     q += p.stage64;
     c->ctl = (Ctl *)q;
@@ -390,20 +413,18 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
     cudaError_t e = cudaMemsetAsync(c->ws, 0, p.total, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
-        std::fprintf(stderr, "af_create: %s\n", cudaGetErrorString(e));
         af_destroy(c);
         return AF_ECUDA;
     }
     if (c->dim == 2) {
         const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
         for (int k = 0; k < 5; ++k) c->map_buf[k] = c->U[k];
-        static const int shape[3][2] = {{16, 8}, {32, 8}, {16, 16}};
-        for (int w = 0; w < 3; ++w)
+        static const int shape[4][2] = {{16, 8}, {32, 8}, {16, 16}, {32, 16}};
+        for (int w = 0; w < 4; ++w)
             for (int k = 0; k < 5; ++k)
                 if (!make_stage_map(&c->maps[w][k], c->map_buf[k], c->L, esz, shape[w][0], shape[w][1])) {
-                    std::fprintf(stderr, "af_create: tensor map encoding failed\n");
                     af_destroy(c);
-                    return AF_ECUDA;
+                    return AF_ECUDA;   // tensor map encoding failed
                 }
     }
     *out = c;
@@ -424,7 +445,7 @@ af_status af_destroy(afns_ctx *c)
     return AF_OK;
 }
 
-const char *af_last_error(const afns_ctx *c) { return c ? c->err.c_str() : "null context"; }
+const char *af_last_error(const afns_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 af_status af_sizes(const afns_ctx *c, size_t *cells, size_t *faces, size_t *site_elems4)
 {
@@ -487,7 +508,7 @@ static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
     int k = 0;
     while (k < 5 && c->map_buf[k] != A.uin) ++k;
     if (k == 5) return cudaErrorInvalidValue;
-    const CUtensorMap *map = &c->maps[c->tile_x == 32 ? 1 : (c->tile_y == 16 ? 2 : 0)][k];
+    const CUtensorMap *map = &c->maps[c->tile_x == 32 ? (c->tile_y == 16 ? 3 : 1) : (c->tile_y == 16 ? 2 : 0)][k];
     if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->tile_y, c->threads, map, c->st);
     return launch_stage2d_fp64(A, c->tile_x, c->tile_y, c->threads, map, c->st);
 }
@@ -561,6 +582,7 @@ extern "C" af_status af_set_state(afns_ctx *c, const double *const site[4], int 
     if (*c->h_flag & 2) return fail(c, AF_EINVAL, "periodic duplicate point values differ from their partners");
     c->t = t;
     c->has_state = true;
+    c->cfl_ready = false;
     return AF_OK;
 }
 
@@ -617,6 +639,7 @@ extern "C" af_status af_set_state_f32(afns_ctx *c, const float *const site[4], i
     if (*c->h_flag & 2) return fail(c, AF_EINVAL, "periodic duplicate point values differ from their partners");
     c->t = t;
     c->has_state = true;
+    c->cfl_ready = false;
     return AF_OK;
 }
 
@@ -659,6 +682,7 @@ static StageArgs base_args(afns_ctx *c)
     A.limiter = c->opts.limiter;
     A.source = c->opts.source;
     A.src_p0 = c->opts.src_p0;
+    A.cfl = c->cflk;
     return A;
 }
 
@@ -733,6 +757,7 @@ static cudaError_t run_rk(afns_ctx *c)
     ks[3] = k;
     // u5 = acc + a44 u4 + b4 dt L(u4)
     k.acc = 0; k.a0 = 0; k.a2 = 1; k.a1 = kRK_a[4][4]; k.cl = kRK_b[4]; k.ct = ct[4];
+    k.cfl_out = c->dim == 2;   // u5 = u^{n+1}: its CFL maxima give the next step
     ks[4] = k;
     cudaError_t e;
     int slot0 = -1;
@@ -762,6 +787,7 @@ static af_status read_ctl(afns_ctx *c)
 static af_status step_from_ctl(afns_ctx *c, double *dt_taken, int *halvings)
 {
     int h = 0;
+    c->cfl_ready = false;
     for (;;) {
         cudaError_t e = run_rk(c);
         if (e != cudaSuccess) return cuda_check(c, e, "stage");
@@ -778,6 +804,7 @@ static af_status step_from_ctl(afns_ctx *c, double *dt_taken, int *halvings)
     }
     std::swap(c->U[0], c->U[1]);
     c->t += c->h_ctl->dt;
+    c->cfl_ready = c->dim == 2;   // the accepted attempt's last stage merged the maxima of U[0]
     if (dt_taken) *dt_taken = c->h_ctl->dt;
     if (halvings) *halvings = h;
     return AF_OK;
@@ -819,6 +846,8 @@ extern "C" af_status af_step(afns_ctx *c, double dt, double *dt_taken, int *halv
     c->launches += 1;
     if (dt > 0) {
         k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, dt, c->t, c->t);
+    } else if (c->cfl_ready) {
+        k_set_ctl_cfl<<<1, 1, 0, c->st>>>(c->ctl, c->t, c->t, 0);
     } else {
         k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, c->t);
         cudaError_t e = launch_dt(c, 0);
@@ -834,12 +863,16 @@ extern "C" af_status af_advance(afns_ctx *c, double t_end, int *steps, int *rest
     int ns = 0, nr = 0;
     af_status s = AF_OK;
     while (c->t < t_end) {
-        k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, t_end);
         c->launches += 1;
-        cudaError_t e = launch_dt(c, 1);
-        if (e != cudaSuccess) {
-            s = cuda_check(c, e, "dt");
-            break;
+        if (c->cfl_ready) {
+            k_set_ctl_cfl<<<1, 1, 0, c->st>>>(c->ctl, c->t, t_end, 1);
+        } else {
+            k_set_ctl<<<1, 1, 0, c->st>>>(c->ctl, 0.0, c->t, t_end);
+            cudaError_t e = launch_dt(c, 1);
+            if (e != cudaSuccess) {
+                s = cuda_check(c, e, "dt");
+                break;
+            }
         }
         int h = 0;
         s = step_from_ctl(c, nullptr, &h);
@@ -925,7 +958,9 @@ extern "C" af_status af_tune(afns_ctx *c, int *tile_x, int *tile_y, int *threads
         struct Cand {
             int tx, ty, th;
         };
-        const Cand cands[] = {{16, 8, 256}, {16, 8, 128}, {32, 8, 256}, {32, 8, 128}, {16, 16, 256}, {16, 16, 128}};
+        // 32-wide tiles in AF_MIXED only; the 32x16 tile always runs 512 threads
+        const Cand cands[] = {{16, 8, 256}, {16, 8, 128}, {32, 8, 256}, {32, 8, 128},
+                              {16, 16, 256}, {16, 16, 128}, {32, 16, 512}};
         cudaEvent_t a, b;
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
             return cuda_check(c, cudaGetLastError(), "tune events");

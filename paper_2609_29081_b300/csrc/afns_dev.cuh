@@ -76,6 +76,10 @@ struct Ctl {
     double dt_cfl;    // last CFL bound
     int notpp;        // a low-order state the limiters evaluate left G
     int err;          // a tile load of a stage kernel timed out (result invalid)
+    // the two maxima of Eq. (13) over the cell averages a step's last stage wrote
+    // (bit patterns of non-negative doubles, merged by atomic max): the next
+    // step's CFL bound without another pass over the state
+    unsigned long long cfl_mx[2];
 };
 
 // Parameters of the exact moving viscous shock used as 1D boundary data.
@@ -92,6 +96,7 @@ struct StageCoef {
     int acc;
     int residual;
     int wall_fix;
+    int cfl_out;      // 2D: merge the CFL maxima of the output cell averages into Ctl.cfl_mx
 };
 
 // --- ghost index images (two ghost layers; walls mirror about the boundary node,

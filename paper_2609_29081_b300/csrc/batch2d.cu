@@ -69,43 +69,17 @@ __global__ void k_batch_dt_partial(BatchProb *probs, const int *chunk_p, const i
     const long long nc = (long long)L.n1 * L.n2;
     const long long b0 = (long long)chunk_c[blockIdx.x] * kDtChunk;
     const long long b1 = min(nc, b0 + kDtChunk);
-    const double g = P.gamma, g1 = g - 1.0, mu = P.mu, Pr = P.Pr;
     const S *buf = (const S *)P.U[0];
-    double m1 = 0.0, m2 = 0.0;
-    if constexpr (sizeof(S) == 4) {
-        // mixed path: FP32 arithmetic, one reciprocal per cell
-        const float gf = (float)g, g1f = (float)g1;
-        const float rvc = fmaxf(4.f / 3.f, (float)(g / Pr)) * (float)mu;
-        const float ix = (float)(1.0 / (cfl_c * L.dx)), iy = (float)(1.0 / (cfl_c * L.dy));
-        const float vx = (float)(1.0 / (cfl_v * L.dx * L.dx)), vy = (float)(1.0 / (cfl_v * L.dy * L.dy));
-        float f1 = 0.f, f2 = 0.f;
-        // same expression, in the same order, as the single-problem kernel
-        for (long long t = b0 + threadIdx.x; t < b1; t += blockDim.x) {
-            int i = (int)(t % L.n1), j = (int)(t / L.n1);
-            long long off = cell_off(L, i, j);
-            float rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
-            float my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
-            float r = 1.f / rho, u = mx * r, v = my * r;
-            float p = g1f * (E - 0.5f * (mx * u + my * v));
-            float c = sqrtf(gf * p * r);
-            f1 = fmaxf(f1, fmaxf((fabsf(u) + c) * ix, (fabsf(v) + c) * iy));
-            f2 = fmaxf(f2, rvc * r * fmaxf(vx, vy));
-        }
-        m1 = f1;
-        m2 = f2;
-    } else {
-        for (long long t = b0 + threadIdx.x; t < b1; t += blockDim.x) {
-            int i = (int)(t % L.n1), j = (int)(t / L.n1);
-            long long off = cell_off(L, i, j);
-            double rho = buf[plane_of(L, 0, 0) + off], mx = buf[plane_of(L, 0, 1) + off];
-            double my = buf[plane_of(L, 0, 2) + off], E = buf[plane_of(L, 0, 3) + off];
-            double pr = g1 * (E - (mx * mx + my * my) / (2.0 * rho));
-            double c = sqrt(g * pr / rho);
-            double rv = fmax(4.0 * mu / (3.0 * rho), g * mu / (Pr * rho));
-            m1 = fmax(m1, fmax((fabs(mx / rho) + c) / (cfl_c * L.dx), (fabs(my / rho) + c) / (cfl_c * L.dy)));
-            m2 = fmax(m2, fmax(rv / (cfl_v * L.dx * L.dx), rv / (cfl_v * L.dy * L.dy)));
-        }
+    // the per-cell terms of the single-problem kernel (same constants, same order)
+    const CflConst k = cfl_const(P.gamma, P.mu, P.Pr, cfl_c, cfl_v, L.dx, L.dy);
+    S f1 = 0, f2 = 0;
+    for (long long t = b0 + threadIdx.x; t < b1; t += blockDim.x) {
+        int i = (int)(t % L.n1), j = (int)(t / L.n1);
+        long long off = cell_off(L, i, j);
+        cfl_terms(k, buf[plane_of(L, 0, 0) + off], buf[plane_of(L, 0, 1) + off], buf[plane_of(L, 0, 2) + off],
+                  buf[plane_of(L, 0, 3) + off], f1, f2);
     }
+    double m1 = f1, m2 = f2;
     for (int o = 16; o > 0; o >>= 1) {
         m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
         m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));

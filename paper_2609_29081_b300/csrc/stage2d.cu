@@ -53,8 +53,8 @@ cudaError_t launch_stage2d_t(const StageArgs &A, const CUtensorMap *map, cudaStr
 }
 
 // Tile shapes: FP64 16x8 or 16x16 (the 32x8 FP64 tile exceeds shared memory);
-// FP32 16x8, 32x8 or 16x16. threads: 256 or 128 per CTA (every phase loops over
-// its items).
+// FP32 16x8, 32x8, 16x16 or 32x16. threads: 256 or 128 per CTA (every phase
+// loops over its items); the 32x16 FP32 tile (185 KB, one CTA per SM) runs 512.
 cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map,
                                 cudaStream_t st)
 {
@@ -66,7 +66,8 @@ cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads,
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st)
 {
-    k_dt_partial2d<double><<<nparts, 256, 0, st>>>(L, buf, gamma, mu, Pr, cfl_c, cfl_v, partial);
+    k_dt_partial2d<double><<<nparts, 256, 0, st>>>(L, buf, cfl_const(gamma, mu, Pr, cfl_c, cfl_v, L.dx, L.dy),
+                                                   partial);
     k_dt_final<<<1, 256, 0, st>>>(partial, nparts, ctl, clip);
     return cudaGetLastError();
 }
@@ -121,6 +122,7 @@ namespace afns {
 cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map,
                                  cudaStream_t st)
 {
+    if (tx == 32 && ty == 16) return launch_stage2d_n<float, float, 32, 16, 512>(A, map, st);
     if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, map, st, threads > 0 ? threads : 256);
     if (ty == 16) return launch_stage2d_t<float, float, 16, 16>(A, map, st, threads > 0 ? threads : 256);
     return launch_stage2d_t<float, float, 16, 8>(A, map, st, threads > 0 ? threads : 256);
@@ -131,7 +133,8 @@ cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st) { r
 cudaError_t launch_dt2d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st)
 {
-    k_dt_partial2d<float><<<nparts, 256, 0, st>>>(L, buf, gamma, mu, Pr, cfl_c, cfl_v, partial);
+    k_dt_partial2d<float><<<nparts, 256, 0, st>>>(L, buf, cfl_const(gamma, mu, Pr, cfl_c, cfl_v, L.dx, L.dy),
+                                                  partial);
     return launch_dt_final(partial, nparts, ctl, clip, st);
 }
 

@@ -28,6 +28,54 @@
 
 namespace afns {
 
+// The constants of the two terms of Eq. (13) per cell average: the spacings
+// and CFL numbers folded in, so that a cell costs one reciprocal of rho. Formed
+// once on the host and shared by every kernel that evaluates the bound (the
+// CFL pass and the last stage of a step give the same step bit for bit).
+struct CflConst {
+    double g1, gamma, ix, iy, rvc;        // rvc = rho~ rho (Eq. (13)) x max_l 1 / (C^v dx_l^2)
+    float g1f, gf, ixf, iyf, rvcf;
+};
+__host__ __device__ inline CflConst cfl_const(double gamma, double mu, double Pr, double cfl_c, double cfl_v,
+                                              double dx, double dy)
+{
+    CflConst k;
+    k.g1 = gamma - 1.0;
+    k.gamma = gamma;
+    k.ix = 1.0 / (cfl_c * dx);
+    k.iy = 1.0 / (cfl_c * dy);
+    const double vx = 1.0 / (cfl_v * dx * dx), vy = 1.0 / (cfl_v * dy * dy);
+    const double a = 4.0 * mu / 3.0, b = gamma * mu / Pr;
+    k.rvc = (a > b ? a : b) * (vx > vy ? vx : vy);
+    k.g1f = (float)k.g1;
+    k.gf = (float)gamma;
+    k.ixf = (float)k.ix;
+    k.iyf = (float)k.iy;
+    k.rvcf = (float)k.rvc;
+    return k;
+}
+// One cell average's terms, merged into the running maxima m1 (inviscid) and
+// m2 (viscous); FP64 for the FP64 path, FP32 for the mixed path (the step size
+// needs no more than FP32 accuracy). A NaN term is ignored, as by fmax.
+__device__ __forceinline__ void cfl_terms(const CflConst &k, double rho, double mx, double my, double E, double &m1,
+                                          double &m2)
+{
+    const double r = 1.0 / rho, uu = mx * r, vv = my * r;
+    const double p = k.g1 * (E - 0.5 * (mx * uu + my * vv));
+    const double c = sqrt(k.gamma * p * r);
+    m1 = fmax(m1, fmax((fabs(uu) + c) * k.ix, (fabs(vv) + c) * k.iy));
+    m2 = fmax(m2, k.rvc * r);
+}
+__device__ __forceinline__ void cfl_terms(const CflConst &k, float rho, float mx, float my, float E, float &m1,
+                                          float &m2)
+{
+    const float r = 1.f / rho, uu = mx * r, vv = my * r;
+    const float p = k.g1f * (E - 0.5f * (mx * uu + my * vv));
+    const float c = sqrtf(k.gf * p * r);
+    m1 = fmaxf(m1, fmaxf((fabsf(uu) + c) * k.ixf, (fabsf(vv) + c) * k.iyf));
+    m2 = fmaxf(m2, k.rvcf * r);
+}
+
 struct StageArgs {
     Layout L;
     const void *uin;   // state being evaluated (ghosts filled)
@@ -42,6 +90,7 @@ struct StageArgs {
     int source;        // 0: none, 1: Taylor-Green energy source (Sec. 4 example)
     double src_p0;
     const void *tconst;  // per-stage tile constants computed by k_tile_consts (or null)
+    CflConst cfl;        // Eq. (13) constants (used when k.cfl_out)
     int extra_tx;        // test hook: bytes the tile-load barrier expects beyond the copies (0)
 };
 
@@ -292,8 +341,9 @@ template <class R>
 __device__ __forceinline__ bool surely_above(const R V[4], const R mag[4], R gm1, R eps)
 {
     if constexpr (sizeof(R) == 8) {
-        double p = gm1 * (V[3] - (V[1] * V[1] + V[2] * V[2]) / (2.0 * V[0]));
-        return V[0] >= eps && p >= eps;
+        // the exact test without a division: for rho >= eps > 0,
+        // p >= eps  <=>  (gamma-1) (2 rho E - |m|^2) >= 2 rho eps
+        return V[0] >= eps && gm1 * (2.0 * V[0] * V[3] - (V[1] * V[1] + V[2] * V[2])) >= 2.0 * V[0] * eps;
     } else {
         if (!(V[0] > 1e-2f * mag[0] + eps)) return false;
         // a screen with percent-level margins: the fast reciprocal (2 ulp) suffices
@@ -312,6 +362,13 @@ __device__ __forceinline__ bool admissible_input2(const double *U)
 {
     const bool fin = isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
     return fin && U[0] > 0.0 && 2.0 * U[0] * U[3] > U[1] * U[1] + U[2] * U[2];
+}
+
+// Finite, rho >= eps and p >= eps (eps > 0), decided without a division.
+__device__ __forceinline__ bool above_eps2(const double *U, double gm1, double eps)
+{
+    return isfinite(U[0] + U[1] + U[2] + U[3]) && U[0] >= eps &&
+           gm1 * (2.0 * U[0] * U[3] - (U[1] * U[1] + U[2] * U[2])) >= 2.0 * U[0] * eps;
 }
 
 __device__ __forceinline__ bool admissible2(const double *U, double gm1)
@@ -341,6 +398,16 @@ __device__ __forceinline__ void face_pp_fp64(const double FLc[4], const double F
         UHp[c] = UbL[c] - kk * (FLs[c] - FLc[c]);
         ULm[c] = UbR[c] - kk * (FRc[c] - FL[c]);
         UHm[c] = UbR[c] - kk * (FRc[c] - FLs[c]);
+    }
+    // The common case first, without a division: both low-order and both
+    // high-order states finite with density and pressure at or above eps (then
+    // every Theta is 1 and no low-order state leaves G); the pressure test is
+    // (gamma-1) (2 rho E - |m|^2) >= 2 rho eps for rho >= eps > 0.
+    if (above_eps2(ULp, g1, eps) && above_eps2(ULm, g1, eps) && above_eps2(UHp, g1, eps) &&
+        above_eps2(UHm, g1, eps)) {
+        *tpp = 1.0;
+        for (int c = 0; c < 4; ++c) Fout[c] = FL[c] + 1.0 * dF[c];
+        return;
     }
     if (!admissible2(ULp, g1) || !admissible2(ULm, g1)) *bad = true;
     double thr = fmin(theta_fn(ULp[0], UHp[0], fmin(eps, ULp[0])), theta_fn(ULm[0], UHm[0], fmin(eps, ULm[0])));

@@ -287,6 +287,8 @@ __global__ void k_tile_consts5(StageArgs A, StageCoef5 ks, char *out, int stride
     StageArgs B = A;
     B.k = ks.k[s];
     tile_const_init<R>(*reinterpret_cast<TileConst<R> *>(out + (size_t)s * stride_bytes), B, A.ctl->dt);
+    // the step's last stage merges the next CFL maxima from zero
+    if (s == 0) A.ctl->cfl_mx[0] = A.ctl->cfl_mx[1] = 0ull;
 }
 
 // (u, v, T, c) of a lattice node, one reciprocal of rho: u = m_x/rho,
@@ -953,6 +955,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     __syncthreads();
 
     // ---- P6: cell residual (flux differences, Eq. (23)), RK combination, store
+    S cfl1 = S(0), cfl2 = S(0);   // CFL maxima of the output cell averages (k.cfl_out)
     if constexpr (sizeof(S) == 8) {
         const double w = A.k.residual ? 1.0 : A.k.cl * dt;
         const double idx = L.idx[0], idy = L.idx[1];
@@ -971,6 +974,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             const double src = A.source ? tg_cell_source(A.mu, A.kappa, A.gamma, L.lo[0], L.lo[1], L.dx, L.dy,
                                                          i0 + il, j0 + jl, A.ctl->t + A.k.ct * dt)
                                         : 0.0;
+            S o4[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 double res =
@@ -985,8 +989,10 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                     const double ac = A.k.b2 * g2[c] + A.k.b1 * Uin + A.k.bl * dt * res;
                     ((S *)A.aux)[po] = (S)ac;
                 }
-                ((S *)A.out)[po] = (S)(v + w * res);
+                o4[c] = (S)(v + w * res);
+                ((S *)A.out)[po] = o4[c];
             }
+            if (A.k.cfl_out) cfl_terms(A.cfl, o4[0], o4[1], o4[2], o4[3], cfl1, cfl2);
         }
     } else {
         // mixed precision: cell averages are stored as hi + lo (float-float); the
@@ -1001,6 +1007,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         for (int t = tid; t < ntx * nty; t += nth) {
             const int il = t % ntx, jl = t / ntx;
             const long long off = cell_off(L, i0 + il, j0 + jl);
+            float o4[4] = {1.f, 0.f, 0.f, 1.f};
             // every global input of the cell first (one latency for all of them)
             float ulo[4], g0h[4], g0l[4], g2h[4], g2l[4];
 #pragma unroll
@@ -1053,7 +1060,22 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                 v = ff_add(v, inc);
                 out[po] = v.h;
                 out[pl] = v.l;
+                o4[c] = v.h;
             }
+            if (A.k.cfl_out) cfl_terms(A.cfl, o4[0], o4[1], o4[2], o4[3], cfl1, cfl2);
+        }
+    }
+    if (A.k.cfl_out) {
+        // merge the tile's maxima: warp, then one atomic per warp (non-negative
+        // doubles order like their bit patterns)
+        double m1 = cfl1, m2 = cfl2;
+        for (int o = 16; o > 0; o >>= 1) {
+            m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        if ((tid & 31) == 0) {
+            atomicMax(&A.ctl->cfl_mx[0], (unsigned long long)__double_as_longlong(m1));
+            atomicMax(&A.ctl->cfl_mx[1], (unsigned long long)__double_as_longlong(m2));
         }
     }
     if (tid == 0 && s_bad) atomicOr(&A.ctl->notpp, 1);
@@ -1119,79 +1141,31 @@ __device__ __forceinline__ void cell_ij(const Layout &L, long long t, bool small
 // stream the four cell-average planes at HBM speed.
 constexpr int DT_UNROLL = 4;
 template <class S>
-__global__ void k_dt_partial2d(Layout L, const S *buf, double gamma, double mu, double Pr, double cfl_c,
-                               double cfl_v, double *partial)
+__global__ void k_dt_partial2d(Layout L, const S *buf, CflConst k, double *partial)
 {
-    double m1 = 0.0, m2 = 0.0;
     const long long nc = (long long)L.n1 * L.n2;
     const bool small = nc < (1ll << 31);   // 32-bit index arithmetic suffices
     const long long stride = (long long)gridDim.x * blockDim.x * DT_UNROLL;
-    if constexpr (sizeof(S) == 4) {
-        // mixed path: FP32 arithmetic with one reciprocal per cell (the step size
-        // needs no more than FP32 accuracy); maxima merged in FP64 below
-        const float gf = (float)gamma, g1f = (float)(gamma - 1.0), muf = (float)mu;
-        const float rvc = fmaxf(4.f / 3.f, (float)(gamma / Pr)) * muf;
-        const float ix = (float)(1.0 / (cfl_c * L.dx)), iy = (float)(1.0 / (cfl_c * L.dy));
-        const float vx = (float)(1.0 / (cfl_v * L.dx * L.dx)), vy = (float)(1.0 / (cfl_v * L.dy * L.dy));
-        float f1 = 0.f, f2 = 0.f;
-        for (long long t0 = (long long)blockIdx.x * blockDim.x * DT_UNROLL + threadIdx.x; t0 < nc; t0 += stride) {
-            float rho[DT_UNROLL], mx[DT_UNROLL], my[DT_UNROLL], E[DT_UNROLL];
+    S f1 = 0, f2 = 0;
+    for (long long t0 = (long long)blockIdx.x * blockDim.x * DT_UNROLL + threadIdx.x; t0 < nc; t0 += stride) {
+        S rho[DT_UNROLL], mx[DT_UNROLL], my[DT_UNROLL], E[DT_UNROLL];
 #pragma unroll
-            for (int u = 0; u < DT_UNROLL; ++u) {
-                const long long t = t0 + (long long)u * blockDim.x;
-                rho[u] = 1.f, mx[u] = 0.f, my[u] = 0.f, E[u] = 0.f;
-                if (t < nc) {
-                    int i, j;
-                    cell_ij(L, t, small, i, j);
-                    const long long off = cell_off(L, i, j);
-                    rho[u] = buf[plane_of(L, 0, 0) + off], mx[u] = buf[plane_of(L, 0, 1) + off];
-                    my[u] = buf[plane_of(L, 0, 2) + off], E[u] = buf[plane_of(L, 0, 3) + off];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < DT_UNROLL; ++u) {
-                if (t0 + (long long)u * blockDim.x >= nc) continue;
-                const float r = 1.f / rho[u], uu = mx[u] * r, vv = my[u] * r;
-                const float p = g1f * (E[u] - 0.5f * (mx[u] * uu + my[u] * vv));
-                const float c = sqrtf(gf * p * r);
-                f1 = fmaxf(f1, fmaxf((fabsf(uu) + c) * ix, (fabsf(vv) + c) * iy));
-                f2 = fmaxf(f2, rvc * r * fmaxf(vx, vy));
+        for (int u = 0; u < DT_UNROLL; ++u) {
+            const long long t = t0 + (long long)u * blockDim.x;
+            rho[u] = S(1), mx[u] = S(0), my[u] = S(0), E[u] = S(0);
+            if (t < nc) {
+                int i, j;
+                cell_ij(L, t, small, i, j);
+                const long long off = cell_off(L, i, j);
+                rho[u] = buf[plane_of(L, 0, 0) + off], mx[u] = buf[plane_of(L, 0, 1) + off];
+                my[u] = buf[plane_of(L, 0, 2) + off], E[u] = buf[plane_of(L, 0, 3) + off];
             }
         }
-        m1 = f1;
-        m2 = f2;
-    } else {
-        // FP64: one division per cell (the reciprocal of rho), the CFL numbers and
-        // grid spacings folded into host-side constants
-        const double g1 = gamma - 1.0;
-        const double ix = 1.0 / (cfl_c * L.dx), iy = 1.0 / (cfl_c * L.dy);
-        const double vx = 1.0 / (cfl_v * L.dx * L.dx), vy = 1.0 / (cfl_v * L.dy * L.dy);
-        const double rvc = fmax(4.0 * mu / 3.0, gamma * mu / Pr) * fmax(vx, vy);
-        for (long long t0 = (long long)blockIdx.x * blockDim.x * DT_UNROLL + threadIdx.x; t0 < nc; t0 += stride) {
-            double rho[DT_UNROLL], mx[DT_UNROLL], my[DT_UNROLL], E[DT_UNROLL];
 #pragma unroll
-            for (int u = 0; u < DT_UNROLL; ++u) {
-                const long long t = t0 + (long long)u * blockDim.x;
-                rho[u] = 1.0, mx[u] = 0.0, my[u] = 0.0, E[u] = 0.0;
-                if (t < nc) {
-                    int i, j;
-                    cell_ij(L, t, small, i, j);
-                    const long long off = cell_off(L, i, j);
-                    rho[u] = buf[plane_of(L, 0, 0) + off], mx[u] = buf[plane_of(L, 0, 1) + off];
-                    my[u] = buf[plane_of(L, 0, 2) + off], E[u] = buf[plane_of(L, 0, 3) + off];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < DT_UNROLL; ++u) {
-                if (t0 + (long long)u * blockDim.x >= nc) continue;
-                const double r = 1.0 / rho[u], uu = mx[u] * r, vv = my[u] * r;
-                const double p = g1 * (E[u] - 0.5 * (mx[u] * uu + my[u] * vv));
-                const double c = sqrt(gamma * p * r);
-                m1 = fmax(m1, fmax((fabs(uu) + c) * ix, (fabs(vv) + c) * iy));
-                m2 = fmax(m2, rvc * r);
-            }
-        }
+        for (int u = 0; u < DT_UNROLL; ++u)
+            if (t0 + (long long)u * blockDim.x < nc) cfl_terms(k, rho[u], mx[u], my[u], E[u], f1, f2);
     }
+    double m1 = f1, m2 = f2;
     for (int o = 16; o > 0; o >>= 1) {
         m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
         m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));

@@ -64,6 +64,7 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     b.side[0], b.side[1] = 0, 1
     st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))
     assert st == N.AF_EINVAL and not ctx.value
+    assert b"periodic" in L.af_last_error(None)   # the refusal is described, nothing printed
     g.n[0] = 3
     b.side[1] = 0
     st = L.af_create(ctypes.byref(g), 1.4, 0.01, 0.72, ctypes.byref(b), None, None, None, 0, ctypes.byref(ctx))

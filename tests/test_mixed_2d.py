@@ -75,7 +75,7 @@ def test_launch_configuration_does_not_change_results(prec):
     w = W.random_smooth_2d((70, 37), seed=13, bc=(1, 1, 2, 3))
     p = MIXED if prec == "mixed" else FP64
     outs = []
-    for tx, ty in (((16, 8), (32, 8), (16, 16)) if prec == "mixed" else ((16, 8), (16, 16))):
+    for tx, ty in (((16, 8), (32, 8), (16, 16), (32, 16)) if prec == "mixed" else ((16, 8), (16, 16))):
         S = Solver.from_workload(w, precision=p, tile_x=tx, tile_y=ty)
         S.set_state(w.state)
         r0, _ = S.residual(1e-3)

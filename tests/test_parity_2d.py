@@ -201,3 +201,20 @@ def test_device_state_roundtrip():
     out = torch.empty_like(dev)
     S.get_state(out)
     assert torch.equal(out, dev) and S.t == 0.25
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cfl_step_from_the_last_stage_equals_the_cfl_pass(prec):
+    """After a step, the next CFL step comes from the maxima the step's last stage
+    merged while writing the cell averages; it equals the separate pass of
+    Eq. (13) over the same state bit for bit (walls, ragged tiles, both tile
+    shapes of the autotuner's default)."""
+    from paper_2609_29081_b300 import FP64, MIXED, Solver
+    w = W.random_smooth_2d((45, 29), seed=17, bc=(1, 1, 2, 3))
+    S = Solver.from_workload(w, precision=FP64 if prec == "fp64" else MIXED)
+    S.set_state(w.state)
+    for _ in range(3):
+        S.step(0.0)
+        ref = S.dt_max()             # the separate pass over the new state
+        dt, h = S.step(0.0)          # the step takes the merged maxima
+        assert h == 0 and dt == ref
