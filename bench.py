@@ -42,10 +42,10 @@ FP32_DERIVED_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read + write) per stage launch from ncu, with the digest of the
 # kernel sources they were taken on; reported only while the sources match.
 MEASURED_TRAFFIC = {
-    # ncu capture of one mixed stage launch of a timed step, 16x8 tiles, 128 threads
-    "mixed:4309747d6c77c39f": 131.55e6,
+    # ncu capture of one mixed stage launch of a timed step, 32x8 tiles, 256 threads
+    "mixed:527a89c4c305a931": 131.36e6,
     # ncu capture of one FP64 stage launch of a timed step, 16x8 tiles, 128 threads
-    "fp64:4309747d6c77c39f": 229.20e6,
+    "fp64:527a89c4c305a931": 229.32e6,
 }
 
 
@@ -321,6 +321,40 @@ def cpu_all_cores(n=128):
                       % (k, n, n, sec)}
 
 
+def tube_measure(args, steps, warmup):
+    """Walled shock tube (2000 x 1000, no-slip walls, symmetry on top), mixed
+    path, autotuned: `steps` timed CFL steps after the warm-up, with the extreme
+    density and pressure of every DoF afterwards (sub-record of the default line)."""
+    import torch
+    from paper_2609_29081_b300 import Solver, workloads as W
+    from paper_2609_29081_b300._native import MIXED
+    w = W.shock_tube_2d((2000, 1000))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        S = Solver.from_workload(w, precision=MIXED, stream=stream)
+        S.set_state(w.state)
+        tuned = S.tune()
+        warm = preheat(lambda: S.step(0.0), warmup)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        restarts = 0
+        for _ in range(steps):
+            restarts += S.step(0.0)[1]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = W.split_sites(S.get_state(), 2, *w.n)
+        S.close()
+    pmin = min(float((0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])).min()) for U in st)
+    rmin = min(float(U[0].min()) for U in st)
+    return {"value": w.cells * 5 * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup_steps_run": warm, "restarts": restarts, "tuned": tuned,
+            "workload": "2D viscous shock tube, walled box [0,1]x[0,0.5], 2000x1000, mu=1e-3, Pr=0.73, "
+                        "(120,0,0,120/1.4)|(1.2,0,0,1.2/1.4), no-slip x-lo/x-hi/y-lo, symmetry y-hi, mixed, "
+                        "timed CFL steps following the warm-up steps from t = 0",
+            "positivity": {"rho_min": rmin, "p_min": pmin}}
+
+
 def tube_arm(args, dist, rank, ws):
     """2D viscous shock tube in a walled box (no-slip walls, symmetry on top),
     2000 x 1000 cells, Re = 1000: K timed CFL steps after the warm-up; with
@@ -541,6 +575,8 @@ def main():
                     help="skip the accuracy ladder at the run length (128^2 .. 2048^2, FP64 and mixed)")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batched sub-record of the default line")
+    ap.add_argument("--no-tube", dest="tube", action="store_false",
+                    help="skip the walled shock-tube sub-record of the default line")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "tube", "ladder"])
     ap.add_argument("--t-end", type=float, default=0.0)
     ap.add_argument("--nprob", type=int, default=256)
@@ -632,6 +668,8 @@ def main():
                                         "the cell averages, GPU (%s) vs oracle, full grid" % args.precision,
                                 "value": float(np.abs(avg_g - avg_r).sum() / np.abs(avg_r).sum()),
                                 "linf": float(np.abs(avg_g - avg_r).max() / np.abs(avg_r).max())}
+    if args.tube:
+        line["tube"] = tube_measure(args, min(args.steps, 10), args.warmup)
     if args.batch:
         b = batch_measure(args, None, 0, 1, args.steps, args.warmup, args.nprob)
         line["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "workload", "cells", "tuned",
@@ -752,6 +790,12 @@ def single_run(args, w, precision, dist, ws, e2e):
             host_in = torch.from_numpy(S.get_state_f32() if f32 else S.get_state()).pin_memory()
             host_out = torch.empty_like(host_in).pin_memory()
             put, get = (S.set_state_f32, S.get_state_f32) if f32 else (S.set_state, S.get_state)
+            # untimed warm-up of the loop (the first transfers into freshly pinned
+            # host buffers run at half speed)
+            for _ in range(max(2, args.warmup)):
+                put(host_in.numpy())
+                S.step(0.0)
+                get(host_out.numpy())
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()

@@ -235,7 +235,8 @@ static EncodeTiledFn encode_tiled()
 // Tensor map of one 2D state buffer for tiles of TX x TY cells: the box covers
 // the tile's cells with two of halo in each direction (TX+4 elements from the
 // 16-byte aligned row start i0, TY+4 rows) and the 4 component planes of a site.
-static bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty)
+// (Also used by the batched path for its per-problem maps.)
+bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty)
 {
     EncodeTiledFn f = encode_tiled();
     if (!f) return false;

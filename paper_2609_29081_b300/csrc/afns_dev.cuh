@@ -207,9 +207,10 @@ __device__ __forceinline__ ff ff_from(double x)
 }
 
 // --- asynchronous global -> shared copies of single 4- or 8-byte elements
-// (cp.async): a thread issues all its tile loads without waiting on any, then
-// one wait and a barrier publish them. The host-compiler pass of this header
-// (never executed on the GPU) copies synchronously.
+// (cp.async), used for the per-tile constants: the words are issued while the
+// tile's TMA copies are in flight, then one wait and a barrier publish them. The
+// host-compiler pass of this header (never executed on the GPU) copies
+// synchronously.
 template <class T>
 __device__ __forceinline__ void cp_async_elem(T *dst_shared, const T *src_global)
 {

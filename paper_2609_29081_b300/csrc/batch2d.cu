@@ -40,7 +40,8 @@ struct BatchProb {
     int accepted;               // accepted steps
     int restarts;               // total rejected steps
     int failed;                 // max_halvings exceeded
-    int pad;
+    int buf_of[4];              // which of the problem's four buffers U[k] is (they rotate):
+                                // selects its tensor map
 };
 
 struct BatchArgs {
@@ -53,7 +54,12 @@ struct BatchArgs {
     double eps, c_s;
     int limiter;
     void *tconst;               // per-problem tile constants of the stage (TileConst<R>[nprob])
+    const CUtensorMap *maps;    // per problem, per buffer: tensor maps of this tile shape
 };
+
+// The tensor maps of the batch (device memory, filled on the host at creation):
+// problem p, tile shape s (0: 16x8, 1: 32x8), buffer b at [(p * kShapes + s) * 4 + b].
+constexpr int kShapes = 2;
 
 // --- CFL: chunks of 4096 cells
 constexpr int kDtChunk = 4096;
@@ -152,7 +158,7 @@ template <class R>
 __device__ __forceinline__ StageArgs batch_stage_args(const BatchArgs &B, int p)
 {
     const BatchProb &P = B.probs[p];
-    StageArgs A;
+    StageArgs A{};   // every field not set below is zero (no test hook, no CFL output)
     A.L = P.L;
     A.uin = P.U[B.in_idx];
     A.u0 = P.U[0];
@@ -185,19 +191,50 @@ __global__ void k_batch_tile_consts(BatchArgs B, int nprob)
 }
 
 // --- the persistent stage kernel over the work list
+// Work item `item` at or after `from` (stride gridDim.x) whose problem has not
+// failed, or nitems (uniform per block: every thread computes the same).
+__device__ __forceinline__ int next_live_item(const BatchArgs &B, int from)
+{
+    int item = from;
+    while (item < B.nitems && B.probs[B.item_p[item]].failed) item += gridDim.x;
+    return item;
+}
+
+// Each CTA walks its items as the single-problem kernel walks its tiles: the
+// tile is loaded by TMA through its problem's tensor map (buffer U[in_idx]), and
+// the next item's copies are issued as soon as the current tile's point phase is
+// done, through the next item's map, so they land while the face and cell
+// phases run. Every item loads its problem's tile constants and keeps its own
+// restart flag.
 template <class R, class S, int TX, int TY, int NTH>
 __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch_stage(BatchArgs B)
 {
-    extern __shared__ __align__(32) unsigned char smem_batch[];
+    extern __shared__ __align__(128) unsigned char smem_batch[];
     V4<R> *sm = reinterpret_cast<V4<R> *>(smem_batch);
-    for (int item = blockIdx.x; item < B.nitems; item += gridDim.x) {
+    constexpr int shape = TX == 32 ? 1 : 0;
+    int item = next_live_item(B, blockIdx.x);
+    for (int it = 0; item < B.nitems; ++it) {
         const int p = B.item_p[item];
         const BatchProb &P = B.probs[p];
-        if (P.failed) continue;   // uniform per block
         const int tile = B.item_t[item];
         const StageArgs A = batch_stage_args<R>(B, p);
-        stage_tile<R, S, TX, TY, NTH, false>(A, tile % P.tiles_x, tile / P.tiles_x, sm, nullptr);
+        const CUtensorMap *map = B.maps + ((size_t)p * kShapes + shape) * 4 + P.buf_of[B.in_idx];
+        const int next = next_live_item(B, item + gridDim.x);
+        int nbx = -1, nby = -1;
+        const CUtensorMap *nmap = nullptr;
+        if (next < B.nitems) {
+            const int np = B.item_p[next], nt = B.item_t[next];
+            const BatchProb &Q = B.probs[np];
+            nbx = nt % Q.tiles_x;
+            nby = nt / Q.tiles_x;
+            nmap = B.maps + ((size_t)np * kShapes + shape) * 4 + Q.buf_of[B.in_idx];
+        }
+        if (!stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm, map, it, nbx, nby, nmap,
+                                                   true))
+            break;
+        // the next item's records overwrite this item's
         __syncthreads();
+        item = next;
     }
 }
 
@@ -217,6 +254,9 @@ __global__ void k_batch_commit(BatchProb *probs, int nprob, int max_halvings)
         void *t = P.U[0];
         P.U[0] = P.U[1];
         P.U[1] = t;
+        const int b = P.buf_of[0];
+        P.buf_of[0] = P.buf_of[1];
+        P.buf_of[1] = b;
         P.ctl->t += P.ctl->dt;
         P.accepted += 1;
         P.rejected = 0;
@@ -273,6 +313,9 @@ __global__ void k_batch_validate(const S *buf, Layout L, double gamma, int *flag
 
 using namespace afns;
 
+// Tensor map of one state buffer for TX x TY tiles (afns.cu).
+bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty);
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -296,6 +339,7 @@ struct afb_ctx {
     void *d_tconst = nullptr;           // per-problem tile constants of the current stage
     int nchunks = 0;
     int *d_items[3][2] = {};            // per tile config: item_p, item_t (configs share the schedule arrays)
+    CUtensorMap *d_maps = nullptr;      // tensor maps of every problem, buffer and tile shape
     int nitems[3] = {0, 0, 0};
     double *stage64 = nullptr;          // FP64 staging of the largest problem
     int *d_flag = nullptr;
@@ -436,6 +480,7 @@ static cudaError_t issue_step(afb_ctx *c)
             k.bl = 0.063692468666290;
         }
         B.tconst = c->d_tconst;
+        B.maps = c->d_maps;
         if (c->mixed) k_batch_tile_consts<float><<<(c->nprob + 127) / 128, 128, 0, c->st>>>(B, c->nprob);
         else k_batch_tile_consts<double><<<(c->nprob + 127) / 128, 128, 0, c->st>>>(B, c->nprob);
         if ((e = launch_batch_stage(c, B)) != cudaSuccess) return e;
@@ -541,7 +586,7 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
         L.lo[1] = g.lo[1];
         layout_finish(&L);
         size_t st = al256((size_t)L.plane * (16 + (c->mixed ? 4 : 0)) * (c->mixed ? 4 : 8));
-        for (int k = 0; k < 4; ++k) P.U[k] = q, q += st;
+        for (int k = 0; k < 4; ++k) P.U[k] = q, P.buf_of[k] = k, q += st;
         P.U[4] = nullptr;
         P.ctl = (Ctl *)q;
         q += al256(sizeof(Ctl));
@@ -602,6 +647,23 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
         c->d_items[tb][0] = dp;
         c->d_items[tb][1] = dt_;
     }
+    // tensor maps of the four buffers of every problem for both tile shapes
+    if (e == cudaSuccess) {
+        std::vector<CUtensorMap> maps((size_t)nprob * kShapes * 4);
+        const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
+        static const int shape_tile[kShapes][2] = {{16, 8}, {32, 8}};
+        for (int p = 0; p < nprob && e == cudaSuccess; ++p)
+            for (int sh = 0; sh < kShapes && e == cudaSuccess; ++sh)
+                for (int b = 0; b < 4; ++b)
+                    if (!make_stage_map(&maps[((size_t)p * kShapes + sh) * 4 + b], c->h_probs[p].U[b],
+                                        c->h_probs[p].L, esz, shape_tile[sh][0], shape_tile[sh][1])) {
+                        e = cudaErrorInvalidValue;   // tensor map encoding failed
+                        break;
+                    }
+        if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_maps, sizeof(CUtensorMap) * maps.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+    }
     // tile counts of the 32-wide configuration live in the descriptors at launch time
     if (e == cudaSuccess) e = cudaMemcpy(c->d_probs, c->h_probs.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_flag, 64);
@@ -625,6 +687,7 @@ af_status afb_destroy(afb_ctx *c)
         for (int k = 0; k < 2; ++k)
             if (c->d_items[tb][k]) cudaFree(c->d_items[tb][k]);
     if (c->d_probs) cudaFree(c->d_probs);
+    if (c->d_maps) cudaFree(c->d_maps);
     if (c->d_chunk_p) cudaFree(c->d_chunk_p);
     if (c->d_tconst) cudaFree(c->d_tconst);
     if (c->h_flag) cudaFreeHost(c->h_flag);

@@ -487,11 +487,13 @@ __device__ __forceinline__ void tile_issue(const StageArgs &A, int bx, int by, R
 // nbx < 0) into the staging area as soon as that area is free (after the point
 // phase), so the copies land while the face and cell phases run. Returns false
 // when the tile's copies did not land in time (reported in Ctl.err): the CTA
-// stops. The element-copy path (batched kernel) loads its own tile and ignores
-// it / nbx / nby.
-template <class R, class S, int TX, int TY, int NTH, bool TMA>
+// stops. Several problems (the batched kernel): `ntmap` is the tensor map of the
+// next tile's problem (null: the same map), and with `multi` every tile loads
+// its problem's constants and starts its own restart flag.
+template <class R, class S, int TX, int TY, int NTH>
 __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm, const void *tmap,
-                                           int it = 0, int nbx = -1, int nby = -1)
+                                           int it = 0, int nbx = -1, int nby = -1, const void *ntmap = nullptr,
+                                           bool multi = false)
 {
     using T = Tile2<TX, TY>;
     using Q4 = V4<R>;
@@ -508,145 +510,98 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     constexpr int NP = point_count<LX, T::LY>();
     Q4 *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
     Q4 *sA = sm + T::oA, *sCQ = sm + T::oCQ, *sFX = sm + T::oFX, *sFY = sm + T::oFY;
-    const S *uin = (const S *)A.uin;
     const Q4 benign = {R(1), R(0), R(0), R(2.5)};
 
     // ---- P0: load point values and cell averages (two-node / two-cell halo)
     static_assert(sizeof(R) == sizeof(S), "tile and storage precision are the same");
-    if constexpr (TMA) {
-        // the tile's four 3D tensor copies land in a staging area in the
-        // gradient space (unused outside P3/P4); one pass turns the planes into
-        // the 4-component node and cell records
-        constexpr int BX = TX + 4, BY = TY + 4, BOX = 4 * BX * BY;
-        static_assert(BX == CX && BY == T::CY, "the box is the cell frame");
-        static_assert(4 * BOX * sizeof(R) + 128 <= (size_t)(T::NGX + T::NGY) * sizeof(Q4), "staging fits");
-        R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
-        // gas constants of the transposition pass: from the per-launch constants
-        // once they are in place (no FP64 instruction per tile)
-        const R gm1_in = it == 0 ? (R)(A.gamma - 1.0) : tc.gm1, gam_in = it == 0 ? (R)A.gamma : tc.gam;
-        if (it == 0) {
-            if (tid == 0) {
-                mbar_init(&s_bar, 1);
-                s_stop = 0;
-                s_bad = 0;
-            }
-            __syncthreads();
-            if (tid == 0) tile_issue<R, TX, TY>(A, bx, by, stg, tmap, &s_bar);
-            // while the copies are in flight: the per-launch constants
-            load_tile_consts<R>(tc, A, tid);
+    // the tile's four 3D tensor copies land in a staging area in the
+    // gradient space (unused outside P3/P4); one pass turns the planes into
+    // the 4-component node and cell records
+    constexpr int BX = TX + 4, BY = TY + 4, BOX = 4 * BX * BY;
+    static_assert(BX == CX && BY == T::CY, "the box is the cell frame");
+    static_assert(4 * BOX * sizeof(R) + 128 <= (size_t)(T::NGX + T::NGY) * sizeof(Q4), "staging fits");
+    R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
+    // gas constants of the transposition pass: from the per-launch constants
+    // once they are in place (no FP64 instruction per tile); several
+    // problems: from this tile's problem
+    const bool fresh = it == 0 || multi;   // this tile loads its constants
+    const R gm1_in = fresh ? (R)(A.gamma - 1.0) : tc.gm1, gam_in = fresh ? (R)A.gamma : tc.gam;
+    if (it == 0) {
+        if (tid == 0) {
+            mbar_init(&s_bar, 1);
+            s_stop = 0;
+            s_bad = 0;
         }
-        // a copy that has not landed after 2 s is reported, not waited for forever
-        if (!mbar_wait(&s_bar, (unsigned)(it & 1), 2000000000ull)) {
-            atomicOr(&A.ctl->err, 1);
-            s_stop = 1;
-        }
-        for (int t = tid; t < NP; t += nth) {
-            int la, lb;
-            point_node<LX>(t, la, lb);
-            const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
-            const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
-            const int site = ea ? (eb ? 3 : 1) : 2;
-            const int i = ea ? (a >> 1) : ((a - 1) >> 1);
-            const int j = eb ? (b >> 1) : ((b - 1) >> 1);
-            const R *g = stg + site * BOX + (j - j0 + 2) * BX + (i - i0 + 2);
-            const Q4 U = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]}
-                                                          : benign;
-            sU[T::node(la, lb)] = U;
-            // the point's primitives right away (the centres get theirs in P1)
-            sQ[T::node(la, lb)] = node_prims(U, gm1_in, gam_in);
-        }
-        for (int t = tid; t < T::NCA; t += nth) {
-            const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
-            const R *g = stg + t;
-            sA[t] = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]} : benign;
-        }
-    } else {
-        // element copies (cp.async): every load of the thread is in flight
-        // before the one wait
-        for (int t = tid; t < NP; t += nth) {
-            int la, lb;
-            point_node<LX>(t, la, lb);
-            const int t_ = T::node(la, lb);
-            const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
-            const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
-            const int site = ea ? (eb ? 3 : 1) : 2;
-            const int i = ea ? (a >> 1) : ((a - 1) >> 1);
-            const int j = eb ? (b >> 1) : ((b - 1) >> 1);
-            if (i <= L.n1 + 2 && j <= L.n2 + 2) {
-                const S *g = uin + plane_of(L, site, 0) + cell_off(L, i, j);
-                cp_async_elem(&sU[t_].x, g);
-                cp_async_elem(&sU[t_].y, g + L.plane);
-                cp_async_elem(&sU[t_].z, g + 2 * L.plane);
-                cp_async_elem(&sU[t_].w, g + 3 * L.plane);
-            } else {
-                sU[t_] = benign;
-            }
-        }
-        for (int t = tid; t < T::NCA; t += nth) {
-            const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
-            if (i <= L.n1 + 2 && j <= L.n2 + 2) {
-                const S *g = uin + plane_of(L, 0, 0) + cell_off(L, i, j);
-                cp_async_elem(&sA[t].x, g);
-                cp_async_elem(&sA[t].y, g + L.plane);
-                cp_async_elem(&sA[t].z, g + 2 * L.plane);
-                cp_async_elem(&sA[t].w, g + 3 * L.plane);
-            } else {
-                sA[t] = benign;
-            }
-        }
-        // while the tile loads are in flight: the per-tile constants
-        load_tile_consts<R>(tc, A, tid);
-        if (tid == 0) s_bad = 0;
-        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) tile_issue<R, TX, TY>(A, bx, by, stg, tmap, &s_bar);
     }
+    // while the copies are in flight: the constants (published by the
+    // cp.async wait and the barrier after the transposition)
+    if (fresh) load_tile_consts<R>(tc, A, tid);
+    if (multi && tid == 0) s_bad = 0;
+    // a copy that has not landed after 2 s is reported, not waited for forever
+    if (!mbar_wait(&s_bar, (unsigned)(it & 1), 2000000000ull)) {
+        atomicOr(&A.ctl->err, 1);
+        s_stop = 1;
+    }
+    for (int t = tid; t < NP; t += nth) {
+        int la, lb;
+        point_node<LX>(t, la, lb);
+        const int a = 2 * i0 - 2 + la, b = 2 * j0 - 2 + lb;
+        const bool ea = (a & 1) == 0, eb = (b & 1) == 0;
+        const int site = ea ? (eb ? 3 : 1) : 2;
+        const int i = ea ? (a >> 1) : ((a - 1) >> 1);
+        const int j = eb ? (b >> 1) : ((b - 1) >> 1);
+        const R *g = stg + site * BOX + (j - j0 + 2) * BX + (i - i0 + 2);
+        const Q4 U = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]}
+                                                      : benign;
+        sU[T::node(la, lb)] = U;
+        // the point's primitives right away (the centres get theirs in P1)
+        sQ[T::node(la, lb)] = node_prims(U, gm1_in, gam_in);
+    }
+    for (int t = tid; t < T::NCA; t += nth) {
+        const int i = i0 - 2 + t % CX, j = j0 - 2 + t / CX;
+        const R *g = stg + t;
+        sA[t] = (i <= L.n1 + 2 && j <= L.n2 + 2) ? Q4{g[0], g[BX * BY], g[2 * BX * BY], g[3 * BX * BY]} : benign;
+    }
+    if (fresh) cp_async_wait_all();
     __syncthreads();
-    if constexpr (TMA) {
-        if (s_stop) return false;
-    }
+    if (s_stop) return false;
     const double dt = A.ctl->dt;
     const R gam = tc.gam, gm1 = tc.gm1, mu = tc.mu, ka = tc.ka;
 
     // ---- P1: cell centres (Simpson inversion, Sec. 2.2) + centre scaling limiter
-    // (Remark 3.1), and the primitive quantities (u, v, T, c) of the centres; of
-    // the point nodes too unless the TMA path formed them in P0.
-    for (int t = tid; t < T::NCQ + (TMA ? 0 : NP); t += nth) {
-        int n;
-        Q4 U;
-        if (t < T::NCQ) {
-            const int qi = t % QX, qj = t / QX;
-            // centre (2 qi + 1, 2 qj + 1); its x-neighbours 2 qi, 2 qi + 2 are the
-            // consecutive records w, w + 1 of the row's even half
-            n = T::node(2 * qi + 1, 2 * qj + 1);
-            const int w = (2 * qj + 1) * LX + qi;
-            const Q4 ab = sA[(qj + 1) * CX + (qi + 1)];
-            const Q4 e0 = sU[w], e1 = sU[w + 1], e2 = sU[n - LX], e3 = sU[n + LX];
-            const Q4 v0 = sU[w - LX], v1 = sU[w + 1 - LX], v2 = sU[w + LX], v3 = sU[w + 1 + LX];
-            R Uc[4];
+    // (Remark 3.1), and the primitive quantities (u, v, T, c) of the centres (the
+    // point nodes got theirs in P0)
+    for (int t = tid; t < T::NCQ; t += nth) {
+        const int qi = t % QX, qj = t / QX;
+        // centre (2 qi + 1, 2 qj + 1); its x-neighbours 2 qi, 2 qi + 2 are the
+        // consecutive records w, w + 1 of the row's even half
+        const int n = T::node(2 * qi + 1, 2 * qj + 1);
+        const int w = (2 * qj + 1) * LX + qi;
+        const Q4 ab = sA[(qj + 1) * CX + (qi + 1)];
+        const Q4 e0 = sU[w], e1 = sU[w + 1], e2 = sU[n - LX], e3 = sU[n + LX];
+        const Q4 v0 = sU[w - LX], v1 = sU[w + 1 - LX], v2 = sU[w + LX], v3 = sU[w + 1 + LX];
+        R Uc[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const R edges = comp(e0, c) + comp(e1, c) + comp(e2, c) + comp(e3, c);
-                const R verts = comp(v0, c) + comp(v1, c) + comp(v2, c) + comp(v3, c);
-                Uc[c] = (R(36) * comp(ab, c) - R(4) * edges - verts) / R(16);
-            }
-            if (A.limiter != LIM_NONE) {
-                R mag[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    mag[c] = R(4) * (fabs(comp(ab, c)) + fabs(comp(e0, c)) + fabs(comp(e1, c)) + fabs(comp(e2, c)) +
-                                     fabs(comp(e3, c)));
-                if (!surely_above(Uc, mag, gm1, tc.eps)) {
-                    const V4<R> cf = centre_island<R>(ab, e0, e1, e2, e3, v0, v1, v2, v3, A.gamma - 1.0, eps);
-                    Uc[0] = cf.x, Uc[1] = cf.y, Uc[2] = cf.z, Uc[3] = cf.w;
-                }
-            }
-            U = Q4{Uc[0], Uc[1], Uc[2], Uc[3]};
-            sU[n] = U;
-        } else {
-            int la, lb;
-            point_node<LX>(t - T::NCQ, la, lb);
-            n = T::node(la, lb);
-            U = sU[n];
+        for (int c = 0; c < 4; ++c) {
+            const R edges = comp(e0, c) + comp(e1, c) + comp(e2, c) + comp(e3, c);
+            const R verts = comp(v0, c) + comp(v1, c) + comp(v2, c) + comp(v3, c);
+            Uc[c] = (R(36) * comp(ab, c) - R(4) * edges - verts) / R(16);
         }
+        if (A.limiter != LIM_NONE) {
+            R mag[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                mag[c] = R(4) * (fabs(comp(ab, c)) + fabs(comp(e0, c)) + fabs(comp(e1, c)) + fabs(comp(e2, c)) +
+                                 fabs(comp(e3, c)));
+            if (!surely_above(Uc, mag, gm1, tc.eps)) {
+                const V4<R> cf = centre_island<R>(ab, e0, e1, e2, e3, v0, v1, v2, v3, A.gamma - 1.0, eps);
+                Uc[0] = cf.x, Uc[1] = cf.y, Uc[2] = cf.z, Uc[3] = cf.w;
+            }
+        }
+        const Q4 U = Q4{Uc[0], Uc[1], Uc[2], Uc[3]};
+        sU[n] = U;
         sQ[n] = node_prims(U, gm1, gam);
     }
     __syncthreads();
@@ -794,12 +749,10 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     // low-order cell records overwrite them, and the next tile's copies go to the
     // staging area (ordered after this tile's generic accesses to it)
     __syncthreads();
-    if constexpr (TMA) {
-        if (tid == 0 && nbx >= 0) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
-            tile_issue<R, TX, TY>(A, nbx, nby, stg, tmap, &s_bar);
-        }
+    if (tid == 0 && nbx >= 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
+        tile_issue<R, TX, TY>(A, nbx, nby, stg, ntmap ? ntmap : tmap, &s_bar);
     }
 
     // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
@@ -1110,7 +1063,7 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int tn = t + gridDim.x;
         const bool more = tn < ntiles;
-        if (!stage_tile<R, S, TX, TY, NTH, true>(A, t % tiles_x, t / tiles_x, reinterpret_cast<V4<R> *>(smem_raw),
+        if (!stage_tile<R, S, TX, TY, NTH>(A, t % tiles_x, t / tiles_x, reinterpret_cast<V4<R> *>(smem_raw),
                                                  &tmap, it, more ? tn % tiles_x : -1, more ? tn / tiles_x : -1))
             break;
         // the next tile's records overwrite this tile's

@@ -218,3 +218,4 @@ def test_cfl_step_from_the_last_stage_equals_the_cfl_pass(prec):
         ref = S.dt_max()             # the separate pass over the new state
         dt, h = S.step(0.0)          # the step takes the merged maxima
         assert h == 0 and dt == ref
+
