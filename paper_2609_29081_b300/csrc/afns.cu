@@ -24,7 +24,8 @@ constexpr int kTconstStride = (int)((sizeof(afns::TileConst<double>) + 255) / 25
 }
 
 namespace afns {
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map, cudaStream_t st);
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *const *maps,
+                                cudaStream_t st);
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
                              double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
 cudaError_t launch_ghost2d_fp64(const Layout &L, double *buf, cudaStream_t st);
@@ -43,7 +44,8 @@ cudaError_t launch_validate1d_f32(const Layout &L, const float *buf, double gamm
 cudaError_t launch_stage1d_mixed(const StageArgs &A, cudaStream_t st);
 cudaError_t launch_dt1d_f32(const Layout &L, const float *buf, double gamma, double mu, double Pr, double cfl_c,
                             double cfl_v, double *partial, int nparts, Ctl *ctl, int clip, cudaStream_t st);
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map, cudaStream_t st);
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *const *maps,
+                                 cudaStream_t st);
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st);
 cudaError_t launch_tile_consts5(const StageArgs &A, const StageCoef *ks, void *out, int stride_bytes, int fp32,
                                 cudaStream_t st);
@@ -123,6 +125,7 @@ struct afns_ctx {
     // TMA tensor maps of the five state buffers for the 2D stage kernel, per tile
     // shape (16x8, 32x8, 16x16): 3D (element of a row, row, plane), box (TX+4, TY+4, 4)
     CUtensorMap maps[4][5];      // per tile shape (16x8, 32x8, 16x16, 32x16) and buffer
+    CUtensorMap rmaps[4][5];     // the same, with the row box of the cell-update inputs
     void *map_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // buffer of maps[.][k] (U[] rotates)
     void *tconst = nullptr;      // per-stage tile constants (2D stage kernel)
     int debug_extra_tx = 0;      // test hook of af_debug_tile_wait
@@ -235,14 +238,17 @@ static EncodeTiledFn encode_tiled()
 // Tensor map of one 2D state buffer for tiles of TX x TY cells: the box covers
 // the tile's cells with two of halo in each direction (TX+4 elements from the
 // 16-byte aligned row start i0, TY+4 rows) and the 4 component planes of a site.
+// With `rows` (cell-update inputs) the box is TX+4 elements by the tile's TY
+// rows, and the planes reach the compensation planes of a mixed buffer.
 // (Also used by the batched path for its per-problem maps.)
-bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty)
+bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty, bool rows)
 {
     EncodeTiledFn f = encode_tiled();
     if (!f) return false;
-    const cuuint64_t gdim[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)L.nsite * L.nc};
+    const cuuint64_t planes = (cuuint64_t)L.nsite * L.nc + (rows && esz == 4 ? (cuuint64_t)L.nc : 0);
+    const cuuint64_t gdim[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, planes};
     const cuuint64_t gstride[2] = {(cuuint64_t)L.pitch * esz, (cuuint64_t)L.plane * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)(tx + 4), (cuuint32_t)(ty + 4), 4};
+    const cuuint32_t box[3] = {(cuuint32_t)(tx + 4), (cuuint32_t)(rows ? ty : ty + 4), 4};
     const cuuint32_t estride[3] = {1, 1, 1};
     return f(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, buf, gdim, gstride, box,
              estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -423,7 +429,8 @@ af_status af_create(const af_grid *grid, double gamma, double mu, double Pr, con
         static const int shape[4][2] = {{16, 8}, {32, 8}, {16, 16}, {32, 16}};
         for (int w = 0; w < 4; ++w)
             for (int k = 0; k < 5; ++k)
-                if (!make_stage_map(&c->maps[w][k], c->map_buf[k], c->L, esz, shape[w][0], shape[w][1])) {
+                if (!make_stage_map(&c->maps[w][k], c->map_buf[k], c->L, esz, shape[w][0], shape[w][1], false) ||
+                    !make_stage_map(&c->rmaps[w][k], c->map_buf[k], c->L, esz, shape[w][0], shape[w][1], true)) {
                     af_destroy(c);
                     return AF_ECUDA;   // tensor map encoding failed
                 }
@@ -506,12 +513,18 @@ static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
 {
     c->launches += 1;
     if (c->dim == 1) return c->mixed ? launch_stage1d_mixed(A, c->st) : launch_stage1d_fp64(A, c->st);
-    int k = 0;
-    while (k < 5 && c->map_buf[k] != A.uin) ++k;
-    if (k == 5) return cudaErrorInvalidValue;
-    const CUtensorMap *map = &c->maps[c->tile_x == 32 ? (c->tile_y == 16 ? 3 : 1) : (c->tile_y == 16 ? 2 : 0)][k];
-    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->tile_y, c->threads, map, c->st);
-    return launch_stage2d_fp64(A, c->tile_x, c->tile_y, c->threads, map, c->st);
+    auto slot = [&](const void *b) {
+        int k = 0;
+        while (k < 5 && c->map_buf[k] != b) ++k;
+        return k;
+    };
+    const int k = slot(A.uin), k0 = slot(A.u0), k2 = slot(A.aux);
+    if (k == 5 || k0 == 5 || k2 == 5) return cudaErrorInvalidValue;
+    const int w = c->tile_x == 32 ? (c->tile_y == 16 ? 3 : 1) : (c->tile_y == 16 ? 2 : 0);
+    // the tile map of the stage input, the row maps of u^n and of the auxiliary state
+    const CUtensorMap *maps[3] = {&c->maps[w][k], &c->rmaps[w][k0], &c->rmaps[w][k2]};
+    if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->tile_y, c->threads, maps, c->st);
+    return launch_stage2d_fp64(A, c->tile_x, c->tile_y, c->threads, maps, c->st);
 }
 
 // Public FP64 site arrays <-> state buffer. The FP64 path copies directly; the

@@ -55,6 +55,7 @@ struct BatchArgs {
     int limiter;
     void *tconst;               // per-problem tile constants of the stage (TileConst<R>[nprob])
     const CUtensorMap *maps;    // per problem, per buffer: tensor maps of this tile shape
+    const CUtensorMap *rmaps;   // the same with the row box of the cell-update inputs
 };
 
 // The tensor maps of the batch (device memory, filled on the host at creation):
@@ -218,7 +219,8 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch
         const BatchProb &P = B.probs[p];
         const int tile = B.item_t[item];
         const StageArgs A = batch_stage_args<R>(B, p);
-        const CUtensorMap *map = B.maps + ((size_t)p * kShapes + shape) * 4 + P.buf_of[B.in_idx];
+        const size_t mb = ((size_t)p * kShapes + shape) * 4;
+        const CUtensorMap *map = B.maps + mb + P.buf_of[B.in_idx];
         const int next = next_live_item(B, item + gridDim.x);
         int nbx = -1, nby = -1;
         const CUtensorMap *nmap = nullptr;
@@ -229,8 +231,8 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch
             nby = nt / Q.tiles_x;
             nmap = B.maps + ((size_t)np * kShapes + shape) * 4 + Q.buf_of[B.in_idx];
         }
-        if (!stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm, map, it, nbx, nby, nmap,
-                                                   true))
+        if (!stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm, map, it, nbx, nby, nmap, true,
+                                           B.rmaps + mb + P.buf_of[0], B.rmaps + mb + P.buf_of[2]))
             break;
         // the next item's records overwrite this item's
         __syncthreads();
@@ -314,7 +316,7 @@ __global__ void k_batch_validate(const S *buf, Layout L, double gamma, int *flag
 using namespace afns;
 
 // Tensor map of one state buffer for TX x TY tiles (afns.cu).
-bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty);
+bool make_stage_map(CUtensorMap *m, void *buf, const Layout &L, size_t esz, int tx, int ty, bool rows);
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -340,6 +342,7 @@ struct afb_ctx {
     int nchunks = 0;
     int *d_items[3][2] = {};            // per tile config: item_p, item_t (configs share the schedule arrays)
     CUtensorMap *d_maps = nullptr;      // tensor maps of every problem, buffer and tile shape
+    CUtensorMap *d_rmaps = nullptr;     // the same with the row box of the cell-update inputs
     int nitems[3] = {0, 0, 0};
     double *stage64 = nullptr;          // FP64 staging of the largest problem
     int *d_flag = nullptr;
@@ -481,6 +484,7 @@ static cudaError_t issue_step(afb_ctx *c)
         }
         B.tconst = c->d_tconst;
         B.maps = c->d_maps;
+        B.rmaps = c->d_rmaps;
         if (c->mixed) k_batch_tile_consts<float><<<(c->nprob + 127) / 128, 128, 0, c->st>>>(B, c->nprob);
         else k_batch_tile_consts<double><<<(c->nprob + 127) / 128, 128, 0, c->st>>>(B, c->nprob);
         if ((e = launch_batch_stage(c, B)) != cudaSuccess) return e;
@@ -649,20 +653,27 @@ af_status afb_create(int nprob, const af_grid *grids, const double *gamma, const
     }
     // tensor maps of the four buffers of every problem for both tile shapes
     if (e == cudaSuccess) {
-        std::vector<CUtensorMap> maps((size_t)nprob * kShapes * 4);
+        std::vector<CUtensorMap> maps((size_t)nprob * kShapes * 4), rmaps(maps.size());
         const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
         static const int shape_tile[kShapes][2] = {{16, 8}, {32, 8}};
         for (int p = 0; p < nprob && e == cudaSuccess; ++p)
             for (int sh = 0; sh < kShapes && e == cudaSuccess; ++sh)
-                for (int b = 0; b < 4; ++b)
-                    if (!make_stage_map(&maps[((size_t)p * kShapes + sh) * 4 + b], c->h_probs[p].U[b],
-                                        c->h_probs[p].L, esz, shape_tile[sh][0], shape_tile[sh][1])) {
+                for (int b = 0; b < 4; ++b) {
+                    const size_t m = ((size_t)p * kShapes + sh) * 4 + b;
+                    if (!make_stage_map(&maps[m], c->h_probs[p].U[b], c->h_probs[p].L, esz, shape_tile[sh][0],
+                                        shape_tile[sh][1], false) ||
+                        !make_stage_map(&rmaps[m], c->h_probs[p].U[b], c->h_probs[p].L, esz, shape_tile[sh][0],
+                                        shape_tile[sh][1], true)) {
                         e = cudaErrorInvalidValue;   // tensor map encoding failed
                         break;
                     }
+                }
         if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_maps, sizeof(CUtensorMap) * maps.size());
+        if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_rmaps, sizeof(CUtensorMap) * rmaps.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_rmaps, rmaps.data(), sizeof(CUtensorMap) * rmaps.size(), cudaMemcpyHostToDevice);
     }
     // tile counts of the 32-wide configuration live in the descriptors at launch time
     if (e == cudaSuccess) e = cudaMemcpy(c->d_probs, c->h_probs.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice);
@@ -688,6 +699,7 @@ af_status afb_destroy(afb_ctx *c)
             if (c->d_items[tb][k]) cudaFree(c->d_items[tb][k]);
     if (c->d_probs) cudaFree(c->d_probs);
     if (c->d_maps) cudaFree(c->d_maps);
+    if (c->d_rmaps) cudaFree(c->d_rmaps);
     if (c->d_chunk_p) cudaFree(c->d_chunk_p);
     if (c->d_tconst) cudaFree(c->d_tconst);
     if (c->h_flag) cudaFreeHost(c->h_flag);

@@ -17,7 +17,7 @@ cudaError_t launch_ghost2d(const Layout &L, S *buf, cudaStream_t st)
 }
 
 template <class R, class S, int TX, int TY, int NTH>
-cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *map, cudaStream_t st)
+cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *const *maps, cudaStream_t st)
 {
     using T = Tile2<TX, TY>;
     size_t smem = T::template bytes<R>();
@@ -40,27 +40,27 @@ cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *map, cudaStr
     }
     const long long ntiles = (long long)((A.L.n1 + TX - 1) / TX) * ((A.L.n2 + TY - 1) / TY);
     const int grid = (int)std::min<long long>(ntiles, resident);
-    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A, *map);
+    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A, *maps[0], *maps[1], *maps[2]);
     return cudaGetLastError();
 }
 
 // threads: 128 or 256 per CTA (a compile-time constant of the kernel)
 template <class R, class S, int TX, int TY>
-cudaError_t launch_stage2d_t(const StageArgs &A, const CUtensorMap *map, cudaStream_t st, int threads = 256)
+cudaError_t launch_stage2d_t(const StageArgs &A, const CUtensorMap *const *maps, cudaStream_t st, int threads = 256)
 {
-    if (threads == 128) return launch_stage2d_n<R, S, TX, TY, 128>(A, map, st);
-    return launch_stage2d_n<R, S, TX, TY, 256>(A, map, st);
+    if (threads == 128) return launch_stage2d_n<R, S, TX, TY, 128>(A, maps, st);
+    return launch_stage2d_n<R, S, TX, TY, 256>(A, maps, st);
 }
 
 // Tile shapes: FP64 16x8 or 16x16 (the 32x8 FP64 tile exceeds shared memory);
 // FP32 16x8, 32x8, 16x16 or 32x16. threads: 256 or 128 per CTA (every phase
 // loops over its items); the 32x16 FP32 tile (185 KB, one CTA per SM) runs 512.
-cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map,
+cudaError_t launch_stage2d_fp64(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *const *maps,
                                 cudaStream_t st)
 {
     (void)tx;
-    if (ty == 16) return launch_stage2d_t<double, double, 16, 16>(A, map, st, threads > 0 ? threads : 256);
-    return launch_stage2d_t<double, double, 16, 8>(A, map, st, threads > 0 ? threads : 256);
+    if (ty == 16) return launch_stage2d_t<double, double, 16, 16>(A, maps, st, threads > 0 ? threads : 256);
+    return launch_stage2d_t<double, double, 16, 8>(A, maps, st, threads > 0 ? threads : 256);
 }
 
 cudaError_t launch_dt2d_fp64(const Layout &L, const double *buf, double gamma, double mu, double Pr, double cfl_c,
@@ -119,13 +119,13 @@ cudaError_t launch_validate2d_fp64(const Layout &L, const double *buf, double ga
 // ---------------------------------------------------------------------------
 namespace afns {
 
-cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *map,
+cudaError_t launch_stage2d_mixed(const StageArgs &A, int tx, int ty, int threads, const CUtensorMap *const *maps,
                                  cudaStream_t st)
 {
-    if (tx == 32 && ty == 16) return launch_stage2d_n<float, float, 32, 16, 512>(A, map, st);
-    if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, map, st, threads > 0 ? threads : 256);
-    if (ty == 16) return launch_stage2d_t<float, float, 16, 16>(A, map, st, threads > 0 ? threads : 256);
-    return launch_stage2d_t<float, float, 16, 8>(A, map, st, threads > 0 ? threads : 256);
+    if (tx == 32 && ty == 16) return launch_stage2d_n<float, float, 32, 16, 512>(A, maps, st);
+    if (tx == 32) return launch_stage2d_t<float, float, 32, 8>(A, maps, st, threads > 0 ? threads : 256);
+    if (ty == 16) return launch_stage2d_t<float, float, 16, 16>(A, maps, st, threads > 0 ? threads : 256);
+    return launch_stage2d_t<float, float, 16, 8>(A, maps, st, threads > 0 ? threads : 256);
 }
 
 cudaError_t launch_ghost2d_f32(const Layout &L, float *buf, cudaStream_t st) { return launch_ghost2d<float>(L, buf, st); }

@@ -489,18 +489,21 @@ __device__ __forceinline__ void tile_issue(const StageArgs &A, int bx, int by, R
 // when the tile's copies did not land in time (reported in Ctl.err): the CTA
 // stops. Several problems (the batched kernel): `ntmap` is the tensor map of the
 // next tile's problem (null: the same map), and with `multi` every tile loads
-// its problem's constants and starts its own restart flag.
+// its problem's constants and starts its own restart flag. `rmap0` / `rmap2`
+// are the row maps (box: the tile's cell rows) of u^n and of the auxiliary
+// state: the cell update's inputs from them are copied by TMA once the point
+// phase is done, so they land while the low-order and face phases run.
 template <class R, class S, int TX, int TY, int NTH>
 __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm, const void *tmap,
-                                           int it = 0, int nbx = -1, int nby = -1, const void *ntmap = nullptr,
-                                           bool multi = false)
+                                           int it, int nbx, int nby, const void *ntmap, bool multi,
+                                           const void *rmap0, const void *rmap2)
 {
     using T = Tile2<TX, TY>;
     using Q4 = V4<R>;
     constexpr int LX = T::LX, CX = T::CX, QX = T::QX;
     __shared__ int s_bad, s_stop;
     __shared__ TileConst<R> tc;
-    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(8) uint64_t s_bar, s_bar6;
     const Layout &L = A.L;
     const int i0 = bx * TX, j0 = by * TY;
     const int tid = threadIdx.x;
@@ -529,6 +532,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     if (it == 0) {
         if (tid == 0) {
             mbar_init(&s_bar, 1);
+            mbar_init(&s_bar6, 1);
             s_stop = 0;
             s_bad = 0;
         }
@@ -749,10 +753,27 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     // low-order cell records overwrite them, and the next tile's copies go to the
     // staging area (ordered after this tile's generic accesses to it)
     __syncthreads();
-    if (tid == 0 && nbx >= 0) {
+    // the cell update's inputs from u^n (stages 2-4) and from the auxiliary
+    // state (stages 4-5): the tile's cell rows of the cell-average planes (and,
+    // in FP32, of their compensation planes), by TMA into the dead lattice space
+    // past the low-order cell records
+    R *p6 = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oCQ + 4 * T::NCQ) + 127) & ~(uintptr_t)127);
+    constexpr int P6W = TX + 4, P6BOX = 4 * P6W * TY, P6N = sizeof(S) == 4 ? 2 : 1;   // planes per input: hi (+ lo)
+    static_assert((4 * T::NCQ + 8) * sizeof(Q4) + 2 * P6N * P6BOX * sizeof(R) <= 2 * (size_t)T::NL * sizeof(Q4),
+                  "cell-update inputs fit in the lattice space");
+    const bool in0 = tc.ua0, in2 = tc.ua2 || A.k.acc;
+    if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
-        tile_issue<R, TX, TY>(A, nbx, nby, stg, ntmap ? ntmap : tmap, &s_bar);
+        if (nbx >= 0) {
+            R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
+            tile_issue<R, TX, TY>(A, nbx, nby, stg, ntmap ? ntmap : tmap, &s_bar);
+        }
+        const int nin = (in0 ? 1 : 0) + (in2 ? 1 : 0);
+        mbar_expect_tx(&s_bar6, (unsigned)(nin * P6N * P6BOX * sizeof(R)));
+        for (int q = 0; q < P6N; ++q) {   // plane 16 + c holds the compensation word of component c
+            if (in0) tma_load_3d(p6 + q * P6BOX, rmap0, i0, j0 + 2, 16 * q, &s_bar6);
+            if (in2) tma_load_3d(p6 + (P6N + q) * P6BOX, rmap2, i0, j0 + 2, 16 * q, &s_bar6);
+        }
     }
 
     // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
@@ -908,6 +929,13 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     __syncthreads();
 
     // ---- P6: cell residual (flux differences, Eq. (23)), RK combination, store
+    // (its u^n and auxiliary inputs landed in p6: [input][plane][row][col], the
+    // columns from i0 - 2)
+    if (!mbar_wait(&s_bar6, (unsigned)(it & 1), 2000000000ull)) {
+        atomicOr(&A.ctl->err, 1);
+        return false;
+    }
+    const R *p6u0 = p6, *p6aux = p6 + P6N * P6BOX;
     S cfl1 = S(0), cfl2 = S(0);   // CFL maxima of the output cell averages (k.cfl_out)
     if constexpr (sizeof(S) == 8) {
         const double w = A.k.residual ? 1.0 : A.k.cl * dt;
@@ -918,11 +946,12 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             const Q4 fyt = sFY[(jl + 1) * TX + il], fyb = sFY[jl * TX + il];
             const Q4 ui = sA[(jl + 2) * CX + (il + 2)];
             const long long po0 = plane_of(L, 0, 0) + cell_off(L, i0 + il, j0 + jl);
-            double g0[4] = {0, 0, 0, 0}, g2[4] = {0, 0, 0, 0};   // global inputs first
+            const int q6 = jl * P6W + il + 2;
+            double g0[4] = {0, 0, 0, 0}, g2[4] = {0, 0, 0, 0};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                if (tc.ua0) g0[c] = ld<S>(A.u0, po0 + c * L.plane);
-                if (tc.ua2 || A.k.acc) g2[c] = ld<S>(A.aux, po0 + c * L.plane);
+                if (in0) g0[c] = p6u0[c * P6W * TY + q6];
+                if (in2) g2[c] = p6aux[c * P6W * TY + q6];
             }
             const double src = A.source ? tg_cell_source(A.mu, A.kappa, A.gamma, L.lo[0], L.lo[1], L.dx, L.dy,
                                                          i0 + il, j0 + jl, A.ctl->t + A.k.ct * dt)
@@ -955,22 +984,23 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         const ff a0 = tc.fa0, a1 = tc.fa1, a2 = tc.fa2, wx = tc.fwx, wy = tc.fwy;
         const ff b1 = tc.fb1, b2 = tc.fb2, bx = tc.fbx, by = tc.fby;
         float *out = (float *)A.out;
-        const float *u0 = (const float *)A.u0;
         float *aux = (float *)A.aux;
         for (int t = tid; t < ntx * nty; t += nth) {
             const int il = t % ntx, jl = t / ntx;
             const long long off = cell_off(L, i0 + il, j0 + jl);
             float o4[4] = {1.f, 0.f, 0.f, 1.f};
-            // every global input of the cell first (one latency for all of them)
+            // the compensation words of the input (global), u^n and the auxiliary
+            // state (landed in p6)
+            const int q6 = jl * P6W + il + 2;
             float ulo[4], g0h[4], g0l[4], g2h[4], g2l[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const long long po = plane_of(L, 0, c) + off, pl = comp_plane(L, c) + off;
+                const long long pl = comp_plane(L, c) + off;
                 ulo[c] = A.k.residual ? 0.f : ((const float *)A.uin)[pl];
-                g0h[c] = tc.ua0 ? u0[po] : 0.f;
-                g0l[c] = tc.ua0 ? u0[pl] : 0.f;
-                g2h[c] = (tc.ua2 || A.k.acc) ? aux[po] : 0.f;
-                g2l[c] = (tc.ua2 || A.k.acc) ? aux[pl] : 0.f;
+                g0h[c] = in0 ? p6u0[c * P6W * TY + q6] : 0.f;
+                g0l[c] = in0 ? p6u0[P6BOX + c * P6W * TY + q6] : 0.f;
+                g2h[c] = in2 ? p6aux[c * P6W * TY + q6] : 0.f;
+                g2l[c] = in2 ? p6aux[P6BOX + c * P6W * TY + q6] : 0.f;
             }
             const Q4 fxr = sFX[jl * (TX + 1) + il + 1], fxl = sFX[jl * (TX + 1) + il];
             const Q4 fyt = sFY[(jl + 1) * TX + il], fyb = sFY[jl * TX + il];
@@ -1055,7 +1085,8 @@ constexpr int stage_min_ctas()
 // tile's copies issued while the previous tile finishes.
 template <class R, class S, int TX, int TY, int NTH>
 __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
-    k_stage2d(StageArgs A, const __grid_constant__ CUtensorMap tmap)
+    k_stage2d(StageArgs A, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap rmap0,
+              const __grid_constant__ CUtensorMap rmap2)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tiles_x = (A.L.n1 + TX - 1) / TX, ntiles = tiles_x * ((A.L.n2 + TY - 1) / TY);
@@ -1064,7 +1095,8 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
         const int tn = t + gridDim.x;
         const bool more = tn < ntiles;
         if (!stage_tile<R, S, TX, TY, NTH>(A, t % tiles_x, t / tiles_x, reinterpret_cast<V4<R> *>(smem_raw),
-                                                 &tmap, it, more ? tn % tiles_x : -1, more ? tn / tiles_x : -1))
+                                           &tmap, it, more ? tn % tiles_x : -1, more ? tn / tiles_x : -1, nullptr,
+                                           false, &rmap0, &rmap2))
             break;
         // the next tile's records overwrite this tile's
         __syncthreads();
