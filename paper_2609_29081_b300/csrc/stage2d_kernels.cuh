@@ -777,11 +777,28 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     }
 
     // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
+    // FP64: the primitives (u, v, p, T) of every cell of the frame first, once
+    // each, past the cell-update inputs (each cell's quantities need those of its
+    // four neighbours, and a reciprocal costs many FP64 instructions; in FP32 it
+    // is one approximate instruction and recomputing is cheaper than the records)
+    Q4 *sW = reinterpret_cast<Q4 *>(p6 + 2 * P6N * P6BOX);
+    if constexpr (sizeof(R) == 8) {
+        static_assert((4 * T::NCQ + 8) * sizeof(Q4) + 2 * P6N * P6BOX * sizeof(R) + T::NCA * sizeof(Q4) <=
+                          2 * (size_t)T::NL * sizeof(Q4),
+                      "cell primitives fit in the lattice space");
+        for (int t = tid; t < T::NCA; t += nth) sW[t] = cell_prims(sA[t], gm1);
+        __syncthreads();
+    }
     for (int t = tid; t < T::NCQ; t += nth) {
         const int ca = (t / QX + 1) * CX + (t % QX + 1);
         const Q4 U = sA[ca];
-        const Q4 W = cell_prims(U, gm1), We = cell_prims(sA[ca + 1], gm1), Ww = cell_prims(sA[ca - 1], gm1);
-        const Q4 Wn = cell_prims(sA[ca + CX], gm1), Ws = cell_prims(sA[ca - CX], gm1);
+        Q4 W, We, Ww, Wn, Ws;
+        if constexpr (sizeof(R) == 8) {
+            W = sW[ca], We = sW[ca + 1], Ww = sW[ca - 1], Wn = sW[ca + CX], Ws = sW[ca - CX];
+        } else {
+            W = cell_prims(U, gm1), We = cell_prims(sA[ca + 1], gm1), Ww = cell_prims(sA[ca - 1], gm1);
+            Wn = cell_prims(sA[ca + CX], gm1), Ws = cell_prims(sA[ca - CX], gm1);
+        }
         const R i2x = tc.i2[0], i2y = tc.i2[1];
         const R Sxu = (We.x - Ww.x) * i2x, Sxv = (We.y - Ww.y) * i2x, SxT = (We.w - Ww.w) * i2x;
         const R Syu = (Wn.x - Ws.x) * i2y, Syv = (Wn.y - Ws.y) * i2y, SyT = (Wn.w - Ws.w) * i2y;
