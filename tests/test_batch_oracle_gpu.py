@@ -156,3 +156,22 @@ def test_batch_mixed_tracks_fp64_oracle(orc):
             assert err < 1e-4, (name, err, where)
         else:
             assert err < 2e-5 and l1 < 2e-6, (name, err, l1, where)
+
+
+def test_batch_largest_problem_one_step_matches_oracle(orc):
+    """The largest grid of the batched workload (sides up to 512), non-square, in
+    a batch with a small problem: one FP64 batch step equals one oracle step to
+    1e-12 (many full tiles in both directions and ragged work-list neighbours)."""
+    from paper_2609_29081_b300 import FP64
+    big = [w for w in W.batch_problems(nprob=40, seed=7, sizes=(384, 512), blast_frac=0.0) if w.n[0] != w.n[1]][0]
+    small = W.random_smooth_2d((20, 13), seed=33)
+    cases = [("big_%dx%d" % big.n, big), ("small_20x13", small)]
+    first, _, stats, _ = run_batch(cases, FP64, 1)
+    for k, (name, w) in enumerate(cases):
+        assert stats[k]["accepted"] == 1 and stats[k]["restarts"] == 0
+        P = oracle_problem(orc, w)
+        s = w.state.copy()
+        rc, taken, halv = orc.step(P, s, orc.dt_max(P, s))
+        assert rc == 0 and halv == 0
+        err, where = max_rel_err(first[k], s, 2, w.n)
+        assert err < TOL_STEP, (name, err, where)
