@@ -81,7 +81,8 @@ __device__ __forceinline__ R comp(const V4<R> &v, int c)
 
 // ---------------------------------------------------------------------------
 // Point-value residual of Eq. (12) at lattice node n of the shared tile.
-// sU: conservative, sQ: (u, v, T, c), sGX / sGY: D_c gradients of (u, v, T).
+// sU: conservative, sQ: (u, v, T, c), sGX / sGY: D_c gradients of (v, u, T)
+// (v first: the FP32 form below pairs them crosswise with (u, v)).
 // ---------------------------------------------------------------------------
 template <class R, int TX, int TY>
 __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, const TileConst<R> &tc, R res[4])
@@ -160,20 +161,139 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
             const R wc = (R)kDC[k];
             if (l == 0) {   // K_12 d_y Z at the x-neighbours (y gradients: rows from 2)
                 const V4<R> gy = sGY[xl[k] - 2 * LX];
-                g1 += wc * (-mu23 * gy.y);
-                g2 += wc * (mu * gy.x);
-                g3 += wc * (mu * q[k].y * gy.x - mu23 * q[k].x * gy.y);
+                const R gyu = gy.y, gyv = gy.x;
+                g1 += wc * (-mu23 * gyv);
+                g2 += wc * (mu * gyu);
+                g3 += wc * (mu * q[k].y * gyu - mu23 * q[k].x * gyv);
             } else {        // K_21 d_x Z at the y-neighbours
                 const V4<R> gx = sGX[T::gx(la, lb) + (k - 2) * T::GXW];
-                g1 += wc * (mu * gx.y);
-                g2 += wc * (-mu23 * gx.x);
-                g3 += wc * (-mu23 * q[k].y * gx.x + mu * q[k].x * gx.y);
+                const R gxu = gx.y, gxv = gx.x;
+                g1 += wc * (mu * gxv);
+                g2 += wc * (-mu23 * gxu);
+                g3 += wc * (-mu23 * q[k].y * gxu + mu * q[k].x * gxv);
             }
         }
         res[1] += g1 * inv6h;
         res[2] += g2 * inv6h;
         res[3] += g3 * inv6h;
     }
+}
+
+// Two-lane FP32 arithmetic (the packed FFMA2 / FADD2 / FMUL2 instructions of
+// sm_100 and later): one instruction for a pair of independent FP32 operations.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 xy2(const V4<float> &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 zw2(const V4<float> &v) { return make_float2(v.z, v.w); }
+
+// FP32 form of the point residual: the sums of the generic form above, carried
+// in the component pairs (rho, m_x), (m_y, E), (u, v) and the gradient pairs
+// (v, u) of the stored records, with the FVS flux sums regrouped as
+//   sum_k dc_k F_k = sum_k (dc_k u_l,k) U_k + (0, P e_x, P e_y, sum_k dc_k u_l,k p_k),
+//   P = sum_k dc_k p_k   (F_l = u_l U + p (0, e_x, e_y, u_l)),
+// the fourth-difference dissipation as alpha * sum_k d4_k U_k, the cross
+// viscous terms as sums of dc_k (d v, d u) and of dc_k (u d v, v d u) that the
+// K coefficients multiply once, and the energy term of D^2 as
+// c1 sum_m u_m (B u)_m + c2 sum_m v_m (B v)_m.
+template <int TX, int TY>
+__device__ __forceinline__ void point_residual_f32(const V4<float> *sm, int la, int lb, const TileConst<float> &tc,
+                                                   float res[4])
+{
+    using T = Tile2<TX, TY>;
+    constexpr int LX = T::LX;
+    const int n = T::node(la, lb);
+    const int row = lb * LX;
+    const int xl[5] = {n - 1, row + T::col(la - 1), n, row + T::col(la + 1), n + 1};
+    const V4<float> *sU = sm + T::oU, *sQ = sm + T::oQ, *sGX = sm + T::oGX, *sGY = sm + T::oGY;
+    const float mu = tc.mu, ka = tc.ka;
+    const float mu43 = 4.0f / 3.0f * mu, mu23 = 2.0f / 3.0f * mu;
+    float2 r01 = bc2(0.0f), r23 = bc2(0.0f);   // inviscid part of (res0, res1), (res2, res3)
+    float2 v12 = bc2(0.0f);                     // viscous part of (res1, res2)
+    float v3 = 0.0f;                            // viscous part of res3
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        V4<float> q[5], u[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int m = l == 0 ? xl[k] : n + (k - 2) * LX;
+            q[k] = sQ[m];
+            u[k] = sU[m];
+        }
+        // --- inviscid
+        float al = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) al = fmaxf(al, fabsf(l == 0 ? q[k].x : q[k].y) + q[k].w);
+        float2 a01 = bc2(0.0f), a23 = bc2(0.0f), d01 = bc2(0.0f), d23 = bc2(0.0f);
+        float sp = 0.0f, spu = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (kDC[k] != 0.0) {
+                const float wc = (float)kDC[k];
+                const float ul = l == 0 ? q[k].x : q[k].y;
+                const float p = u[k].x * q[k].z;   // rho T
+                const float a = wc * ul;
+                a01 = fma2(bc2(a), xy2(u[k]), a01);
+                a23 = fma2(bc2(a), zw2(u[k]), a23);
+                sp = fmaf(wc, p, sp);
+                spu = fmaf(a, p, spu);
+            }
+            const float2 w4 = bc2((float)kD4[k]);
+            d01 = fma2(w4, xy2(u[k]), d01);
+            d23 = fma2(w4, zw2(u[k]), d23);
+        }
+        float2 f01 = fma2(bc2(al), d01, a01), f23 = fma2(bc2(al), d23, a23);
+        if (l == 0)
+            f01.y += sp;
+        else
+            f23.x += sp;
+        f23.y += spu;
+        const float2 mi6 = bc2(-tc.i6[l]);
+        r01 = fma2(f01, mi6, r01);
+        r23 = fma2(f23, mi6, r23);
+        // --- viscous, same direction: D^{(l),2}(K_ll, Z) of Eq. (9)
+        const float c1 = l == 0 ? mu43 : mu, c2 = l == 0 ? mu : mu43;
+        float2 d2 = bc2(0.0f), e = bc2(0.0f);
+        float d2T = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const float2 qm = xy2(q[m]);
+            d2 = fma2(bc2((float)kD2[m]), qm, d2);
+            d2T = fmaf((float)kD2[m], q[m].z, d2T);
+            float2 b = bc2(0.0f);
+#pragma unroll
+            for (int nn = 0; nn < 5; ++nn)
+                if (kB[m][nn] != 0.0) b = fma2(bc2((float)kB[m][nn]), xy2(q[nn]), b);
+            e = fma2(qm, b, e);
+        }
+        const float i3h2 = tc.i3h2[l];
+        v12 = fma2(make_float2(c1 * i3h2, c2 * i3h2), d2, v12);
+        v3 = fmaf(ka * i3h2, d2T, v3);
+        v3 = fmaf(tc.f4h2[l], fmaf(c1, e.x, c2 * e.y), v3);
+        // --- viscous, mixed: D_c^{(l)}(K_lm D_c^{(m)} Z), m != l
+        float2 sg = bc2(0.0f), cg = bc2(0.0f);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (k == 2) continue;
+            const float2 wc = bc2((float)kDC[k]);
+            // (d v, d u): y gradients at the x-neighbours, x gradients at the y-neighbours
+            const float2 gp = xy2(l == 0 ? sGY[xl[k] - 2 * LX] : sGX[T::gx(la, lb) + (k - 2) * T::GXW]);
+            sg = fma2(wc, gp, sg);
+            cg = fma2(wc, mul2(xy2(q[k]), gp), cg);   // (u d v, v d u)
+        }
+        const float i6 = tc.i6[l];
+        if (l == 0) {   // K_12 d_y Z: (g1, g2) = (-mu23 S_v, mu S_u), g3 = mu (v d u) - mu23 (u d v)
+            v12 = fma2(make_float2(-mu23 * i6, mu * i6), sg, v12);
+            v3 = fmaf(i6, fmaf(mu, cg.y, -mu23 * cg.x), v3);
+        } else {        // K_21 d_x Z: (g1, g2) = (mu S_v, -mu23 S_u), g3 = mu (u d v) - mu23 (v d u)
+            v12 = fma2(make_float2(mu * i6, -mu23 * i6), sg, v12);
+            v3 = fmaf(i6, fmaf(mu, cg.x, -mu23 * cg.y), v3);
+        }
+    }
+    res[0] = r01.x;
+    res[1] = r01.y + v12.x;
+    res[2] = r23.x + v12.y;
+    res[3] = r23.y + v3;
 }
 
 // Total flux F^c_l - F^v_l at a node with node gradients (gx, gy) of (u, v, T).
@@ -340,7 +460,7 @@ __device__ __forceinline__ void face_high_order(V4<R> *sm, int f, int ntx, int n
         const int n = T::node(la, lb);
         const V4<R> U = sU[n], Qn = sQ[n], gx = sGX[T::gx(la, lb)], gy = sGY[T::gy(la, lb)];
         R Fn[4];
-        node_flux<R>(l, U.x, U.y, U.z, U.w, Qn.x, Qn.y, Qn.z, gx.x, gx.y, gx.z, gy.x, gy.y, gy.z, mu, ka, Fn);
+        node_flux<R>(l, U.x, U.y, U.z, U.w, Qn.x, Qn.y, Qn.z, gx.y, gx.x, gx.z, gy.y, gy.x, gy.z, mu, ka, Fn);
         const R ws = s == 1 ? R(4) / R(6) : R(1) / R(6);
 #pragma unroll
         for (int c = 0; c < 4; ++c) FH[c] += ws * Fn[c];
@@ -611,20 +731,20 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     __syncthreads();
 
     // ---- P3: D_c gradients (Eq. (8)) of Z = (u, v, T) along x (lattice columns
-    // [2, LX-3]) and along y (rows [2, LY-3]), stored compactly
+    // [2, LX-3]) and along y (rows [2, LY-3]), stored compactly as (v, u, T, 0)
     {
         const R i6x = tc.i6[0], i6y = tc.i6[1];
         for (int t = tid; t < T::NGX; t += nth) {
             const int lb = t / T::GXW, la = T::gxcol_inv(t - lb * T::GXW), row = lb * LX;
             const int n = T::node(la, lb);
             const Q4 a = sQ[n - 1], b = sQ[row + T::col(la - 1)], c = sQ[row + T::col(la + 1)], d = sQ[n + 1];
-            sGX[t] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6x, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6x,
+            sGX[t] = Q4{(a.y - R(8) * b.y + R(8) * c.y - d.y) * i6x, (a.x - R(8) * b.x + R(8) * c.x - d.x) * i6x,
                         (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6x, R(0)};
         }
         for (int t = tid; t < T::NGY; t += nth) {
             const int n = 2 * LX + t;
             const Q4 a = sQ[n - 2 * LX], b = sQ[n - LX], c = sQ[n + LX], d = sQ[n + 2 * LX];
-            sGY[t] = Q4{(a.x - R(8) * b.x + R(8) * c.x - d.x) * i6y, (a.y - R(8) * b.y + R(8) * c.y - d.y) * i6y,
+            sGY[t] = Q4{(a.y - R(8) * b.y + R(8) * c.y - d.y) * i6y, (a.x - R(8) * b.x + R(8) * c.x - d.x) * i6y,
                         (a.z - R(8) * b.z + R(8) * c.z - d.z) * i6y, R(0)};
         }
     }
@@ -689,7 +809,10 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                 for (int c = 0; c < 4; ++c) g2[c] = ((const S *)A.aux)[po0 + c * L.plane];
             }
             R r[4];
-            point_residual<R, TX, TY>(sm, la, lb, tc, r);
+            if constexpr (sizeof(R) == 4)
+                point_residual_f32<TX, TY>(sm, la, lb, tc, r);
+            else
+                point_residual<R, TX, TY>(sm, la, lb, tc, r);
             if (A.source)
                 r[3] += (R)tg_point_source(A.mu, A.kappa, A.gamma, L.lo[0], L.lo[1], L.dx, L.dy, a, b,
                                            A.ctl->t + A.k.ct * dt);
