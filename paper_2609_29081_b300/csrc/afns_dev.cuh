@@ -257,6 +257,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
 #endif
 }
 
+// Bring one box of a 3D tensor map into L2 without a shared-memory destination
+// (no barrier; the data is then read by ordinary loads at L2 latency).
+__device__ __forceinline__ void tma_prefetch_l2_3d(const void *tmap, int x, int y, int z)
+{
+#ifdef __CUDA_ARCH__
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(tmap), "r"(x), "r"(y),
+                 "r"(z)
+                 : "memory");
+#endif
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst_shared, const void *tmap, int x, int y, int z, uint64_t *bar)
 {
 #ifdef __CUDA_ARCH__

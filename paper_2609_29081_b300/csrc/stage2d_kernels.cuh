@@ -659,6 +659,15 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         __syncthreads();
         if (tid == 0) tile_issue<R, TX, TY>(A, bx, by, stg, tmap, &s_bar);
     }
+    // the point combination's inputs of this tile (the point sites of u^n and
+    // of the auxiliary state, the tile's rows) are fetched into L2 now, so that
+    // the point phase reads them at L2 latency
+    if (tid == 0 && rmap0) {
+        for (int site = 1; site < 4; ++site) {
+            if (A.k.a0 != 0.0) tma_prefetch_l2_3d(rmap0, i0, j0 + 2, 4 * site);
+            if (A.k.a2 != 0.0 || A.k.acc) tma_prefetch_l2_3d(rmap2, i0, j0 + 2, 4 * site);
+        }
+    }
     // while the copies are in flight: the constants (published by the
     // cp.async wait and the barrier after the transposition)
     if (fresh) load_tile_consts<R>(tc, A, tid);
