@@ -521,8 +521,9 @@ static cudaError_t do_stage(afns_ctx *c, const StageArgs &A)
     const int k = slot(A.uin), k0 = slot(A.u0), k2 = slot(A.aux);
     if (k == 5 || k0 == 5 || k2 == 5) return cudaErrorInvalidValue;
     const int w = c->tile_x == 32 ? (c->tile_y == 16 ? 3 : 1) : (c->tile_y == 16 ? 2 : 0);
-    // the tile map of the stage input, the row maps of u^n and of the auxiliary state
-    const CUtensorMap *maps[3] = {&c->maps[w][k], &c->rmaps[w][k0], &c->rmaps[w][k2]};
+    // the tile map of the stage input, the row maps of u^n, of the auxiliary
+    // state and of the stage input
+    const CUtensorMap *maps[4] = {&c->maps[w][k], &c->rmaps[w][k0], &c->rmaps[w][k2], &c->rmaps[w][k]};
     if (c->mixed) return launch_stage2d_mixed(A, c->tile_x, c->tile_y, c->threads, maps, c->st);
     return launch_stage2d_fp64(A, c->tile_x, c->tile_y, c->threads, maps, c->st);
 }

@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>()) k_batch
             nmap = B.maps + ((size_t)np * kShapes + shape) * 4 + Q.buf_of[B.in_idx];
         }
         if (!stage_tile<R, S, TX, TY, NTH>(A, tile % P.tiles_x, tile / P.tiles_x, sm, map, it, nbx, nby, nmap, true,
-                                           B.rmaps + mb + P.buf_of[0], B.rmaps + mb + P.buf_of[2]))
+                                           B.rmaps + mb + P.buf_of[0], B.rmaps + mb + P.buf_of[2],
+                                           B.rmaps + mb + P.buf_of[B.in_idx]))
             break;
         // the next item's records overwrite this item's
         __syncthreads();

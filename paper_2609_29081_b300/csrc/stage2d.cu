@@ -40,7 +40,7 @@ cudaError_t launch_stage2d_n(const StageArgs &A, const CUtensorMap *const *maps,
     }
     const long long ntiles = (long long)((A.L.n1 + TX - 1) / TX) * ((A.L.n2 + TY - 1) / TY);
     const int grid = (int)std::min<long long>(ntiles, resident);
-    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A, *maps[0], *maps[1], *maps[2]);
+    k_stage2d<R, S, TX, TY, NTH><<<grid, NTH, smem, st>>>(A, *maps[0], *maps[1], *maps[2], *maps[3]);
     return cudaGetLastError();
 }
 

@@ -610,13 +610,15 @@ __device__ __forceinline__ void tile_issue(const StageArgs &A, int bx, int by, R
 // stops. Several problems (the batched kernel): `ntmap` is the tensor map of the
 // next tile's problem (null: the same map), and with `multi` every tile loads
 // its problem's constants and starts its own restart flag. `rmap0` / `rmap2`
-// are the row maps (box: the tile's cell rows) of u^n and of the auxiliary
-// state: the cell update's inputs from them are copied by TMA once the point
-// phase is done, so they land while the low-order and face phases run.
+// / `rmapin` are the row maps (box: the tile's cell rows) of u^n, of the
+// auxiliary state and of the stage input: the cell update's inputs from them
+// (in FP32 also the compensation words of the input's cell averages) are
+// copied by TMA once the point phase is done, so they land while the low-order
+// and face phases run.
 template <class R, class S, int TX, int TY, int NTH>
 __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V4<R> *sm, const void *tmap,
                                            int it, int nbx, int nby, const void *ntmap, bool multi,
-                                           const void *rmap0, const void *rmap2)
+                                           const void *rmap0, const void *rmap2, const void *rmapin)
 {
     using T = Tile2<TX, TY>;
     using Q4 = V4<R>;
@@ -780,12 +782,13 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
             int la, lb;
             if (t < nreg) {
                 if (t < 2 * ncell) {
-                    // an even row: its ntx vertices, then its ntx y-edges
-                    const int rw = t / (2 * ntx), k = t - rw * (2 * ntx);
+                    // an even row: its ntx vertices, then its ntx y-edges (a
+                    // full-width tile divides by the constant TX)
+                    const int rw = ntx == TX ? t / (2 * TX) : t / (2 * ntx), k = t - rw * (2 * ntx);
                     la = k < ntx ? 2 + 2 * k : 3 + 2 * (k - ntx);
                     lb = 2 + 2 * rw;
                 } else {
-                    const int cc = t - 2 * ncell, jl = cc / ntx;
+                    const int cc = t - 2 * ncell, jl = ntx == TX ? cc / TX : cc / ntx;
                     la = 2 + 2 * (cc - jl * ntx);
                     lb = 3 + 2 * jl;
                 }
@@ -894,18 +897,23 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
     static_assert((4 * T::NCQ + 8) * sizeof(Q4) + 2 * P6N * P6BOX * sizeof(R) <= 2 * (size_t)T::NL * sizeof(Q4),
                   "cell-update inputs fit in the lattice space");
     const bool in0 = tc.ua0, in2 = tc.ua2 || A.k.acc;
+    // FP32: the compensation words of the input's cell averages, in the gradient
+    // space past the staging area of the next tile's copies
+    constexpr bool kLo = sizeof(S) == 4;
+    const bool inlo = kLo && !A.k.residual;
+    R *const plo = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(stg + 4 * BOX) + 127) & ~(uintptr_t)127);
+    static_assert(!kLo || 256 + (4 * BOX + P6BOX) * sizeof(R) <= (size_t)(T::NGX + T::NGY) * sizeof(Q4),
+                  "the input's compensation rows fit past the staging area");
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        if (nbx >= 0) {
-            R *stg = reinterpret_cast<R *>((reinterpret_cast<uintptr_t>(sm + T::oGX) + 127) & ~(uintptr_t)127);
-            tile_issue<R, TX, TY>(A, nbx, nby, stg, ntmap ? ntmap : tmap, &s_bar);
-        }
+        if (nbx >= 0) tile_issue<R, TX, TY>(A, nbx, nby, stg, ntmap ? ntmap : tmap, &s_bar);
         const int nin = (in0 ? 1 : 0) + (in2 ? 1 : 0);
-        mbar_expect_tx(&s_bar6, (unsigned)(nin * P6N * P6BOX * sizeof(R)));
+        mbar_expect_tx(&s_bar6, (unsigned)((nin * P6N + (inlo ? 1 : 0)) * P6BOX * sizeof(R)));
         for (int q = 0; q < P6N; ++q) {   // plane 16 + c holds the compensation word of component c
             if (in0) tma_load_3d(p6 + q * P6BOX, rmap0, i0, j0 + 2, 16 * q, &s_bar6);
             if (in2) tma_load_3d(p6 + (P6N + q) * P6BOX, rmap2, i0, j0 + 2, 16 * q, &s_bar6);
         }
+        if (inlo) tma_load_3d(plo, rmapin, i0, j0 + 2, 16, &s_bar6);
     }
 
     // ---- P5a: low-order cell quantities (Sec. 3.1, 3.2) on cells [i0-1, i0+TX] x [j0-1, j0+TY]
@@ -1090,7 +1098,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         const double w = A.k.residual ? 1.0 : A.k.cl * dt;
         const double idx = L.idx[0], idy = L.idx[1];
         for (int t = tid; t < ntx * nty; t += nth) {
-            const int il = t % ntx, jl = t / ntx;
+            const int jl = ntx == TX ? t / TX : t / ntx, il = t - jl * ntx;
             const Q4 fxr = sFX[jl * (TX + 1) + il + 1], fxl = sFX[jl * (TX + 1) + il];
             const Q4 fyt = sFY[(jl + 1) * TX + il], fyb = sFY[jl * TX + il];
             const Q4 ui = sA[(jl + 2) * CX + (il + 2)];
@@ -1135,17 +1143,16 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         float *out = (float *)A.out;
         float *aux = (float *)A.aux;
         for (int t = tid; t < ntx * nty; t += nth) {
-            const int il = t % ntx, jl = t / ntx;
+            const int jl = ntx == TX ? t / TX : t / ntx, il = t - jl * ntx;
             const long long off = cell_off(L, i0 + il, j0 + jl);
             float o4[4] = {1.f, 0.f, 0.f, 1.f};
-            // the compensation words of the input (global), u^n and the auxiliary
-            // state (landed in p6)
+            // the compensation words of the input (landed in plo), u^n and the
+            // auxiliary state (landed in p6)
             const int q6 = jl * P6W + il + 2;
             float ulo[4], g0h[4], g0l[4], g2h[4], g2l[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const long long pl = comp_plane(L, c) + off;
-                ulo[c] = A.k.residual ? 0.f : ((const float *)A.uin)[pl];
+                ulo[c] = inlo ? plo[c * P6W * TY + q6] : 0.f;
                 g0h[c] = in0 ? p6u0[c * P6W * TY + q6] : 0.f;
                 g0l[c] = in0 ? p6u0[P6BOX + c * P6W * TY + q6] : 0.f;
                 g2h[c] = in2 ? p6aux[c * P6W * TY + q6] : 0.f;
@@ -1235,7 +1242,7 @@ constexpr int stage_min_ctas()
 template <class R, class S, int TX, int TY, int NTH>
 __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
     k_stage2d(StageArgs A, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap rmap0,
-              const __grid_constant__ CUtensorMap rmap2)
+              const __grid_constant__ CUtensorMap rmap2, const __grid_constant__ CUtensorMap rmapin)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tiles_x = (A.L.n1 + TX - 1) / TX, ntiles = tiles_x * ((A.L.n2 + TY - 1) / TY);
@@ -1245,7 +1252,7 @@ __global__ void __launch_bounds__(NTH, stage_min_ctas<R, TX, TY, NTH>())
         const bool more = tn < ntiles;
         if (!stage_tile<R, S, TX, TY, NTH>(A, t % tiles_x, t / tiles_x, reinterpret_cast<V4<R> *>(smem_raw),
                                            &tmap, it, more ? tn % tiles_x : -1, more ? tn / tiles_x : -1, nullptr,
-                                           false, &rmap0, &rmap2))
+                                           false, &rmap0, &rmap2, &rmapin))
             break;
         // the next tile's records overwrite this tile's
         __syncthreads();
