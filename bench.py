@@ -39,13 +39,13 @@ N_CELLS = 1024
 FP64_DERIVED_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 # 148 SMs x 128 FP32 lanes x 2 flops x 2.032 GHz
 FP32_DERIVED_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# DRAM bytes (read + write) per stage launch from ncu, with the digest of the
-# kernel sources they were taken on; reported only while the sources match.
+# DRAM bytes (read + write) per stage launch from ncu (one launch of a step of
+# the benchmark flow at 1024x1024), keyed by the digest of the kernel sources and
+# the launch configuration they were taken on; reported only while both match.
 MEASURED_TRAFFIC = {
-    # ncu capture of one mixed stage launch of a timed step, 32x8 tiles, 256 threads
-    "mixed:527a89c4c305a931": 131.36e6,
-    # ncu capture of one FP64 stage launch of a timed step, 16x8 tiles, 128 threads
-    "fp64:527a89c4c305a931": 229.32e6,
+    "mixed:e9476c8fd32ffe6d:32x8x256": 87.653e6 + 42.739e6,
+    "mixed:e9476c8fd32ffe6d:16x8x128": 88.060e6 + 43.867e6,
+    "fp64:e9476c8fd32ffe6d:16x8x128": 137.821e6 + 92.136e6,
 }
 
 
@@ -71,7 +71,7 @@ def measure_alu_peaks():
     return out
 
 
-def stage_roofline(precision, cells, stage_ms, peaks, alu_pk):
+def stage_roofline(precision, cells, stage_ms, peaks, alu_pk, tuned=None):
     """Roofline of the stage kernel: the slower of the algorithmic HBM bytes at
     the measured copy bandwidth and the algorithmic flops at the measured FMA
     rate (FP64 path: FP64 flops; mixed path: FP32 flops, 256 B per cell-stage)."""
@@ -89,9 +89,10 @@ def stage_roofline(precision, cells, stage_ms, peaks, alu_pk):
     t_hbm = bpc * cells / (hbm * 1e9)
     t_alu = FLOPS_PER_CELL_STAGE * cells / (alu * 1e12)
     dig = kernel_digest(precision)
-    traffic = MEASURED_TRAFFIC.get(dig)
+    cfg = "%dx%dx%d" % (tuned["tile_x"], tuned["tile_y"], tuned["threads"]) if tuned else ""
+    traffic = MEASURED_TRAFFIC.get(dig + ":" + cfg)
     kern = "k_stage2d<double>" if precision == "fp64" else "k_stage2d<float>"
-    common = {"traffic": traffic, "kernel": kern, "kernel_digest": dig,
+    common = {"traffic": traffic, "kernel": kern, "kernel_digest": dig, "launch_config": cfg,
               "hbm_frac": t_hbm / sec, "alu_frac": t_alu / sec,
               "alu_peak_tflops": alu, "alu_peak_source": alu_src,
               "alu_peak_derived_tflops": derived, "hbm_peak_gbs": hbm}
@@ -624,7 +625,7 @@ def main():
                        "l2": "working set larger than L2: a stage reads 1-3 state buffers of %.0f MB and writes 1-2"
                              % (w.cells * (20 * 4 if args.precision == "mixed" else 16 * 8) / 1e6),
                        "restarts": r["restarts"], "tuned": r["tuned"], "warmup_steps_run": r["warm_done"]},
-            "roofline": stage_roofline(args.precision, cells, r["stage_ms"], peaks, alu_pk),
+            "roofline": stage_roofline(args.precision, cells, r["stage_ms"], peaks, alu_pk, r["tuned"]),
             "clocks": r["clocks"],
             "e2e": {"value": r["e2e_pipe"]["value"], "unit": UNIT, "h2d_bytes_per_step": r["state_bytes"],
                     "d2h_bytes_per_step": r["state_bytes"], "ms_per_step": r["e2e_pipe"]["ms_per_step"],
@@ -643,7 +644,7 @@ def main():
         c = cmp_run
         line[other] = {"value": c["value"], "unit": UNIT, "ms_per_step": c["ms"] / args.steps,
                        "stage_ms": c["stage_ms"], "tuned": c["tuned"], "restarts": c["restarts"],
-                       "roofline": stage_roofline(other, cells, c["stage_ms"], peaks, alu_pk)}
+                       "roofline": stage_roofline(other, cells, c["stage_ms"], peaks, alu_pk, c["tuned"])}
     if args.ladder:
         acc = accuracy_ladder(args.n, ACCURACY_STEPS)
         key = str(args.n)
