@@ -306,8 +306,8 @@ __global__ void k_batch_validate(const S *buf, Layout L, double gamma, int *flag
         while (r >= per_site[site]) r -= per_site[site++];
         int w = (site == 1 || site == 3) ? n1 + 1 : n1;
         long long off = cell_off(L, (int)(r % w), (int)(r / w));
-        double U[4];
-        for (int c = 0; c < 4; ++c) U[c] = (double)buf[plane_of(L, site, c) + off];
+        S U[4];
+        for (int c = 0; c < 4; ++c) U[c] = buf[plane_of(L, site, c) + off];
         if (!admissible_input2(U)) atomicOr(flag, 1);
     }
 }

@@ -177,11 +177,11 @@ __global__ void k_unpack_site(Layout L, const T *src, T *buf, int site, int w, i
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < wh; e += gridDim.x * blockDim.x) {
         const int j = e / w, i = e - j * w;
         const long long off = L.dim == 2 ? cell_off(L, i, j) : 2 + i;
-        double U[4];
+        T U[4] = {T(0), T(0), T(0), T(0)};
         for (int c = 0; c < nc; ++c) {
             const T v = src[(long long)c * wh + e];
             buf[plane_of(L, site, c) + off] = v;
-            U[c] = (double)v;
+            U[c] = v;
         }
         if (L.dim != 2 || !flag) continue;
         if (!admissible_input2(U)) atomicOr(flag, 1);

@@ -364,6 +364,21 @@ __device__ __forceinline__ bool admissible_input2(const double *U)
     return fin && U[0] > 0.0 && 2.0 * U[0] * U[3] > U[1] * U[1] + U[2] * U[2];
 }
 
+// The same check for FP32 values: decided in FP32 when 2 rho E and |m|^2 differ by
+// more than 1e-5 relatively (their FP32 roundings are below 2e-7 relatively, so
+// the order is certain), in FP64 otherwise and near the ends of the FP32 range.
+__device__ __forceinline__ bool admissible_input2(const float *v)
+{
+    if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]) && v[0] > 0.f)) return false;
+    const float a = 2.f * v[0] * v[3], b = fmaf(v[1], v[1], v[2] * v[2]);
+    if (a > 1e-30f && a < 1e30f && b < 1e30f) {
+        if (a > b * 1.00001f) return true;
+        if (a < b * 0.99999f) return false;
+    }
+    const double U[4] = {v[0], v[1], v[2], v[3]};
+    return admissible_input2(U);
+}
+
 // Finite, rho >= eps and p >= eps (eps > 0), decided without a division.
 __device__ __forceinline__ bool above_eps2(const double *U, double gm1, double eps)
 {

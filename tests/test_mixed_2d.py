@@ -176,3 +176,27 @@ def test_f32_upload_checks_values():
         S.set_state_f32(bad)
     S.set_state_f32(w.state.astype(np.float32))
     assert np.array_equal(S.get_state_f32(), w.state.astype(np.float32))
+
+
+def test_f32_upload_check_is_exact_at_zero_pressure():
+    """The FP32 upload check decides p > 0 exactly, also where 2 rho E and |m|^2
+    agree to FP32 rounding (its FP32 screen leaves those to FP64): E = 1/2 + 2^-24
+    with rho = m_x = 1 has p > 0 and is accepted; E = 1/2 (p = 0) and
+    E = 1/2 - 2^-25 (p < 0) are refused, for a cell average and for a vertex."""
+    from paper_2609_29081_b300 import MIXED, AfnsError, Solver
+    w = W.random_smooth_2d((33, 17), seed=6)
+    S = Solver.from_workload(w, precision=MIXED)
+    n1, n2 = w.n
+    vert = 4 * n1 * n2 + 4 * (n1 + 1) * n2 + 4 * n1 * (n2 + 1)
+    for base, stride in ((0, n1 * n2), (vert, (n1 + 1) * (n2 + 1))):
+        k = base + 2 * (n1 + (1 if base else 0)) + 3      # (i, j) = (3, 2)
+        for E, ok in ((0.5 + 2.0 ** -24, True), (0.5, False), (0.5 - 2.0 ** -25, False)):
+            s = w.state.astype(np.float32)
+            s[k], s[k + stride], s[k + 2 * stride], s[k + 3 * stride] = 1.0, 1.0, 0.0, E
+            assert float(np.float32(E)) == E
+            if ok:
+                S.set_state_f32(s)
+                assert np.array_equal(S.get_state_f32(), s)
+            else:
+                with pytest.raises(AfnsError):
+                    S.set_state_f32(s)
