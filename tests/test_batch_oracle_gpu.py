@@ -1,10 +1,10 @@
 """GPU parity of the batched persistent path (afb_*) against the CPU oracle
 directly, through the C-ABI.
 
-The batched kernel is separate code from the single-problem kernel (element
-copies instead of TMA tile loads, per-problem descriptors and tile constants, a
-device-side commit / halving kernel), so it is held to the oracle itself, not
-only to the single path: FP64 after one batch step to 1e-12 and after several
+The batched kernel is separate code around the single-problem tile function
+(a work list over problems, per-problem tensor maps, descriptors and tile
+constants, a device-side commit / halving kernel), so it is held to the oracle
+itself, not only to the single path: FP64 after one batch step to 1e-12 and after several
 to 1e-10 of each component's scale, with each problem's accepted steps and
 restarts (Remark 3.2) equal to the oracle's; the mixed form against the FP64
 oracle at the single-path mixed bounds. The batch holds problems of the
