@@ -424,46 +424,62 @@ def tube_arm(args, dist, rank, ws):
 
 
 def ladder_arm(args, rank):
-    """Grid-refinement ladder of the smooth periodic flow (256^2 .. 2048^2 by
-    default) to --t-end (default 0.05): relative L1 distance of the cell averages
-    of N cells from the 2N solution restricted by 2x2 averaging, and the observed
-    orders, for the FP64 and the mixed path (limiter s+pp)."""
+    """Grid-refinement ladder of the smooth periodic flow, 256^2 .. 2048^2, to
+    --t-end (default: the time 200 FP64 CFL steps reach on 1024^2, the benchmark's
+    run length), with the limiter s+pp and without limiter: relative L1 distance
+    of the cell averages of N cells from the 2N solution restricted by 2x2
+    averaging and the observed orders, for the FP64 and the mixed path, and the
+    mixed path's distance from FP64 on every grid."""
     import torch
     from paper_2609_29081_b300 import Solver, build, workloads as W
     from paper_2609_29081_b300._native import FP64, MIXED
     build.build()
-    t_end = args.t_end if args.t_end > 0 else 0.05
+    if args.t_end > 0:
+        t_end = args.t_end
+    else:
+        w = W.smooth_2d(1024)
+        S = Solver.from_workload(w, precision=FP64)
+        S.set_state(w.state)
+        for _ in range(ACCURACY_STEPS):
+            S.step(0.0)
+        S.get_state()
+        t_end = S.t
+        S.close()
     ns = [256, 512, 1024, 2048]
-    out = {}
-    for name, prec in (("mixed", MIXED), ("fp64", FP64)):
-        sol, secs = {}, {}
-        for n in ns:
-            w = W.smooth_2d(n)
-            S = Solver.from_workload(w, precision=prec)
-            S.set_state(w.state)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            steps, _ = S.advance(t_end)
-            torch.cuda.synchronize()
-            secs[n] = (time.perf_counter() - t0, steps)
-            sol[n] = W.split_sites(S.get_state(), 2, n, n)[0]
-            S.close()
-        err = []
-        for n in ns[:-1]:
-            f = sol[2 * n]
-            r = 0.25 * (f[:, 0::2, 0::2] + f[:, 1::2, 0::2] + f[:, 0::2, 1::2] + f[:, 1::2, 1::2])
-            err.append(float(np.abs(sol[n] - r).sum() / np.abs(r).sum()))
-        out[name] = {"n": ns[:-1], "l1": err,
-                     "orders": [float(np.log2(err[k] / err[k + 1])) for k in range(len(err) - 1)],
-                     "seconds_steps": {str(n): secs[n] for n in ns}}
-        if name == "mixed":
-            mixed_sol = sol
-        else:
-            out["mixed_vs_fp64_l1"] = {str(n): float(np.abs(mixed_sol[n] - sol[n]).sum() / np.abs(sol[n]).sum())
-                                       for n in ns}
+    out = {"t_end": t_end}
+    for lim_name, lim in (("s+pp", 2), ("none", 0)):
+        res = {}
+        for name, prec in (("mixed", MIXED), ("fp64", FP64)):
+            sol, secs = {}, {}
+            for n in ns:
+                w = W.smooth_2d(n)
+                S = Solver.from_workload(w, precision=prec, limiter=lim)
+                S.set_state(w.state)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                steps, _ = S.advance(t_end)
+                torch.cuda.synchronize()
+                secs[n] = (time.perf_counter() - t0, steps)
+                sol[n] = W.split_sites(S.get_state(), 2, n, n)[0]
+                S.close()
+                torch.cuda.empty_cache()
+            err = []
+            for n in ns[:-1]:
+                f = sol[2 * n]
+                r = 0.25 * (f[:, 0::2, 0::2] + f[:, 1::2, 0::2] + f[:, 0::2, 1::2] + f[:, 1::2, 1::2])
+                err.append(float(np.abs(sol[n] - r).sum() / np.abs(r).sum()))
+            res[name] = {"n": ns[:-1], "l1": err,
+                         "orders": [float(np.log2(err[k] / err[k + 1])) for k in range(len(err) - 1)],
+                         "seconds_steps": {str(n): secs[n] for n in ns}}
+            if name == "mixed":
+                mixed_sol = sol
+            else:
+                res["mixed_vs_fp64_l1"] = {str(n): float(np.abs(mixed_sol[n] - sol[n]).sum() / np.abs(sol[n]).sum())
+                                           for n in ns}
+        out[lim_name] = res
     if rank == 0:
-        print(json.dumps({"workload": "2D smooth periodic NS refinement ladder, t_end=%g, limiter s+pp" % t_end,
-                          "ladder": out}), flush=True)
+        print(json.dumps({"workload": "2D smooth periodic NS refinement ladder, t_end=%g, limiter s+pp and none"
+                                      % t_end, "ladder": out}), flush=True)
 
 
 def batch_measure(args, dist, rank, ws, steps, warmup, nprob):
