@@ -107,34 +107,43 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
             q[k] = sQ[m];
             u[k] = sU[m];
         }
-        // --- inviscid: D_+ F^+ + D_- F^- = [sum_k dc_k F_k + alpha d4_k U_k] / (6 h)
+        // --- inviscid: D_+ F^+ + D_- F^- = [sum_k dc_k F_k + alpha sum_k d4_k U_k] / (6 h)
+        // (alpha multiplies the fourth-difference sum once; dc_2 = 0 skips the
+        // centre's flux)
         R al = R(0);
 #pragma unroll
         for (int k = 0; k < 5; ++k) al = dmax(al, fabs(l == 0 ? q[k].x : q[k].y) + q[k].w);
-        R f0 = 0, f1 = 0, f2 = 0, f3 = 0;
+        R f0 = 0, f1 = 0, f2 = 0, f3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
+            const R w4 = (R)kD4[k];
+            h0 += w4 * u[k].x;
+            h1 += w4 * u[k].y;
+            h2 += w4 * u[k].z;
+            h3 += w4 * u[k].w;
+            if (kDC[k] == 0.0) continue;
             const R p = u[k].x * q[k].z;   // rho T
             const R ul = l == 0 ? q[k].x : q[k].y;
             const R F0 = l == 0 ? u[k].y : u[k].z;
             const R F1 = u[k].y * ul + (l == 0 ? p : R(0));
             const R F2 = u[k].z * ul + (l == 1 ? p : R(0));
             const R F3 = (u[k].w + p) * ul;
-            const R wc = (R)kDC[k], w4 = al * (R)kD4[k];
-            f0 += wc * F0 + w4 * u[k].x;
-            f1 += wc * F1 + w4 * u[k].y;
-            f2 += wc * F2 + w4 * u[k].z;
-            f3 += wc * F3 + w4 * u[k].w;
+            const R wc = (R)kDC[k];
+            f0 += wc * F0;
+            f1 += wc * F1;
+            f2 += wc * F2;
+            f3 += wc * F3;
         }
         const R inv6h = tc.i6[l];
-        res[0] -= f0 * inv6h;
-        res[1] -= f1 * inv6h;
-        res[2] -= f2 * inv6h;
-        res[3] -= f3 * inv6h;
-        // --- viscous, same direction: D^{(l),2}(K_ll, Z) of Eq. (9)
+        res[0] -= (f0 + al * h0) * inv6h;
+        res[1] -= (f1 + al * h1) * inv6h;
+        res[2] -= (f2 + al * h2) * inv6h;
+        res[3] -= (f3 + al * h3) * inv6h;
+        // --- viscous, same direction: D^{(l),2}(K_ll, Z) of Eq. (9), the K
+        // coefficients applied once to the sums over the stencil
         const R c1 = l == 0 ? mu43 : mu;   // K_ll entry on u
         const R c2 = l == 0 ? mu : mu43;   // K_ll entry on v
-        R d2u = 0, d2v = 0, d2T = 0, eq = 0;
+        R d2u = 0, d2v = 0, d2T = 0, equ = 0, eqv = 0;
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             d2u += (R)kD2[m] * q[m].x;
@@ -147,31 +156,37 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
                 bu += (R)kB[m][nn] * q[nn].x;
                 bv += (R)kB[m][nn] * q[nn].y;
             }
-            eq += c1 * q[m].x * bu + c2 * q[m].y * bv;
+            equ += q[m].x * bu;
+            eqv += q[m].y * bv;
         }
         const R i3h2 = tc.i3h2[l];   // (4/dx^2)/12
         res[1] += c1 * d2u * i3h2;
         res[2] += c2 * d2v * i3h2;
-        res[3] += ka * d2T * i3h2 + tc.f4h2[l] * eq;
-        // --- viscous, mixed: D_c^{(l)}(K_lm D_c^{(m)} Z), m != l
-        R g1 = 0, g2 = 0, g3 = 0;
+        res[3] += ka * d2T * i3h2 + tc.f4h2[l] * (c1 * equ + c2 * eqv);
+        // --- viscous, mixed: D_c^{(l)}(K_lm D_c^{(m)} Z), m != l, as sums of
+        // dc_k (d u, d v) and of dc_k (u d v, v d u) that the K entries multiply once
+        R su = 0, sv = 0, cuv = 0, cvu = 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             if (k == 2) continue;
             const R wc = (R)kDC[k];
-            if (l == 0) {   // K_12 d_y Z at the x-neighbours (y gradients: rows from 2)
-                const V4<R> gy = sGY[xl[k] - 2 * LX];
-                const R gyu = gy.y, gyv = gy.x;
-                g1 += wc * (-mu23 * gyv);
-                g2 += wc * (mu * gyu);
-                g3 += wc * (mu * q[k].y * gyu - mu23 * q[k].x * gyv);
-            } else {        // K_21 d_x Z at the y-neighbours
-                const V4<R> gx = sGX[T::gx(la, lb) + (k - 2) * T::GXW];
-                const R gxu = gx.y, gxv = gx.x;
-                g1 += wc * (mu * gxv);
-                g2 += wc * (-mu23 * gxu);
-                g3 += wc * (-mu23 * q[k].y * gxu + mu * q[k].x * gxv);
-            }
+            // y gradients at the x-neighbours (rows from 2), x gradients at the
+            // y-neighbours; records hold (d v, d u, d T)
+            const V4<R> g = l == 0 ? sGY[xl[k] - 2 * LX] : sGX[T::gx(la, lb) + (k - 2) * T::GXW];
+            su += wc * g.y;
+            sv += wc * g.x;
+            cuv += wc * (q[k].x * g.x);   // u d v
+            cvu += wc * (q[k].y * g.y);   // v d u
+        }
+        R g1, g2, g3;
+        if (l == 0) {   // K_12 d_y Z: (-2/3 mu d_y v, mu d_y u, mu v d_y u - 2/3 mu u d_y v)
+            g1 = -mu23 * sv;
+            g2 = mu * su;
+            g3 = mu * cvu - mu23 * cuv;
+        } else {        // K_21 d_x Z: (mu d_x v, -2/3 mu d_x u, mu u d_x v - 2/3 mu v d_x u)
+            g1 = mu * sv;
+            g2 = -mu23 * su;
+            g3 = mu * cuv - mu23 * cvu;
         }
         res[1] += g1 * inv6h;
         res[2] += g2 * inv6h;
