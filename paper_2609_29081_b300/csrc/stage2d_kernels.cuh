@@ -140,7 +140,9 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
         res[2] -= (f2 + al * h2) * inv6h;
         res[3] -= (f3 + al * h3) * inv6h;
         // --- viscous, same direction: D^{(l),2}(K_ll, Z) of Eq. (9), the K
-        // coefficients applied once to the sums over the stencil
+        // coefficients applied once to the sums over the stencil; the energy
+        // term's sum_m z_m (B z)_m is the quadratic form z^T B z, evaluated with
+        // the upper triangle of B + B^T (12 nonzero products instead of 19 + 5)
         const R c1 = l == 0 ? mu43 : mu;   // K_ll entry on u
         const R c2 = l == 0 ? mu : mu43;   // K_ll entry on v
         R d2u = 0, d2v = 0, d2T = 0, equ = 0, eqv = 0;
@@ -151,10 +153,11 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
             d2T += (R)kD2[m] * q[m].z;
             R bu = 0, bv = 0;
 #pragma unroll
-            for (int nn = 0; nn < 5; ++nn) {
-                if (kB[m][nn] == 0.0) continue;
-                bu += (R)kB[m][nn] * q[nn].x;
-                bv += (R)kB[m][nn] * q[nn].y;
+            for (int nn = m; nn < 5; ++nn) {
+                const double cmn = nn == m ? kB[m][m] : kB[m][nn] + kB[nn][m];
+                if (cmn == 0.0) continue;
+                bu += (R)cmn * q[nn].x;
+                bv += (R)cmn * q[nn].y;
             }
             equ += q[m].x * bu;
             eqv += q[m].y * bv;
@@ -971,15 +974,21 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
         const R ib = frcp(R(2) * rho * re);
         const R bx = (fsqrt(rho * rho * qx * qx + R(2) * rho * re * (txx * txx + txy * txy)) + rho * fabs(qx)) * ib;
         const R by = (fsqrt(rho * rho * qy * qy + R(2) * rho * re * (txy * txy + tyy * tyy)) + rho * fabs(qy)) * ib;
-        // Sec. 3.2 sensors
-        const R px = fabs(We.z - R(2) * p + Ww.z) * frcp(fabs(We.z + R(2) * p + Ww.z));
-        const R py = fabs(Wn.z - R(2) * p + Ws.z) * frcp(fabs(Wn.z + R(2) * p + Ws.z));
+        // Sec. 3.2 sensors: the larger of the two pressure ratios (FP64: one
+        // division, the ratios compared by cross-multiplication)
+        const R ax = fabs(We.z - R(2) * p + Ww.z), bxs = fabs(We.z + R(2) * p + Ww.z);
+        const R ay = fabs(Wn.z - R(2) * p + Ws.z), bys = fabs(Wn.z + R(2) * p + Ws.z);
+        R pxy;
+        if constexpr (sizeof(R) == 8)
+            pxy = ax * bys >= ay * bxs ? ax / bxs : ay / bys;
+        else
+            pxy = dmax(ax * frcp(bxs), ay * frcp(bys));
         const R curl = Sxv - Syu;
         const R ph2 = -div * frsqrt(div * div + curl * curl + R(1e-13));
         sCQ[CQ_FX * T::NCQ + t] = Q4{Fx[0], Fx[1], Fx[2], Fx[3]};
         sCQ[CQ_FY * T::NCQ + t] = Q4{Fy[0], Fy[1], Fy[2], Fy[3]};
         sCQ[CQ_RB * T::NCQ + t] = Q4{fabs(u) + cs, fabs(v) + cs, bx, by};
-        sCQ[CQ_PH * T::NCQ + t] = Q4{dmax(px, py), dmax(ph2, R(0)), R(0), R(0)};
+        sCQ[CQ_PH * T::NCQ + t] = Q4{pxy, dmax(ph2, R(0)), R(0), R(0)};
     }
     __syncthreads();
 
