@@ -296,7 +296,9 @@ __device__ __forceinline__ R pressure2(R rho, R mx, R my, R E, R gm1)
 // compute precision. FP32: the hardware approximations (PTX rcp/sqrt/rsqrt
 // .approx.ftz, __expf), within about 2 ulp: their values feed FP32 stencils and
 // screens whose own rounding is larger, and every positivity decision that they
-// could tip is re-taken in FP64. FP64: the correctly rounded operations.
+// could tip is re-taken in FP64. FP64: correctly rounded division and square
+// root; the reciprocal square root from the math library's rsqrt (1 ulp), one
+// operation instead of a square root and a division.
 template <class R>
 __device__ __forceinline__ R frcp(R x)
 {
@@ -327,7 +329,7 @@ __device__ __forceinline__ R frsqrt(R x)
         asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     } else {
-        return 1.0 / sqrt(x);
+        return rsqrt(x);
     }
 }
 template <class R>

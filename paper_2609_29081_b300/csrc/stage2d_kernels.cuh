@@ -113,7 +113,10 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
         R al = R(0);
 #pragma unroll
         for (int k = 0; k < 5; ++k) al = dmax(al, fabs(l == 0 ? q[k].x : q[k].y) + q[k].w);
-        R f0 = 0, f1 = 0, f2 = 0, f3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+        // F_l = u_l U + p (0, e_x, e_y, u_l) with the mass flux m_l kept exact:
+        // sum_k dc_k F_k = (sum dc_k m_l, sum a_k m_x, sum a_k m_y, sum a_k E)
+        //                + (0, P e_x, P e_y, sum a_k p_k),  a_k = dc_k u_l,k, P = sum dc_k p_k
+        R f0 = 0, f1 = 0, f2 = 0, f3 = 0, h0 = 0, h1 = 0, h2 = 0, h3 = 0, sp = 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const R w4 = (R)kD4[k];
@@ -122,18 +125,19 @@ __device__ __forceinline__ void point_residual(const V4<R> *sm, int la, int lb, 
             h2 += w4 * u[k].z;
             h3 += w4 * u[k].w;
             if (kDC[k] == 0.0) continue;
-            const R p = u[k].x * q[k].z;   // rho T
-            const R ul = l == 0 ? q[k].x : q[k].y;
-            const R F0 = l == 0 ? u[k].y : u[k].z;
-            const R F1 = u[k].y * ul + (l == 0 ? p : R(0));
-            const R F2 = u[k].z * ul + (l == 1 ? p : R(0));
-            const R F3 = (u[k].w + p) * ul;
             const R wc = (R)kDC[k];
-            f0 += wc * F0;
-            f1 += wc * F1;
-            f2 += wc * F2;
-            f3 += wc * F3;
+            const R p = u[k].x * q[k].z;   // rho T
+            const R a = wc * (l == 0 ? q[k].x : q[k].y);
+            f0 += wc * (l == 0 ? u[k].y : u[k].z);
+            f1 += a * u[k].y;
+            f2 += a * u[k].z;
+            f3 += a * (u[k].w + p);
+            sp += wc * p;
         }
+        if (l == 0)
+            f1 += sp;
+        else
+            f2 += sp;
         const R inv6h = tc.i6[l];
         res[0] -= (f0 + al * h0) * inv6h;
         res[1] -= (f1 + al * h1) * inv6h;
