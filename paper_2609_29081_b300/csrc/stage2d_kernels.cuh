@@ -208,6 +208,40 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 xy2(const V4<float> &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 zw2(const V4<float> &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+// Float-float arithmetic of two components at once: the error-free sums and
+// products of ff_quick / ff_two_sum / ff_add / ff_mul, lane by lane, with the
+// same operations in the same order (so the same bits as the one-lane form).
+struct ff2 {
+    float2 h, l;
+};
+__device__ __forceinline__ ff2 ff2_quick(float2 a, float2 b)
+{
+    const float2 s = add2(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ ff2 ff2_two_sum(float2 a, float2 b)
+{
+    const float2 s = add2(a, b), bb = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b)
+{
+    const ff2 s = ff2_two_sum(a.h, b.h);
+    return ff2_quick(s.h, add2(add2(s.l, a.l), b.l));
+}
+// a weight (the same for both lanes) times a pair
+__device__ __forceinline__ ff2 ff2_mul(ff a, ff2 b)
+{
+    const float2 ah = bc2(a.h), al = bc2(a.l);
+    const float2 p = mul2(ah, b.h);
+    float2 e = fma2(ah, b.h, neg2(p));
+    e = fma2(ah, b.l, fma2(al, b.h, e));
+    return ff2_quick(p, e);
+}
 
 // FP32 form of the point residual: the sums of the generic form above, carried
 // in the component pairs (rho, m_x), (m_y, E), (u, v) and the gradient pairs
@@ -1199,6 +1233,41 @@ __device__ __forceinline__ bool stage_tile(const StageArgs &A, int bx, int by, V
                 src_f = (float)src;
                 src_inc = ff_from(A.k.cl * dt * src);
                 src_acc = ff_from(A.k.bl * dt * src);
+            }
+            if (!A.source && !A.k.residual) {
+                // components in pairs (rho, m_x), (m_y, E) through two-lane FP32
+                // instructions: the same float-float operations lane by lane
+#pragma unroll
+                for (int hp = 0; hp < 2; ++hp) {
+                    const int c = 2 * hp;
+                    const float2 fr = hp ? zw2(fxr) : xy2(fxr), fl = hp ? zw2(fxl) : xy2(fxl);
+                    const float2 ft = hp ? zw2(fyt) : xy2(fyt), fb = hp ? zw2(fyb) : xy2(fyb);
+                    const ff2 dxf = ff2_two_sum(fl, neg2(fr)), dyf = ff2_two_sum(fb, neg2(ft));   // exact
+                    const ff2 inc = ff2_add(ff2_mul(wx, dxf), ff2_mul(wy, dyf));
+                    const ff2 uv = {hp ? zw2(ui) : xy2(ui), make_float2(ulo[c], ulo[c + 1])};
+                    const ff2 g0 = {make_float2(g0h[c], g0h[c + 1]), make_float2(g0l[c], g0l[c + 1])};
+                    const ff2 g2 = {make_float2(g2h[c], g2h[c + 1]), make_float2(g2l[c], g2l[c + 1])};
+                    ff2 v = ff2_mul(a1, uv);
+                    if (tc.ua0) v = ff2_add(v, ff2_mul(a0, g0));
+                    if (tc.ua2) v = ff2_add(v, ff2_mul(a2, g2));
+                    if (A.k.acc) {
+                        ff2 ac = ff2_add(ff2_mul(b2, g2), ff2_mul(b1, uv));
+                        ac = ff2_add(ac, ff2_add(ff2_mul(bx, dxf), ff2_mul(by, dyf)));
+                        aux[plane_of(L, 0, c) + off] = ac.h.x;
+                        aux[comp_plane(L, c) + off] = ac.l.x;
+                        aux[plane_of(L, 0, c + 1) + off] = ac.h.y;
+                        aux[comp_plane(L, c + 1) + off] = ac.l.y;
+                    }
+                    v = ff2_add(v, inc);
+                    out[plane_of(L, 0, c) + off] = v.h.x;
+                    out[comp_plane(L, c) + off] = v.l.x;
+                    out[plane_of(L, 0, c + 1) + off] = v.h.y;
+                    out[comp_plane(L, c + 1) + off] = v.l.y;
+                    o4[c] = v.h.x;
+                    o4[c + 1] = v.h.y;
+                }
+                if (A.k.cfl_out) cfl_terms(A.cfl, o4[0], o4[1], o4[2], o4[3], cfl1, cfl2);
+                continue;
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
